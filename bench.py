@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark of the Ozaki-scheme multi-component product on GB300.
+
+Workload (the headline one): double-double C = A B with m = n = k = 4096,
+operands of Eq. 1 with exponent spread phi = 1 (synthetic, seeded), the
+slice count chosen automatically for the 2^-100 target; the digit form is
+selectable (default: the e4m3-digit form).  A step is the whole hot path:
+exponent reduce + digit split (K1, K2) and the fused slice products with
+exact accumulation (K3).  Metric: effective GFLOP/s = 2 m n k / time.
+
+Printed: one JSON line (rank 0).  Besides the contract keys it carries
+  roofline      -- the slice-product kernel: algorithmic tensor FLOPs
+                   (pairs * 2 m n k) / its CUDA-event time, against the
+                   e4m3 dense peak derived from the measured bf16 peak;
+  splitter      -- HBM bytes of K1 + K2 / their time, against measured HBM;
+  e2e           -- the same metric through the C ABI with host buffers
+                   (pinned H2D of A, B and D2H of C inside the timed region);
+  cpu_baseline  -- the oracle (exact product rounded to 512 bits) on the
+                   host cores, on a bounded block of the same product, with
+                   the GPU result's error against it;
+  variants      -- single timed passes of the other forms/precisions
+                   (DD and QD, e4m3 / int8 / binary64 digits) at 4096^3.
+
+--impl reference times the oracle itself (the CPU reference of this repo)
+on a bounded block per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_BYTES = 129 * 2 ** 20
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("bf16_tflops_sustained", 1700.0), "measured"
+    return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons, pw = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+                pw.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(pw) if pw else None}
+
+
+# ---------------------------------------------------------------------------
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _host_operands(prec, m, n, k, phi, seed):
+    from ozmp_inputs import gen_problem
+    return gen_problem(prec, m, n, k, phi=phi, seed=seed)
+
+
+def run_variant(oz, torch, prec, form, n, phi, steps, warmup, nslices=0):
+    """Device-resident timing of one (precision, form): returns a dict."""
+    import numpy as np
+    A, B = _host_operands(prec, n, n, n, phi, 0)
+    Ad = [oz.colmajor(a) for a in A]
+    Bd = [oz.colmajor(b) for b in B]
+    dt = torch.float32 if prec == "ts" else torch.float64
+    q = len(A)
+    C = [torch.empty((n, n), dtype=dt, device="cuda").T for _ in range(q)]
+    p = oz.Plan(prec, n, n, n, form, nslices)
+    for _ in range(warmup):
+        p.split(Ad, Bd)
+        p.multiply(C)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    for s in range(steps):
+        ev[s][0].record()
+        p.split(Ad, Bd)
+        ev[s][1].record()
+        p.multiply(C)
+        ev[s][2].record()
+    torch.cuda.synchronize()
+    split_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    gemm_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    tot = ev[0][0].elapsed_time(ev[-1][2]) / steps
+    st = p.status()
+    i = p.info
+    flops = 2.0 * n * n * n
+    out = {"prec": prec, "form": oz.Form(i.form).name.lower(), "beta": i.beta, "nslices": i.nslices,
+           "pairs": i.npairs, "ms_per_step": tot, "gflops": flops / (tot * 1e-3) / 1e9,
+           "split_ms": sum(split_ms) / steps, "gemm_ms": sum(gemm_ms) / steps,
+           "slice_tflops": i.npairs * flops / (sum(gemm_ms) / steps * 1e-3) / 1e12, "status": st.name}
+    del p, Ad, Bd, C
+    torch.cuda.empty_cache()
+    return out
+
+
+def splitter_bytes(q, w, m, n, k, s, db):
+    # K1 reads both operands, K2 reads them again and writes the digits
+    return 2 * q * w * (m * k + k * n) + s * db * (m * k + k * n)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="dd")
+    ap.add_argument("--form", default="fp8")
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--phi", type=float, default=1.0)
+    ap.add_argument("--nslices", type=int, default=0)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = _dist()
+    workload = f"{args.prec} gemm m=n=k={args.n}, phi={args.phi}, Eq. 1 operands (configs: DD/QD 4096^3 fp64 vs int8 slices)"
+    metric = "DD/QD GEMM effective GFLOP/s (2mnk/s) and % of slice roofline, INT8 vs FP64"
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        from oracle import _clib
+        m = n = k = args.n
+        A, B = _host_operands(args.prec, m, n, k, args.phi, 0)
+        blk = 48
+        rows, cols = list(range(blk)), list(range(blk))
+        for _ in range(args.warmup):
+            _clib.exact_block(A, B, rows[:8], cols[:8])
+        t0 = time.time()
+        for s in range(args.steps):
+            r0 = (s * blk) % m
+            _clib.exact_block(A, B, [r0 + i for i in rows], cols)
+        dt = (time.time() - t0) / args.steps
+        val = 2.0 * blk * blk * k / dt / 1e9
+        cores = os.cpu_count()
+        line = {"impl": "reference", "metric": metric, "value": val, "unit": "GFLOP/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64 components, exact 512-bit",
+                "data": "synthetic (Eq. 1, seeded)",
+                "config": {"workload": workload, "sample": f"{blk}x{blk} block of C per step, full k={k}"},
+                "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                                 "sample": f"{blk}x{blk} block of C, k={k}, exact dot products rounded to 512 bits"},
+                "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    import paper_2301_09960_gb300 as oz
+
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    oz.load()
+
+    m = n = k = args.n
+    prec, form = args.prec, args.form
+    A, B = _host_operands(prec, m, n, k, args.phi, 1000 * rank)
+    q = len(A)
+    dt = torch.float32 if prec == "ts" else torch.float64
+    w = 4 if prec == "ts" else 8
+    Ad = [oz.colmajor(a) for a in A]
+    Bd = [oz.colmajor(b) for b in B]
+    C = [torch.empty((n, m), dtype=dt, device="cuda").T for _ in range(q)]
+    plan = oz.Plan(prec, m, n, k, form, args.nslices)
+    info = plan.info
+
+    for _ in range(args.warmup):
+        plan.split(Ad, Bd)
+        plan.multiply(C)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    for s in range(args.steps):
+        ev[s][0].record()
+        plan.split(Ad, Bd)
+        ev[s][1].record()
+        plan.multiply(C)
+        ev[s][2].record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    total_ms = ev[0][0].elapsed_time(ev[-1][2])
+    clk = clocks.stop()
+    split_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
+    gemm_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / args.steps
+    status = plan.status()
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    flops = 2.0 * m * n * k
+    value = ws * flops / (ms_per_step * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers ----
+    Ah = [torch.from_numpy(a.T.copy()).pin_memory() for a in A]     # (k, m) rows = columns of A
+    Bh = [torch.from_numpy(b.T.copy()).pin_memory() for b in B]
+    Ch = [torch.empty((n, m), dtype=dt).pin_memory() for _ in range(q)]
+    Ad2 = [torch.empty((k, m), dtype=dt, device="cuda") for _ in range(q)]
+    Bd2 = [torch.empty((n, k), dtype=dt, device="cuda") for _ in range(q)]
+    Cd2 = [torch.empty((n, m), dtype=dt, device="cuda") for _ in range(q)]
+    h2d = sum(t.numel() * t.element_size() for t in Ah + Bh)
+    d2h = sum(t.numel() * t.element_size() for t in Ch)
+    e2e_steps = max(1, min(args.steps, 5))
+
+    def e2e_step():
+        for x, y in zip(Ad2, Ah):
+            x.copy_(y, non_blocking=True)
+        for x, y in zip(Bd2, Bh):
+            x.copy_(y, non_blocking=True)
+        plan.execute([x.T for x in Ad2], [x.T for x in Bd2], [x.T for x in Cd2])
+        for x, y in zip(Ch, Cd2):
+            x.copy_(y, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_val = ws * flops / (e2e_ms * 1e-3) / 1e9
+
+    # ---- roofline of the dominant kernel (slice products) ----
+    hbm, bf16, bf16_sus, src = measured_peaks()
+    peak_fp8 = bf16 * 2.0        # e4m3 dense / bf16 dense nominal ratio (4.5 / 2.25)
+    alg_flops = info.npairs * flops
+    achieved = alg_flops / (gemm_ms * 1e-3) / 1e12
+    if info.form == oz.Form.FP8:
+        peak, peak_note = peak_fp8, f"e4m3 dense = bf16 {src} x 2 (nominal ratio)"
+    elif info.form == oz.Form.INT8:
+        peak, peak_note = 151.3, "IMMA mma.sync s8 microbenchmark on this GB300 (no MEASURED_PEAKS entry)"
+    else:
+        peak, peak_note = 1.05, "DMMA mma.sync f64 microbenchmark on this GB300 (no MEASURED_PEAKS entry)"
+    sbytes = splitter_bytes(q, w, m, n, k, info.nslices, info.digit_bytes)
+
+    line = {
+        "metric": metric, "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "e4m3 digits / f32 acc" if info.form == oz.Form.FP8 else
+        ("s8 digits / s32 acc" if info.form == oz.Form.INT8 else "f64 digits / f64 acc"),
+        "data": "synthetic (Eq. 1, seeded)",
+        "config": {"workload": workload, "prec": prec, "form": oz.Form(info.form).name.lower(), "m": m, "n": n,
+                   "k": k, "phi": args.phi, "beta": info.beta, "nslices": info.nslices, "pairs": info.npairs,
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 gpu",
+                   "l2": "inputs larger than L2 (A, B and the digit workspace each exceed 129 MB)"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_gemm_b1/k_gemm_f64 (slice products)",
+                     "peak_source": peak_note},
+        "splitter": {"ms": split_ms, "bytes": sbytes, "achieved_gbs": sbytes / (split_ms * 1e-3) / 1e9,
+                     "peak_gbs": hbm, "frac": sbytes / (split_ms * 1e-3) / 1e9 / hbm},
+        "stage_ms": {"split": split_ms, "products": gemm_ms},
+        "e2e": {"value": e2e_val, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_ms},
+        "gpu_launches": 6 * args.steps,
+        "clocks": clk,
+        "device_status": status.name,
+    }
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        # oracle on the host cores: exact product of a bounded block, and the
+        # GPU result's error on that block
+        from oracle import _clib
+        from oracle import exact as X
+        blk = 160
+        rows = list(range(0, m, m // blk))[:blk]
+        cols = list(range(0, n, n // blk))[:blk]
+        t0 = time.time()
+        ex = _clib.exact_block(A, B, rows, cols)
+        tcpu = time.time() - t0
+        Cg = [c.cpu().numpy() for c in C]
+        chat = [[[float(c[a, b]) for c in Cg] for b in cols] for a in rows]
+        em = X.error_metrics(chat, ex)
+        line["cpu_baseline"] = {"value": 2.0 * len(rows) * len(cols) * k / tcpu / 1e9, "unit": "GFLOP/s",
+                                "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"{len(rows)}x{len(cols)} strided block of C, full k={k}: exact dot "
+                                          f"products rounded to 512 bits ({tcpu:.1f} s)"}
+        line["error"] = {"err_nw": em["err_nw"], "err_max_rel": em["err_max"],
+                         "vs": "exact product rounded to 512 bits, same block", "target": 2.0 ** -100}
+
+    if rank == 0 and ws == 1 and not args.no_variants:
+        del Ad, Bd, C, Ad2, Bd2, Cd2
+        torch.cuda.empty_cache()
+        var = []
+        for vp, vf in [("dd", "int8"), ("dd", "fp64"), ("qd", "fp8"), ("qd", "int8"), ("qd", "fp64")]:
+            try:
+                var.append(run_variant(oz, torch, vp, vf, args.n, args.phi, 1, 1))
+            except Exception as ex:  # report, do not hide
+                var.append({"prec": vp, "form": vf, "error": repr(ex)[:200]})
+        line["variants"] = var
+
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

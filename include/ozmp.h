@@ -1,0 +1,189 @@
+/*
+ * ozmp -- Ozaki-scheme multiple-precision matrix product on GB300 (sm_103a).
+ *
+ * C ABI of the library.  It computes C := A * B (paper, Sec. 1 problem
+ * statement; Sec. 3, Algorithm 1) for multi-component operands: every
+ * element is the exact sum of q components, DD/TD/QD = 2/3/4 binary64
+ * words, TS = 3 binary32 words (Sec. 1).
+ *
+ * Layout and ownership (every entry point):
+ *   - Matrices are column-major (BLAS convention of the problem C := AB).
+ *     A is m x k with leading dimension lda >= max(1, m), B is k x n with
+ *     ldb >= max(1, k), C is m x n with ldc >= max(1, m).
+ *   - Each component is a separate device array; all components of one
+ *     operand share its leading dimension.  A[c], B[c], C[c] are device
+ *     pointers owned by the caller.  C's components must not alias A's or
+ *     B's.  Inputs may be unnormalised and sign-mixed: the value is the exact
+ *     component sum.
+ *   - Output: C's components are the canonical expansion of the computed
+ *     Ozaki sum S: c_0 = RN(S), c_t = RN(S - c_0 - ... - c_{t-1}).
+ *
+ * Method (Algorithm 1 with exact truncating digit slices):
+ *   1. exponent reduce: E_i = max_p E(a_ip), F_j = max_p E(b_pj) with
+ *      E(x) = floor(log2|x|) + 1 of the exact value (the power of two of the
+ *      tau vectors of Algorithm 1); all-zero rows/columns get OZMP_EXP_ZERO.
+ *   2. digit split: |x| * 2^(beta*s - E) truncated toward zero to beta*s
+ *      bits, cut into s signed digits of beta bits (sign of x); the digits
+ *      plus a remainder below 2^(E - beta*s) sum to x exactly.
+ *   3. slice products over the pairs t + u <= s + 1 (Algorithm 1's pair
+ *      triangle), exact on the tensor cores: binary64 digits (DMMA),
+ *      int8 digits (IMMA, int32 accumulation) or e4m3 digits |d| <= 15
+ *      (QMMA, binary32 accumulation of integers below 2^24).
+ *   4. the slice products are summed exactly in integer arithmetic and
+ *      rounded once into the output components (the "L-bit computation" of
+ *      Algorithm 1), fused into the product kernel.
+ *
+ * Errors: argument errors return synchronously; data errors (NaN/Inf input,
+ * exponents outside the representable window) are written to a device
+ * status word, readable with ozmp_plan_get_status / ozmp_last_status after
+ * the stream has been synchronised.  C is unspecified after a data error.
+ * Calls are stream-ordered and asynchronous.
+ */
+#ifndef OZMP_H
+#define OZMP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OZMP_OK = 0,
+    OZMP_ERR_INVALID_ARG = 1,  /* null pointer, ld too small, bad enum, s out of range */
+    OZMP_ERR_NONFINITE = 2,    /* device status: an input component is NaN or Inf */
+    OZMP_ERR_RANGE = 3,        /* device status: a scale or output exponent leaves the normal range */
+    OZMP_ERR_NOMEM = 4,        /* workspace allocation failed or supplied workspace too small */
+    OZMP_ERR_CUDA = 5,         /* a CUDA runtime call failed */
+    OZMP_ERR_UNSUPPORTED = 6,  /* shape/precision/form combination not provided */
+    OZMP_ERR_TIMEOUT = 7       /* device status: a bounded wait in the batched scheduler gave up */
+} ozmp_status;
+
+/* precision of the operands (component count and word type) */
+typedef enum { OZMP_DD = 2, OZMP_TD = 3, OZMP_QD = 4, OZMP_TS = 103 } ozmp_prec;
+
+/* digit form of the slice products */
+typedef enum {
+    OZMP_FORM_AUTO = 0,  /* fastest exact form on this GPU (FP8 digits) */
+    OZMP_FORM_FP64 = 1,  /* binary64 digits, beta = max{b: k (2^b - 1)^2 <= 2^53}, DMMA */
+    OZMP_FORM_INT8 = 2,  /* int8 digits, beta = 7, IMMA int32 accumulation */
+    OZMP_FORM_FP8  = 3   /* e4m3 digits, beta = 4, QMMA binary32 accumulation */
+} ozmp_form;
+
+/* all-zero row/column exponent */
+#define OZMP_EXP_ZERO ((int32_t)(-2147483647 - 1))
+/* largest slice count */
+#define OZMP_MAX_SLICES 64
+
+/* cudaStream_t, passed as an opaque pointer (NULL = the legacy default stream) */
+typedef void* ozmp_stream;
+typedef struct ozmp_plan_s* ozmp_plan;
+
+/* Read-only description of a plan. */
+typedef struct {
+    int prec;            /* ozmp_prec */
+    int form;            /* ozmp_form actually used */
+    int beta;            /* bits per digit */
+    int nslices;         /* s */
+    int64_t npairs;      /* s (s + 1) / 2 */
+    int64_t m, n, k;
+    int64_t mp, np, kp;  /* padded sizes of the digit workspace */
+    int digit_bytes;     /* 1 (int8 / e4m3) or 8 (binary64) */
+    int acc_words;       /* 64-bit words of the exact per-element accumulator */
+    int ngroups;         /* diagonal groups, one accumulator update each */
+    int pairs_per_drain; /* slice pairs summed in the tensor-core accumulator */
+    size_t workspace_bytes;
+    /* byte offsets of the workspace regions (device layout) */
+    size_t off_E, off_F, off_status, off_Adig, off_Bdig, off_acc;
+} ozmp_plan_info;
+
+/*
+ * ozmp_plan_create -- fix precision, shape, digit form and slice count.
+ * Sec. 3, Algorithm 1 (the choice of D, here nslices) and Sec. 3's remark
+ * that the needed slice count depends on the data.
+ *   nslices = 0 chooses s from the precision's target (2^-100 DD, 2^-150 TD,
+ *   2^-200 QD, 2^-66 TS) with a guard of log2 k + 16 bits; 1..64 forces s.
+ *   stream: stream used by later executions through this plan.
+ * The plan allocates its workspace lazily on first execution unless one is
+ * supplied with ozmp_plan_set_workspace.  Returns INVALID_ARG for bad
+ * arguments, UNSUPPORTED when k exceeds the form's exact-accumulation limit.
+ */
+ozmp_status ozmp_plan_create(ozmp_plan* plan, ozmp_prec prec, int64_t m, int64_t n, int64_t k,
+                             ozmp_form form, int nslices, ozmp_stream stream);
+
+/* Release the plan and any workspace it allocated (not a supplied one). */
+ozmp_status ozmp_plan_destroy(ozmp_plan plan);
+
+/* Describe the plan (sizes, digit width, workspace layout). */
+ozmp_status ozmp_plan_get_info(ozmp_plan plan, ozmp_plan_info* info);
+
+/* Use caller-owned device memory of at least info.workspace_bytes bytes
+ * (256-byte aligned) as the workspace; the caller keeps ownership. */
+ozmp_status ozmp_plan_set_workspace(ozmp_plan plan, void* dev_ptr, size_t bytes);
+
+/* Change the stream of later executions. */
+ozmp_status ozmp_plan_set_stream(ozmp_plan plan, ozmp_stream stream);
+
+/*
+ * Execute the whole product through a plan: exponent reduce, digit split,
+ * fused slice products + exact accumulation.  A, B, C are arrays of q
+ * component pointers (double* for DD/TD/QD, float* for TS).
+ */
+ozmp_status ozmp_plan_execute(ozmp_plan plan, const void* const* A, int64_t lda,
+                              const void* const* B, int64_t ldb, void* const* C, int64_t ldc);
+
+/* Device status word of the plan's last execution (synchronises the plan's
+ * stream first). */
+ozmp_status ozmp_plan_get_status(ozmp_plan plan, ozmp_status* device_status);
+
+/*
+ * Plain entry points (Sec. 1 problem statement, C := AB), one per precision.
+ * They use a per-thread cached plan on the stream set with ozmp_set_stream
+ * (default: legacy stream), FORM_AUTO, and nslices as for ozmp_plan_create.
+ */
+ozmp_status ozmp_gemm_dd(int64_t m, int64_t n, int64_t k, const double* const A[2], int64_t lda,
+                         const double* const B[2], int64_t ldb, double* const C[2], int64_t ldc,
+                         int nslices);
+ozmp_status ozmp_gemm_td(int64_t m, int64_t n, int64_t k, const double* const A[3], int64_t lda,
+                         const double* const B[3], int64_t ldb, double* const C[3], int64_t ldc,
+                         int nslices);
+ozmp_status ozmp_gemm_qd(int64_t m, int64_t n, int64_t k, const double* const A[4], int64_t lda,
+                         const double* const B[4], int64_t ldb, double* const C[4], int64_t ldc,
+                         int nslices);
+ozmp_status ozmp_gemm_ts(int64_t m, int64_t n, int64_t k, const float* const A[3], int64_t lda,
+                         const float* const B[3], int64_t ldb, float* const C[3], int64_t ldc,
+                         int nslices);
+
+/* Stream and digit form used by the plain entry points of this thread. */
+ozmp_status ozmp_set_stream(ozmp_stream stream);
+ozmp_status ozmp_set_form(ozmp_form form);
+/* Device status of this thread's last plain call (synchronises its stream). */
+ozmp_status ozmp_last_status(ozmp_status* device_status);
+
+/*
+ * Diagnostics (parity checks of the individual stages).
+ * ozmp_plan_split: run only the exponent reduce and the digit split into the
+ *   workspace (read E, F and the digits through ozmp_plan_get_info's
+ *   offsets).  Digit t of row i of A sits at
+ *   Adig[((t * mp) + i) * kp + p], of column j of B at Bdig[((t * np) + j) * kp + p].
+ * ozmp_plan_diagonal: after a split, write T_d = sum_{t+u=d} A_t B_u^T as
+ *   int64 to the device array T (column-major m x n, leading dimension m),
+ *   computed by the same tensor-core main loop as the product.
+ */
+ozmp_status ozmp_plan_split(ozmp_plan plan, const void* const* A, int64_t lda,
+                            const void* const* B, int64_t ldb);
+/* ozmp_plan_multiply: the fused slice products + exact accumulation alone,
+ *   on the digits and exponents left in the workspace by ozmp_plan_split
+ *   (ozmp_plan_execute = ozmp_plan_split + ozmp_plan_multiply).  C as for
+ *   ozmp_plan_execute. */
+ozmp_status ozmp_plan_multiply(ozmp_plan plan, void* const* C, int64_t ldc);
+ozmp_status ozmp_plan_diagonal(ozmp_plan plan, int d, int64_t* T);
+
+/* Version string of the library build. */
+const char* ozmp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OZMP_H */

@@ -1,0 +1,404 @@
+// Internal device helpers of the ozmp library (not part of the C ABI).
+//
+// All arithmetic that decides a digit, an exponent or an output component is
+// exact integer arithmetic on the IEEE-754 encodings: on GB300 the integer
+// ALU is far faster than the binary64 pipe, and exactness makes every stage
+// reproducible bit for bit.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "../../include/ozmp.h"
+
+namespace ozmp {
+
+// ----------------------------------------------------------------------------
+// status word bits (device) -> ozmp_status (host picks the first set bit)
+// ----------------------------------------------------------------------------
+enum : uint32_t { ST_NONFINITE = 1u, ST_RANGE = 2u, ST_TIMEOUT = 4u };
+
+// ----------------------------------------------------------------------------
+// 64-bit shifts that are defined for every count (0 for counts >= 64)
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t shl(uint64_t x, int n) { return (n >= 64 || n < 0) ? 0ull : (x << n); }
+__device__ __forceinline__ uint64_t shr(uint64_t x, int n) { return (n >= 64 || n < 0) ? 0ull : (x >> n); }
+
+// ----------------------------------------------------------------------------
+// decoding one component: value = (-1)^neg * M * 2^e, M < 2^53 (0 = zero)
+// ----------------------------------------------------------------------------
+struct Comp {
+    uint64_t M;
+    int e;
+    int neg;
+};
+
+__device__ __forceinline__ bool decode(double x, Comp& c) {
+    uint64_t b = (uint64_t)__double_as_longlong(x);
+    int ex = (int)((b >> 52) & 0x7ff);
+    uint64_t fr = b & 0xFFFFFFFFFFFFFull;
+    c.neg = (int)(b >> 63);
+    if (ex == 0x7ff) { c.M = 0; c.e = 0; return false; }
+    if (ex == 0) { c.M = fr; c.e = -1074; }
+    else { c.M = fr | (1ull << 52); c.e = ex - 1075; }
+    return true;
+}
+
+__device__ __forceinline__ bool decode(float x, Comp& c) {
+    uint32_t b = __float_as_uint(x);
+    int ex = (int)((b >> 23) & 0xff);
+    uint32_t fr = b & 0x7fffffu;
+    c.neg = (int)(b >> 31);
+    if (ex == 0xff) { c.M = 0; c.e = 0; return false; }
+    if (ex == 0) { c.M = fr; c.e = -149; }
+    else { c.M = fr | (1u << 23); c.e = ex - 150; }
+    return true;
+}
+
+__device__ __forceinline__ int bitlen(uint64_t x) { return 64 - __clzll((long long)x); }
+
+// ----------------------------------------------------------------------------
+// multiword two's complement helpers (NW words, word 0 least significant)
+// ----------------------------------------------------------------------------
+template <int NW>
+__device__ __forceinline__ void mw_add(uint64_t (&w)[NW], const uint64_t (&p)[NW]) {
+    uint64_t c = 0;
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+        uint64_t s = w[j] + p[j];
+        uint64_t c1 = (s < w[j]);
+        uint64_t s2 = s + c;
+        uint64_t c2 = (s2 < s);
+        w[j] = s2;
+        c = c1 | c2;
+    }
+}
+
+template <int NW>
+__device__ __forceinline__ void mw_sub(uint64_t (&w)[NW], const uint64_t (&p)[NW]) {
+    uint64_t b = 0;
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+        uint64_t d = w[j] - p[j];
+        uint64_t b1 = (w[j] < p[j]);
+        uint64_t d2 = d - b;
+        uint64_t b2 = (d < b);
+        w[j] = d2;
+        b = b1 | b2;
+    }
+}
+
+template <int NW>
+__device__ __forceinline__ void mw_neg(uint64_t (&w)[NW]) {
+    uint64_t c = 1;
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+        uint64_t x = ~w[j] + c;
+        c = (c && x == 0) ? 1ull : 0ull;
+        w[j] = x;
+    }
+}
+
+template <int NW>
+__device__ __forceinline__ bool mw_is_zero(const uint64_t (&w)[NW]) {
+    uint64_t o = 0;
+#pragma unroll
+    for (int j = 0; j < NW; ++j) o |= w[j];
+    return o == 0;
+}
+
+// index of the highest set bit, -1 for zero
+template <int NW>
+__device__ __forceinline__ int mw_top(const uint64_t (&w)[NW]) {
+    int t = -1;
+#pragma unroll
+    for (int j = 0; j < NW; ++j)
+        if (w[j]) t = 64 * j + 63 - __clzll((long long)w[j]);
+    return t;
+}
+
+// the unsigned value v placed with its bit 0 at window bit `sh` (may be < 0:
+// bits below the window are dropped), as NW words
+template <int NW>
+__device__ __forceinline__ void mw_place(uint64_t (&p)[NW], uint64_t v, int sh) {
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+        int o = sh - 64 * j;
+        p[j] = (o >= 0) ? shl(v, o) : shr(v, -o);
+    }
+}
+
+// logical left shift by n bits (0 <= n), static word indices only
+template <int NW>
+__device__ __forceinline__ void mw_shl(uint64_t (&w)[NW], int n) {
+    if (n >= 64 * NW) {
+#pragma unroll
+        for (int j = 0; j < NW; ++j) w[j] = 0;
+        return;
+    }
+    int ws = n >> 6, b = n & 63;
+#pragma unroll
+    for (int step = 1; step < NW; step <<= 1) {
+        if (ws & step) {
+#pragma unroll
+            for (int j = NW - 1; j >= 0; --j) w[j] = (j - step >= 0) ? w[j - step] : 0ull;
+        }
+    }
+    if (b) {
+#pragma unroll
+        for (int j = NW - 1; j >= 0; --j) w[j] = (w[j] << b) | ((j > 0) ? (w[j - 1] >> (64 - b)) : 0ull);
+    }
+}
+
+// logical right shift by n bits (0 <= n)
+template <int NW>
+__device__ __forceinline__ void mw_shr(uint64_t (&w)[NW], int n) {
+    if (n >= 64 * NW) {
+#pragma unroll
+        for (int j = 0; j < NW; ++j) w[j] = 0;
+        return;
+    }
+    int ws = n >> 6, b = n & 63;
+#pragma unroll
+    for (int step = 1; step < NW; step <<= 1) {
+        if (ws & step) {
+#pragma unroll
+            for (int j = 0; j < NW; ++j) w[j] = (j + step < NW) ? w[j + step] : 0ull;
+        }
+    }
+    if (b) {
+#pragma unroll
+        for (int j = 0; j < NW; ++j) w[j] = (w[j] >> b) | ((j + 1 < NW) ? (w[j + 1] << (64 - b)) : 0ull);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// exact sum of up to Q components into a fixed window
+// ----------------------------------------------------------------------------
+// Adds every component, truncated toward zero at window bit 0 (weight 2^L),
+// into the two's complement window w.  Returns true if some component has a
+// non-zero bit below the window (then w is not the exact sum).
+template <int NW>
+__device__ __forceinline__ bool window_sum(uint64_t (&w)[NW], const Comp* c, int q, int L) {
+    bool tail = false;
+#pragma unroll
+    for (int j = 0; j < NW; ++j) w[j] = 0;
+#pragma unroll 4
+    for (int i = 0; i < q; ++i) {
+        if (c[i].M == 0) continue;
+        int sh = c[i].e - L;
+        if (sh < 0) {
+            int r = -sh;
+            uint64_t mask = (r >= 64) ? ~0ull : ((1ull << r) - 1ull);
+            if (c[i].M & mask) tail = true;
+        }
+        uint64_t p[NW];
+        mw_place<NW>(p, c[i].M, sh);
+        if (c[i].neg) mw_sub<NW>(w, p); else mw_add<NW>(w, p);
+    }
+    return tail;
+}
+
+// Window of the wide (slow) path: covers every binary64 and binary32 bit.
+constexpr int SLOW_NW = 36;
+constexpr int SLOW_L = -1152;
+constexpr int FAST_NW = 6;    // 384 bits
+
+// Exact magnitude of x = sum of components, normalised so that the bit of
+// weight 2^(E_top - 1) sits at bit 383 of a 384-bit window `out`
+// (truncating whatever falls below bit 0).  Returns sign (-1, 0, +1).
+// If E_top is OZMP_EXP_ZERO-like (x == 0) the window is zero.
+// Also returns the exact exponent E(x) = floor(log2|x|) + 1 (or EXP_ZERO).
+struct Exact {
+    int sign;
+    int E;          // floor(log2|x|) + 1
+};
+
+// magnitude in an NW-word window with LSB weight 2^L; sign and E computed
+template <int NW>
+__device__ __forceinline__ Exact window_magnitude(uint64_t (&w)[NW], int L) {
+    Exact r;
+    r.sign = 0;
+    r.E = OZMP_EXP_ZERO;
+    if (mw_is_zero<NW>(w)) return r;
+    bool neg = (w[NW - 1] >> 63) != 0;
+    if (neg) mw_neg<NW>(w);
+    r.sign = neg ? -1 : 1;
+    r.E = L + mw_top<NW>(w) + 1;
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ int mant_bits();
+template <> __device__ __forceinline__ int mant_bits<double>() { return 53; }
+template <> __device__ __forceinline__ int mant_bits<float>() { return 24; }
+
+// Decode q components (q <= 4) of type T; returns false on a non-finite one.
+template <typename T>
+__device__ __forceinline__ bool decode_all(const T* v, int q, Comp* c, int& Ptop) {
+    bool ok = true;
+    Ptop = -100000;
+#pragma unroll 4
+    for (int i = 0; i < q; ++i) {
+        ok &= decode(v[i], c[i]);
+        if (c[i].M) {
+            int p = c[i].e + bitlen(c[i].M);
+            Ptop = p > Ptop ? p : Ptop;
+        }
+    }
+    return ok;
+}
+
+// Slow paths (a component has bits below the 384-bit window): exact sums
+// over the whole binary64 range in local memory; kept out of line so the
+// common path stays in registers.
+static __device__ __noinline__ Exact exact_exponent_slow(const Comp* c, int q) {
+    uint64_t W[SLOW_NW];
+    window_sum<SLOW_NW>(W, c, q, SLOW_L);
+    return window_magnitude<SLOW_NW>(W, SLOW_L);
+}
+
+static __device__ __noinline__ int aligned_slow(const Comp* c, int q, int Erow, uint64_t* out) {
+    uint64_t W[SLOW_NW];
+    window_sum<SLOW_NW>(W, c, q, SLOW_L);
+    Exact ex = window_magnitude<SLOW_NW>(W, SLOW_L);
+    if (ex.sign == 0) return 0;
+    int top = Erow - 1 - SLOW_L;         // bit index of weight 2^(Erow - 1) in W
+    int lo = top - 383;                  // bit index that becomes out bit 0
+    for (int j = 0; j < FAST_NW; ++j) {
+        int b = lo + 64 * j;
+        int li = b >> 6;                 // floor division (b may be negative)
+        int sh = b - 64 * li;
+        uint64_t a0 = (li >= 0 && li < SLOW_NW) ? W[li] : 0ull;
+        uint64_t a1 = (li + 1 >= 0 && li + 1 < SLOW_NW) ? W[li + 1] : 0ull;
+        out[j] = sh ? ((a0 >> sh) | (a1 << (64 - sh))) : a0;
+    }
+    return ex.sign;
+}
+
+// Exact exponent E(x) and sign of the sum of the decoded components.
+__device__ __forceinline__ Exact exact_exponent(const Comp* c, int q, int Ptop) {
+    Exact r;
+    r.sign = 0;
+    r.E = OZMP_EXP_ZERO;
+    if (Ptop == -100000) return r;
+    int L = Ptop + 3 - 64 * FAST_NW;
+    uint64_t w[FAST_NW];
+    bool tail = window_sum<FAST_NW>(w, c, q, L);
+    if (!tail) return window_magnitude<FAST_NW>(w, L);
+    return exact_exponent_slow(c, q);
+}
+
+// Exact |x| placed so that weight 2^(Erow - 1) is window bit 383 (bits
+// below bit 0 truncated).  Erow must satisfy |x| < 2^Erow.  Returns sign.
+__device__ __forceinline__ int aligned_magnitude(const Comp* c, int q, int Ptop, int Erow,
+                                                 uint64_t (&out)[FAST_NW]) {
+#pragma unroll
+    for (int j = 0; j < FAST_NW; ++j) out[j] = 0;
+    if (Ptop == -100000) return 0;
+    int L = Ptop + 3 - 64 * FAST_NW;
+    bool tail = window_sum<FAST_NW>(out, c, q, L);
+    if (!tail) {
+        Exact ex = window_magnitude<FAST_NW>(out, L);
+        if (ex.sign == 0) return 0;
+        int pos = Erow - 1 - L;          // window bit of weight 2^(Erow - 1)
+        int left = 383 - pos;
+        if (left >= 0) mw_shl<FAST_NW>(out, left); else mw_shr<FAST_NW>(out, -left);
+        return ex.sign;
+    }
+    uint64_t tmp[FAST_NW];
+    int sg = aligned_slow(c, q, Erow, tmp);
+#pragma unroll
+    for (int j = 0; j < FAST_NW; ++j) out[j] = tmp[j];
+    return sg;
+}
+
+// Digit t (1-based) of the aligned window: bits [384 - beta t, 384 - beta (t-1)).
+template <int BETA>
+__device__ __forceinline__ uint32_t digit_at(const uint64_t (&w)[FAST_NW], int t) {
+    int p = 384 - BETA * t;
+    int wi = p >> 6, off = p & 63;
+    uint64_t v = w[wi] >> off;
+    if (off + BETA > 64 && wi + 1 < FAST_NW) v |= w[wi + 1] << (64 - off);
+    return (uint32_t)(v & ((1ull << BETA) - 1ull));
+}
+
+// runtime beta: top beta bits of the window, then shift the window left
+__device__ __forceinline__ uint32_t take_top(uint64_t (&w)[FAST_NW], int beta) {
+    uint32_t d = (uint32_t)(w[FAST_NW - 1] >> (64 - beta));
+    mw_shl<FAST_NW>(w, beta);
+    return d;
+}
+
+// e4m3 encoding of a small integer |d| <= 15 (exact: 4-bit integers have at
+// most 4 significant bits and e4m3 stores 1 + 3 of them).
+__device__ __forceinline__ uint32_t e4m3_of_int(int d) {
+    uint32_t a = (uint32_t)(d < 0 ? -d : d);
+    if (a == 0) return 0u;
+    int e = 31 - __clz(a);                       // 0..3
+    uint32_t m = ((a << (3 - e)) & 7u);           // 3 mantissa bits below the leading one
+    uint32_t code = ((uint32_t)(e + 7) << 3) | m;
+    return code | (d < 0 ? 0x80u : 0u);
+}
+
+// ----------------------------------------------------------------------------
+// canonical rounding of an exact two's complement accumulator into q words
+// ----------------------------------------------------------------------------
+// value = acc * 2^U.  Writes c_0 = RN(value), c_t = RN(value - c_0 - ...).
+// Returns false if a non-zero component would leave the normal range.
+template <int NW, typename T>
+__device__ __forceinline__ bool canonical_round(uint64_t (&acc)[NW], int U, int q, T* out) {
+    constexpr int P = (sizeof(T) == 8) ? 53 : 24;
+    constexpr int EBIAS = (sizeof(T) == 8) ? 1023 : 127;
+    constexpr int EMAX = (sizeof(T) == 8) ? 2046 : 254;
+    bool ok = true;
+    int sgn = 1;
+    if ((acc[NW - 1] >> 63) != 0) { mw_neg<NW>(acc); sgn = -1; }
+    int scale = U;
+#pragma unroll 4
+    for (int c = 0; c < q; ++c) {
+        int top = mw_top<NW>(acc);
+        if (top < 0) { out[c] = (T)0; continue; }
+        int z = 64 * NW - 1 - top;
+        mw_shl<NW>(acc, z);
+        scale -= z;
+        uint64_t hi = acc[NW - 1];
+        uint64_t mant = hi >> (64 - P);
+        uint64_t rb = (hi >> (63 - P)) & 1ull;
+        uint64_t low = hi & ((1ull << (63 - P)) - 1ull);
+#pragma unroll
+        for (int j = 0; j < NW - 1; ++j) low |= acc[j];
+        bool up = rb && (low != 0 || (mant & 1ull));
+        // residual in the normalised frame
+        acc[NW - 1] = hi & ((1ull << (64 - P)) - 1ull);
+        if (up) {
+            mant += 1;
+            // residual := 2^(64 NW - P) - residual, and the sign flips
+            uint64_t one[NW];
+#pragma unroll
+            for (int j = 0; j < NW; ++j) one[j] = 0;
+            one[NW - 1] = 1ull << (64 - P);
+            mw_sub<NW>(one, acc);
+#pragma unroll
+            for (int j = 0; j < NW; ++j) acc[j] = one[j];
+        }
+        // component = sgn * mant * 2^(scale + 64 NW - P), mant in [2^(P-1), 2^P]
+        int ex = scale + 64 * NW - P;
+        if (mant >> P) { mant >>= 1; ex += 1; }
+        int be = ex + (P - 1) + EBIAS;             // biased exponent of 1.f x 2^(ex + P - 1)
+        if (be < 1 || be > EMAX) {
+            ok = false;
+            out[c] = (T)0;
+        } else if (sizeof(T) == 8) {
+            uint64_t bits = ((uint64_t)(sgn < 0) << 63) | ((uint64_t)be << 52) | (mant & ((1ull << 52) - 1ull));
+            double dv = __longlong_as_double((long long)bits);
+            out[c] = (T)dv;
+        } else {
+            uint32_t bits = ((uint32_t)(sgn < 0) << 31) | ((uint32_t)be << 23) | ((uint32_t)mant & 0x7fffffu);
+            float fv = __uint_as_float(bits);
+            out[c] = (T)fv;
+        }
+        if (up) sgn = -sgn;
+    }
+    return ok;
+}
+
+}  // namespace ozmp

@@ -1,0 +1,36 @@
+// Exponent reduce (K1) and the split dispatcher; kernels in split_impl.cuh.
+#include "split_impl.cuh"
+
+namespace ozmp {
+
+cudaError_t launch_digits_fp8(const SplitArgs& g, cudaStream_t st);
+cudaError_t launch_digits_int8(const SplitArgs& g, cudaStream_t st);
+cudaError_t launch_digits_fp64(const SplitArgs& g, cudaStream_t st);
+
+template <typename T>
+static cudaError_t exponents_impl(const SplitArgs& g, cudaStream_t st) {
+    Operand<T> a = make_op<T>(g.A, g.q, g.lda);
+    Operand<T> b = make_op<T>(g.B, g.q, g.ldb);
+    int64_t mx = g.mp > g.np ? g.mp : g.np;
+    if (mx == 0) mx = 1;
+    k_init_exponents<<<(unsigned)((mx + 255) / 256), 256, 0, st>>>(g.E, g.mp, g.F, g.np, g.status);
+    if (g.m > 0 && g.k > 0) {
+        int kchunk = 256;
+        dim3 gr((unsigned)((g.m + 255) / 256), (unsigned)((g.k + kchunk - 1) / kchunk));
+        k_exp_rows<T><<<gr, 256, 0, st>>>(a, g.m, g.k, kchunk, g.E, g.status);
+    }
+    if (g.n > 0 && g.k > 0) {
+        k_exp_cols<T><<<(unsigned)((g.n + 7) / 8), 256, 0, st>>>(b, g.k, g.n, g.F, g.status);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split(const SplitArgs& g, cudaStream_t st) {
+    cudaError_t e = g.is_f32 ? exponents_impl<float>(g, st) : exponents_impl<double>(g, st);
+    if (e != cudaSuccess) return e;
+    if (g.form == OZMP_FORM_FP64) return launch_digits_fp64(g, st);
+    if (g.form == OZMP_FORM_INT8) return launch_digits_int8(g, st);
+    return launch_digits_fp8(g, st);
+}
+
+}  // namespace ozmp

@@ -1,0 +1,98 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds for
+sm_103a and loads, exports every entry point declared in include/ozmp.h,
+validates arguments, and plans digit widths, slice counts and the exact
+accumulation schedule as the paper's exactness condition requires."""
+import os
+import re
+
+import pytest
+
+import paper_2301_09960_gb300 as oz
+from oracle import ozaki as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "ozmp.h")).read()
+    return sorted(set(re.findall(r"\b(ozmp_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_entry_points():
+    syms = declared_symbols()
+    for s in ["ozmp_gemm_dd", "ozmp_gemm_td", "ozmp_gemm_qd", "ozmp_gemm_ts", "ozmp_plan_create",
+              "ozmp_plan_execute", "ozmp_plan_destroy"]:
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol():
+    L = oz.load()
+    for s in declared_symbols():
+        assert hasattr(L, s), s
+    assert set(declared_symbols()) <= set(oz.SIGNATURES)
+    assert "sm_103a" in oz.ozmp_version()
+
+
+@pytest.mark.parametrize("form,beta", [("fp64", None), ("int8", 7), ("fp8", 4)])
+@pytest.mark.parametrize("k", [1, 128, 1000, 4096, 16384])
+def test_plan_digit_width_and_schedule(form, beta, k):
+    h = oz.ozmp_plan_create(oz.Prec.QD, 300, 200, k, oz.FORM_BY_NAME[form], 0, None)
+    try:
+        i = oz.ozmp_plan_get_info(h)
+        b = O.beta_fp64(k) if form == "fp64" else beta
+        assert i.beta == b
+        dmax = 15 if form == "fp8" else 2 ** b - 1
+        limit = {"fp64": 2 ** 53, "int8": 2 ** 31 - 1, "fp8": 2 ** 24}[form]
+        # pairs summed in the tensor-core accumulator stay exact
+        assert i.pairs_per_drain * k * dmax ** 2 <= limit < (i.pairs_per_drain + 1) * k * dmax ** 2
+        assert i.npairs == i.nslices * (i.nslices + 1) // 2
+        assert i.mp % 128 == 0 and i.np % 128 == 0 and i.kp % 64 == 0 and i.kp >= k
+        # slice count from the target 2^-200 with log2(k) + 16 guard bits
+        import math
+        want = math.ceil((200 + math.ceil(math.log2(k)) + 16) / b)
+        want = min(want, 36 if form == "int8" else 64)
+        while want * b > 376:
+            want -= 1
+        assert i.nslices == want
+        assert 1 <= i.ngroups <= i.nslices
+        assert i.workspace_bytes >= i.nslices * (i.mp + i.np) * i.kp * i.digit_bytes
+    finally:
+        oz.ozmp_plan_destroy(h)
+
+
+def test_plan_rejects_bad_arguments():
+    for args in [(7, 10, 10, 10, 0, 0), (2, -1, 10, 10, 0, 0), (2, 10, 10, 10, 9, 0), (2, 10, 10, 10, 0, 65)]:
+        with pytest.raises(oz.OzmpError) as e:
+            oz.ozmp_plan_create(*args, None)
+        assert e.value.status == oz.Status.ERR_INVALID_ARG
+    # binary32 accumulation of e4m3 digits is exact only up to k = 2^24 / 225
+    with pytest.raises(oz.OzmpError) as e:
+        oz.ozmp_plan_create(oz.Prec.DD, 8, 8, 80000, oz.Form.FP8, 0, None)
+    assert e.value.status == oz.Status.ERR_UNSUPPORTED
+    h = oz.ozmp_plan_create(oz.Prec.DD, 8, 8, 74565, oz.Form.FP8, 0, None)
+    oz.ozmp_plan_destroy(h)
+
+
+def test_group_schedule_keeps_horner_value_below_2_62():
+    for prec in (oz.Prec.DD, oz.Prec.QD):
+        for form in (oz.Form.FP8, oz.Form.INT8, oz.Form.FP64):
+            for k in (64, 4096, 16384):
+                h = oz.ozmp_plan_create(prec, 128, 128, k, form, 0, None)
+                i = oz.ozmp_plan_get_info(h)
+                oz.ozmp_plan_destroy(h)
+                s, b = i.nslices, i.beta
+                dmax = 15 if form == oz.Form.FP8 else 2 ** b - 1
+                tb = lambda d: (d - 1) * k * dmax ** 2
+                # re-derive the greedy grouping and check every group's bound
+                groups, cur, first, hb = 0, [], None, 0
+                for d in range(s + 1, 1, -1):
+                    if first is not None and hb + (tb(d) << (b * (first - d))) < 2 ** 62 and b * (first - d) < 62:
+                        hb += tb(d) << (b * (first - d))
+                    else:
+                        groups += 1
+                        first, hb = d, tb(d)
+                    assert hb < 2 ** 62
+                assert groups == i.ngroups
+                # the exact accumulator holds the largest possible Ozaki sum
+                total = sum(tb(d) << (b * (s + 1 - d)) for d in range(2, s + 2))
+                assert total.bit_length() + 1 <= 64 * i.acc_words

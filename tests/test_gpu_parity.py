@@ -1,0 +1,237 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+* exponents E, F and every digit: bit-exact against oracle.ozaki.split;
+* each diagonal T_d = sum_{t+u=d} A_t B_u^T from the tensor-core main loop:
+  bit-exact against the oracle's int64 slice products;
+* the product: bit-exact against the canonical component rounding of the
+  oracle's exact Ozaki sum, and within the precision's normwise target of
+  the exact product rounded to 512 bits when the slice count is automatic.
+Shapes span several 128 x 128 tiles with ragged m, n and k tails.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2301_09960_gb300 as oz
+from oracle import _clib
+from oracle import exact as X
+from oracle import ozaki as O
+from ozmp_inputs import gen_problem
+
+from _util import digits_to_int, from_dev, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TARGET = {"dd": 2.0 ** -100, "td": 2.0 ** -150, "qd": 2.0 ** -200, "ts": 2.0 ** -66}
+Q = {"dd": 2, "td": 3, "qd": 4, "ts": 3}
+
+
+def _split_check(prec, form, m, n, k, phi, seed, nslices=0):
+    A, B = gen_problem(prec, m, n, k, phi=phi, seed=seed)
+    p = oz.Plan(prec, m, n, k, form, nslices)
+    Ad, Bd = to_dev(A), to_dev(B)
+    p.split(Ad, Bd)
+    torch.cuda.synchronize()
+    i = p.info
+    E, F = [t.cpu().numpy() for t in p.exponents()]
+    ga, gb = [t.cpu().numpy() for t in p.digits()]
+    Eo, dA = O.split(A, i.beta, i.nslices)
+    Fo, dB = O.split([np.asfortranarray(b.T) for b in B], i.beta, i.nslices)
+    assert list(E) == Eo
+    assert list(F) == Fo
+    gA = digits_to_int(ga[:, :m, :k], form)
+    gB = digits_to_int(gb[:, :n, :k], form)
+    np.testing.assert_array_equal(gA, dA)
+    np.testing.assert_array_equal(gB, dB)
+    # the padded region carries zero digits
+    assert not digits_to_int(ga[:, m:, :], form).any() and not digits_to_int(ga[:, :, k:], form).any()
+    assert not digits_to_int(gb[:, n:, :], form).any() and not digits_to_int(gb[:, :, k:], form).any()
+    return p, A, B, Ad, Bd, dA, dB
+
+
+@pytest.mark.parametrize("form", ["fp8", "int8", "fp64"])
+@pytest.mark.parametrize("prec", ["dd", "td", "qd", "ts"])
+def test_split_bit_exact(prec, form):
+    _split_check(prec, form, 150, 140, 130, phi=1.0, seed=1, nslices=6 if form == "fp64" else 14)
+
+
+@pytest.mark.parametrize("form", ["fp8", "int8", "fp64"])
+def test_diagonals_bit_exact(form):
+    s = {"fp8": 20, "int8": 12, "fp64": 5}[form]
+    p, A, B, Ad, Bd, dA, dB = _split_check("dd", form, 200, 150, 130, phi=1.0, seed=2, nslices=s)
+    T = O.slice_products(dA, dB)
+    for d in sorted({2, 3, s // 2 + 1, s + 1}):
+        got = p.diagonal(d).cpu().numpy()
+        np.testing.assert_array_equal(got, T[d])
+
+
+def _product(prec, form, m, n, k, phi, seed, nslices):
+    A, B = gen_problem(prec, m, n, k, phi=phi, seed=seed)
+    C, p = oz.gemm(to_dev(A), to_dev(B), prec, form, nslices)
+    torch.cuda.synchronize()
+    assert p.status() == oz.Status.OK
+    return A, B, from_dev(C), p
+
+
+def _canonical_check(A, B, Cg, p, prec):
+    i = p.info
+    r = O.ozaki_product(A, B, i.beta, i.nslices)
+    kind = "f32" if prec == "ts" else "f64"
+    m, n = Cg[0].shape
+    for a in range(m):
+        for b in range(n):
+            want = X.to_components(r["S"][a][b], Q[prec], kind)
+            got = [float(c[a, b]) for c in Cg]
+            assert got == want, (a, b, got, want)
+    return r
+
+
+CASES = [("dd", "fp8", 130, 140, 150), ("dd", "int8", 200, 150, 130), ("dd", "fp64", 150, 130, 140),
+         ("td", "fp8", 130, 70, 100), ("td", "int8", 140, 130, 70), ("td", "fp64", 130, 140, 70),
+         ("qd", "fp8", 70, 130, 64), ("qd", "int8", 130, 70, 90), ("qd", "fp64", 140, 70, 70),
+         ("ts", "fp8", 150, 140, 130), ("ts", "int8", 140, 130, 150), ("ts", "fp64", 130, 150, 140)]
+
+
+@pytest.mark.parametrize("prec,form,m,n,k", CASES)
+def test_product_bit_exact_and_within_target(prec, form, m, n, k):
+    A, B, Cg, p = _product(prec, form, m, n, k, phi=1.0, seed=3, nslices=0)
+    _canonical_check(A, B, Cg, p, prec)
+    # error against the exact product on a sampled block
+    rows = list(range(0, m, max(1, m // 12)))[:12]
+    cols = list(range(0, n, max(1, n // 12)))[:12]
+    ex = _clib.exact_block(A, B, rows, cols)
+    chat = [[[float(c[a, b]) for c in Cg] for b in cols] for a in rows]
+    err = X.error_metrics(chat, ex)["err_nw"]
+    assert err <= TARGET[prec], err
+
+
+def test_phi4_needs_more_slices_and_fixed_s_is_exact():
+    # exponent spread phi = 4: the automatic count is not enough, a larger
+    # forced count is; both are bit-exact to the oracle's Ozaki sum
+    A, B, Cg, p = _product("dd", "fp8", 128, 130, 140, phi=4.0, seed=4, nslices=48)
+    _canonical_check(A, B, Cg, p, "dd")
+
+
+def test_edge_shapes():
+    for (m, n, k) in [(1, 1, 1), (1, 7, 3), (5, 1, 2), (129, 1, 65), (1, 129, 127)]:
+        A, B, Cg, p = _product("dd", "fp8", m, n, k, phi=1.0, seed=5, nslices=0)
+        _canonical_check(A, B, Cg, p, "dd")
+
+
+def test_k_zero_gives_zero():
+    A = [oz.colmajor(np.zeros((5, 0)))] * 2
+    B = [oz.colmajor(np.zeros((0, 4)))] * 2
+    C = [oz.colmajor(np.full((5, 4), 3.0)) for _ in range(2)]
+    p = oz.Plan("dd", 5, 4, 0, "fp8", 0)
+    p.execute(A, B, C)
+    torch.cuda.synchronize()
+    assert all(float(c.abs().max()) == 0.0 for c in C)
+
+
+def test_zero_rows_unnormalised_and_slow_path():
+    m, n, k = 6, 5, 4
+    hi = np.zeros((m, k))
+    lo = np.zeros((m, k))
+    hi[0] = [1.0, -3.0, 2.0 ** 60, 0.5]
+    lo[0] = [-(2.0 ** -400), 1.0, -(2.0 ** 60), 2.0 ** -1074]     # tails far below the window
+    hi[2] = [2.0 ** -1000, 1.0, 0.0, 0.0]
+    hi[3] = [1.0, 1.0, 1.0, 1.0]
+    lo[3] = [-1.0, 0.0, 0.0, 2.0 ** -53]                           # complete cancellation
+    # row 1 and 4, 5 are zero
+    A = [np.asfortranarray(hi), np.asfortranarray(lo)]
+    rng = np.random.default_rng(0)
+    B = [np.asfortranarray(rng.standard_normal((k, n))), np.zeros((k, n), order="F")]
+    B[0][:, 2] = 0.0
+    for form in ["fp8", "int8", "fp64"]:
+        p = oz.Plan("dd", m, n, k, form, 0)
+        Ad, Bd = to_dev(A), to_dev(B)
+        p.split(Ad, Bd)
+        torch.cuda.synchronize()
+        E, F = [t.cpu().numpy() for t in p.exponents()]
+        Eo, dA = O.split(A, p.info.beta, p.info.nslices)
+        assert list(E) == Eo and E[1] == oz.EXP_ZERO and F[2] == oz.EXP_ZERO
+        ga = p.digits()[0].cpu().numpy()
+        np.testing.assert_array_equal(digits_to_int(ga[:, :m, :k], form), dA)
+        C = [oz.colmajor(np.zeros((m, n))) for _ in range(2)]
+        p.execute(Ad, Bd, C)
+        torch.cuda.synchronize()
+        st = p.status()
+        # 2^-1000 * b underflows the output range: reported, not silently wrong
+        assert st in (oz.Status.OK, oz.Status.ERR_RANGE)
+        Cg = from_dev(C)
+        r = O.ozaki_product(A, B, p.info.beta, p.info.nslices)
+        for a in [0, 1, 3, 4, 5]:
+            for b in range(n):
+                assert [float(c[a, b]) for c in Cg] == X.to_components(r["S"][a][b], 2)
+
+
+def test_nonfinite_input_sets_status():
+    A, B = gen_problem("dd", 40, 30, 20, seed=6)
+    A[0][3, 4] = np.nan
+    B[1][2, 2] = np.inf
+    C, p = oz.gemm(to_dev(A), to_dev(B), "dd", "fp8", 0)
+    assert p.status() == oz.Status.ERR_NONFINITE
+
+
+def test_leading_dimensions_larger_than_rows():
+    A, B = gen_problem("td", 70, 60, 50, seed=7)
+    pad = lambda x, r: np.asfortranarray(np.vstack([x, np.full((r, x.shape[1]), 7.0)]))
+    Ap = [torch.as_tensor(pad(a, 9)).cuda() for a in A]
+    Bp = [torch.as_tensor(pad(b, 5)).cuda() for b in B]
+    # column-major views with ld = rows + pad
+    Av = [torch.empty((50, 79), dtype=torch.float64, device="cuda").T for _ in A]
+    Bv = [torch.empty((60, 55), dtype=torch.float64, device="cuda").T for _ in B]
+    for v, a in zip(Av, Ap):
+        v.copy_(a)
+    for v, b in zip(Bv, Bp):
+        v.copy_(b)
+    Cbig = [torch.full((60, 75), 5.0, dtype=torch.float64, device="cuda").T for _ in range(3)]
+    p = oz.Plan("td", 70, 60, 50, "int8", 0)
+    p.execute([v[:70] for v in Av], [v[:50] for v in Bv], [c[:70] for c in Cbig])
+    torch.cuda.synchronize()
+    Cg = [c[:70].cpu().numpy() for c in Cbig]
+    _canonical_check(A, B, Cg, p, "td")
+    assert all(float(c[70:].min()) == 5.0 and float(c[70:].max()) == 5.0 for c in Cbig)
+
+
+def test_plain_entry_points_match_plan():
+    for prec, fn in [("dd", oz.ozmp_gemm_dd), ("td", oz.ozmp_gemm_td), ("qd", oz.ozmp_gemm_qd),
+                     ("ts", oz.ozmp_gemm_ts)]:
+        A, B = gen_problem(prec, 90, 70, 80, seed=8)
+        Ad, Bd = to_dev(A), to_dev(B)
+        oz.ozmp_set_stream(None)
+        dt = torch.float32 if prec == "ts" else torch.float64
+        C1 = [torch.zeros((70, 90), dtype=dt, device="cuda").T for _ in range(Q[prec])]
+        fn(Ad, Bd, C1, 0)
+        assert oz.ozmp_last_status() == oz.Status.OK
+        C2, p = oz.gemm(Ad, Bd, prec, "auto", 0)
+        torch.cuda.synchronize()
+        for x, y in zip(C1, C2):
+            assert torch.equal(x, y)
+
+
+def test_bad_arguments_are_rejected():
+    A, B = gen_problem("dd", 8, 8, 8, seed=9)
+    Ad, Bd = to_dev(A), to_dev(B)
+    C = [oz.colmajor(np.zeros((8, 8))) for _ in range(2)]
+    p = oz.Plan("dd", 8, 8, 8, "fp8", 0)
+    Cs = [torch.zeros((8, 4), dtype=torch.float64, device="cuda").T for _ in range(2)]   # ld = 4 < m = 8
+    with pytest.raises(oz.OzmpError) as e:
+        oz.ozmp_plan_execute(p.h, Ad, Bd, Cs)
+    assert e.value.status == oz.Status.ERR_INVALID_ARG
+
+
+def test_nondefault_stream_and_repeat():
+    A, B = gen_problem("dd", 300, 260, 200, seed=10)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        Ad, Bd = to_dev(A), to_dev(B)
+        p = oz.Plan("dd", 300, 260, 200, "fp8", 0, stream=s)
+        C1, _ = oz.gemm(Ad, Bd, "dd", plan=p)
+        C2, _ = oz.gemm(Ad, Bd, "dd", plan=p)
+    s.synchronize()
+    for x, y in zip(C1, C2):
+        assert torch.equal(x, y)
