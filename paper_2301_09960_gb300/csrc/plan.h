@@ -1,0 +1,244 @@
+// Internal plan descriptor and its host-side scheduling helpers (not part
+// of the C ABI): digit width, slice count, drain/group schedule, workspace
+// layout and the launch descriptors built from a plan.
+#pragma once
+#include <cstdint>
+#include <cstring>
+#include "kernels.h"
+#include "ozmp_internal.cuh"
+
+struct ozmp_plan_s {
+    int prec, q, is_f32, form;
+    int64_t m, n, k, mp, np, kp;
+    int s, beta, db;
+    int ppd;
+    uint64_t group_start;
+    int ngroups, acc_words;
+    size_t ws_bytes, off_E, off_F, off_status, off_Adig, off_Bdig, off_acc;
+    void* ws;
+    bool ws_owned;
+    cudaStream_t stream;
+};
+
+namespace ozmp_plan_detail {
+using namespace ozmp;
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+inline int64_t roundup(int64_t x, int64_t r) { return (x + r - 1) / r * r; }
+
+inline int prec_q(int prec) {
+    switch (prec) {
+        case OZMP_DD: return 2;
+        case OZMP_TD: return 3;
+        case OZMP_QD: return 4;
+        case OZMP_TS: return 3;
+        default: return 0;
+    }
+}
+
+// target error bits of each precision (2^-100 DD, 2^-150 TD, 2^-200 QD, 2^-66 TS)
+inline int prec_target_bits(int prec) {
+    switch (prec) {
+        case OZMP_DD: return 100;
+        case OZMP_TD: return 150;
+        case OZMP_QD: return 200;
+        default: return 66;
+    }
+}
+
+inline int ceil_log2(int64_t x) {
+    int b = 0;
+    while (((int64_t)1 << b) < x) ++b;
+    return b;
+}
+
+// Largest beta with k (2^beta - 1)^2 <= 2^53: every partial sum of one
+// binary64 slice product is then an integer below 2^53 (Algorithm 1's
+// requirement that C_{alpha beta} = A_alpha B_beta is error-free).
+inline int beta_fp64(int64_t k) {
+    if (k <= 0) k = 1;
+    int b = 1;
+    while (true) {
+        unsigned __int128 d = ((unsigned __int128)1 << (b + 1)) - 1;
+        if ((unsigned __int128)k * d * d <= ((unsigned __int128)1 << 53)) ++b;
+        else break;
+        if (b >= 26) break;
+    }
+    return b;
+}
+
+inline int bitlen128(unsigned __int128 x) {
+    int b = 0;
+    while (x) { ++b; x >>= 1; }
+    return b;
+}
+
+inline ozmp_status fill_schedule(ozmp_plan_s* p) {
+    // largest digit magnitude and the exact-accumulation limit of the engine
+    uint64_t dmax = (p->form == OZMP_FORM_FP8) ? 15u : ((1u << p->beta) - 1u);
+    unsigned __int128 limit = (p->form == OZMP_FORM_FP8) ? ((unsigned __int128)1 << 24)
+                            : (p->form == OZMP_FORM_INT8) ? (unsigned __int128)2147483647u
+                            : ((unsigned __int128)1 << 53);
+    int64_t kk = p->k > 0 ? p->k : 1;
+    unsigned __int128 tpair = (unsigned __int128)kk * dmax * dmax;   // bound of one slice product entry
+    if (tpair > limit) return OZMP_ERR_UNSUPPORTED;
+    unsigned __int128 ppd = limit / tpair;
+    p->ppd = ppd > (unsigned __int128)(1 << 20) ? (1 << 20) : (int)ppd;
+    // diagonal groups: H = sum_{d in group} T_d 2^(beta (dfirst - d)) must stay below 2^62
+    const unsigned __int128 HLIM = (unsigned __int128)1 << 62;
+    p->group_start = 0;
+    p->ngroups = 0;
+    int dfirst = -1;
+    unsigned __int128 hb = 0;
+    for (int d = p->s + 1; d >= 2; --d) {
+        unsigned __int128 tb = (unsigned __int128)(d - 1) * tpair;
+        bool open = (dfirst < 0);
+        if (!open) {
+            int sh = p->beta * (dfirst - d);
+            if (sh >= 62 || bitlen128(tb) + sh >= 126) open = true;
+            else {
+                unsigned __int128 nb = hb + (tb << sh);
+                if (nb >= HLIM) open = true; else hb = nb;
+            }
+        }
+        if (open) {
+            if (tb >= HLIM) return OZMP_ERR_UNSUPPORTED;
+            dfirst = d;
+            hb = tb;
+            p->group_start |= (uint64_t)1 << (d - 2);
+            p->ngroups++;
+        }
+    }
+    // exact accumulator width: |S| <= sum_d Tb_d 2^(beta (s + 1 - d))
+    int maxbits = 0;
+    for (int d = 2; d <= p->s + 1; ++d) {
+        int b = bitlen128((unsigned __int128)(d - 1) * tpair) + p->beta * (p->s + 1 - d);
+        if (b > maxbits) maxbits = b;
+    }
+    int bits = maxbits + ceil_log2(p->s + 1) + 2;   // sum of s terms, sign bit
+    p->acc_words = (bits + 63) / 64;
+    if (p->acc_words < 2) p->acc_words = 2;
+    if (p->acc_words > 7) return OZMP_ERR_UNSUPPORTED;
+    return OZMP_OK;
+}
+
+inline void fill_layout(ozmp_plan_s* p) {
+    size_t off = 0;
+    p->off_E = off; off = align256(off + (size_t)p->mp * 4);
+    p->off_F = off; off = align256(off + (size_t)p->np * 4);
+    p->off_status = off; off = align256(off + 16);
+    p->off_Adig = off; off = align256(off + (size_t)p->s * p->mp * p->kp * p->db);
+    p->off_Bdig = off; off = align256(off + (size_t)p->s * p->np * p->kp * p->db);
+    p->off_acc = off;
+    if (p->ngroups > 1) off = align256(off + (size_t)p->acc_words * p->mp * p->np * 8);
+    p->ws_bytes = off;
+}
+
+inline ozmp_status ensure_ws(ozmp_plan_s* p) {
+    if (p->ws) return OZMP_OK;
+    void* ptr = nullptr;
+    if (cudaMalloc(&ptr, p->ws_bytes ? p->ws_bytes : 256) != cudaSuccess) {
+        cudaGetLastError();
+        return OZMP_ERR_NOMEM;
+    }
+    p->ws = ptr;
+    p->ws_owned = true;
+    return OZMP_OK;
+}
+
+inline bool ptrs_ok(const void* const* v, int q) {
+    if (!v) return false;
+    for (int i = 0; i < q; ++i)
+        if (!v[i]) return false;
+    return true;
+}
+
+inline ozmp_status check_ld(const ozmp_plan_s* p, int64_t lda, int64_t ldb, int64_t ldc, bool need_c) {
+    int64_t m1 = p->m > 1 ? p->m : 1, k1 = p->k > 1 ? p->k : 1;
+    if (lda < m1 || ldb < k1) return OZMP_ERR_INVALID_ARG;
+    if (need_c && ldc < m1) return OZMP_ERR_INVALID_ARG;
+    return OZMP_OK;
+}
+
+inline SplitArgs split_args(ozmp_plan_s* p, const void* const* A, int64_t lda, const void* const* B, int64_t ldb) {
+    SplitArgs a;
+    a.form = p->form;
+    a.q = p->q;
+    a.is_f32 = p->is_f32 != 0;
+    a.m = p->m; a.n = p->n; a.k = p->k;
+    a.mp = p->mp; a.np = p->np; a.kp = p->kp;
+    a.A = A; a.lda = lda; a.B = B; a.ldb = ldb;
+    char* w = (char*)p->ws;
+    a.E = (int32_t*)(w + p->off_E);
+    a.F = (int32_t*)(w + p->off_F);
+    a.status = (uint32_t*)(w + p->off_status);
+    a.Adig = w + p->off_Adig;
+    a.Bdig = w + p->off_Bdig;
+    a.s = p->s;
+    a.beta = p->beta;
+    return a;
+}
+
+inline GemmArgs gemm_args(ozmp_plan_s* p) {
+    GemmArgs g;
+    memset(&g, 0, sizeof(g));
+    char* w = (char*)p->ws;
+    g.form = p->form; g.q = p->q; g.is_f32 = p->is_f32;
+    g.m = p->m; g.n = p->n; g.k = p->k; g.mp = p->mp; g.np = p->np; g.kp = p->kp;
+    g.E = (const int32_t*)(w + p->off_E);
+    g.F = (const int32_t*)(w + p->off_F);
+    g.Adig = w + p->off_Adig;
+    g.Bdig = w + p->off_Bdig;
+    g.s = p->s; g.beta = p->beta; g.ppd = p->ppd; g.group_start = p->group_start;
+    g.acc_words = p->acc_words; g.ngroups = p->ngroups;
+    g.acc = p->ngroups > 1 ? (int64_t*)(w + p->off_acc) : nullptr;
+    g.status = (uint32_t*)(w + p->off_status);
+    return g;
+}
+
+inline ozmp_status zero_c(ozmp_plan_s* p, void* const* C, int64_t ldc) {
+    size_t wb = p->is_f32 ? 4 : 8;
+    for (int c = 0; c < p->q; ++c)
+        if (cudaMemset2DAsync(C[c], (size_t)ldc * wb, 0, (size_t)p->m * wb, (size_t)p->n, p->stream) != cudaSuccess)
+            return OZMP_ERR_CUDA;
+    if (cudaMemsetAsync((char*)p->ws + p->off_status, 0, 16, p->stream) != cudaSuccess) return OZMP_ERR_CUDA;
+    return OZMP_OK;
+}
+
+// Fill a plan descriptor: argument checks, digit width, slice count
+// (automatic: target bits + log2 k + 16 guard bits), padded sizes, the
+// drain/group schedule and the workspace layout.  No memory is allocated.
+inline ozmp_status plan_init(ozmp_plan_s* p, int prec, int64_t m, int64_t n, int64_t k, int form, int nslices,
+                             ozmp_stream stream) {
+    int q = prec_q(prec);
+    if (!q || m < 0 || n < 0 || k < 0 || nslices < 0 || nslices > OZMP_MAX_SLICES) return OZMP_ERR_INVALID_ARG;
+    if (form < OZMP_FORM_AUTO || form > OZMP_FORM_FP8) return OZMP_ERR_INVALID_ARG;
+    memset(p, 0, sizeof(*p));
+    p->prec = prec;
+    p->q = q;
+    p->is_f32 = (prec == OZMP_TS);
+    p->form = (form == OZMP_FORM_AUTO) ? OZMP_FORM_FP8 : form;
+    p->m = m; p->n = n; p->k = k;
+    p->beta = (p->form == OZMP_FORM_FP64) ? beta_fp64(k) : (p->form == OZMP_FORM_INT8 ? 7 : 4);
+    p->db = (p->form == OZMP_FORM_FP64) ? 8 : 1;
+    int maxs = (p->form == OZMP_FORM_INT8) ? 36 : 64;
+    if (nslices == 0) {
+        int bits = prec_target_bits(prec) + ceil_log2(k > 0 ? k : 1) + 16;
+        nslices = (bits + p->beta - 1) / p->beta;
+        if (nslices > maxs) nslices = maxs;
+        while (nslices > 1 && nslices * p->beta > 376) --nslices;
+    }
+    if (nslices > maxs || nslices * p->beta > 376) return OZMP_ERR_UNSUPPORTED;
+    p->s = nslices;
+    p->mp = roundup(m, 128);
+    p->np = roundup(n, 128);
+    p->kp = roundup(k, 64);
+    ozmp_status st = fill_schedule(p);
+    if (st != OZMP_OK) return st;
+    fill_layout(p);
+    p->stream = (cudaStream_t)stream;
+    return OZMP_OK;
+}
+
+}  // namespace ozmp_plan_detail
+
