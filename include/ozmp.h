@@ -155,6 +155,29 @@ ozmp_status ozmp_gemm_ts(int64_t m, int64_t n, int64_t k, const float* const A[3
                          const float* const B[3], int64_t ldb, float* const C[3], int64_t ldc,
                          int nslices);
 
+/*
+ * ozmp_gemm_dd_noalloc -- the double-double product (as ozmp_gemm_dd, form
+ * AUTO) without any memory allocation, on `stream`.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code running while its stream is captured into a CUDA graph,
+ * programs whose device memory all belongs to a pool or caching allocator,
+ * latency-critical serving loops.
+ * Scratch: a file-scope device array of OZMP_NOALLOC_SCRATCH_BYTES (64 MiB)
+ * inside the library, held by every GPU that loads the library until the
+ * process exits.  The first call on a device looks up its address; make that
+ * first call before any stream capture.
+ * Limit: problems whose workspace (workspace_bytes of a DD, FORM_AUTO plan of
+ * the same m, n, k, nslices) exceeds the scratch are rejected with
+ * OZMP_ERR_UNSUPPORTED: m = n = k = 512 fits, 1024^3 does not.
+ * All calls share the scratch and it keeps the last call's contents: calls
+ * whose work overlaps on the GPU race and must be serialised by the caller.
+ * The device status word is not reported; C is unspecified for NaN/Inf input.
+ */
+#define OZMP_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+ozmp_status ozmp_gemm_dd_noalloc(int64_t m, int64_t n, int64_t k, const double* const A[2], int64_t lda,
+                                 const double* const B[2], int64_t ldb, double* const C[2], int64_t ldc,
+                                 int nslices, ozmp_stream stream);
+
 /* Stream and digit form used by the plain entry points of this thread. */
 ozmp_status ozmp_set_stream(ozmp_stream stream);
 ozmp_status ozmp_set_form(ozmp_form form);

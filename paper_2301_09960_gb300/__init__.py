@@ -24,7 +24,7 @@ __all__ = [
     "Status", "Prec", "Form", "OzmpError", "PlanInfo", "Plan", "load", "colmajor",
     "ozmp_plan_create", "ozmp_plan_destroy", "ozmp_plan_get_info", "ozmp_plan_set_workspace",
     "ozmp_plan_set_stream", "ozmp_plan_execute", "ozmp_plan_get_status", "ozmp_plan_split",
-    "ozmp_plan_diagonal", "ozmp_plan_multiply", "ozmp_gemm_dd", "ozmp_gemm_td", "ozmp_gemm_qd", "ozmp_gemm_ts",
+    "ozmp_plan_diagonal", "ozmp_plan_multiply", "ozmp_gemm_dd", "ozmp_gemm_td", "ozmp_gemm_qd", "ozmp_gemm_ts", "ozmp_gemm_dd_noalloc",
     "ozmp_set_stream", "ozmp_set_form", "ozmp_last_status", "ozmp_version", "gemm", "EXP_ZERO",
 ]
 
@@ -107,6 +107,7 @@ SIGNATURES = {
     "ozmp_gemm_td": [_I64, _I64, _I64, _PP, _I64, _PP, _I64, _PP, _I64, ctypes.c_int],
     "ozmp_gemm_qd": [_I64, _I64, _I64, _PP, _I64, _PP, _I64, _PP, _I64, ctypes.c_int],
     "ozmp_gemm_ts": [_I64, _I64, _I64, _PP, _I64, _PP, _I64, _PP, _I64, ctypes.c_int],
+    "ozmp_gemm_dd_noalloc": [_I64, _I64, _I64, _PP, _I64, _PP, _I64, _PP, _I64, ctypes.c_int, _VP],
     "ozmp_set_stream": [_VP],
     "ozmp_set_form": [ctypes.c_int],
     "ozmp_last_status": [ctypes.POINTER(ctypes.c_int)],
@@ -257,6 +258,19 @@ def ozmp_gemm_qd(A, B, C, nslices=0):
 
 def ozmp_gemm_ts(A, B, C, nslices=0):
     _plain("ozmp_gemm_ts", A, B, C, nslices)
+
+
+def ozmp_gemm_dd_noalloc(A, B, C, nslices=0, stream=None):
+    """Double-double product that allocates nothing (a fixed 64 MiB scratch
+    inside the library); for callers that cannot call cudaMalloc."""
+    m, k = A[0].shape
+    n = B[0].shape[1]
+    pa, ka = _ptrs(A)
+    pb, kb = _ptrs(B)
+    pc, kc = _ptrs(C)
+    st = load().ozmp_gemm_dd_noalloc(m, n, k, pa, _ld(A[0]), pb, _ld(B[0]), pc, _ld(C[0]), nslices,
+                                     _stream_handle(stream))
+    _check(st, "ozmp_gemm_dd_noalloc")
 
 
 def ozmp_set_stream(stream=None):
