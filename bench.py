@@ -303,7 +303,7 @@ def main():
     peak_fp8 = bf16 * 2.0        # e4m3 dense / bf16 dense nominal ratio (4.5 / 2.25)
     alg_flops = info.npairs * flops
     achieved = alg_flops / (gemm_ms * 1e-3) / 1e12
-    if info.form == oz.Form.FP8:
+    if info.form in (oz.Form.FP8, oz.Form.FP8_MMA):
         peak, peak_note = peak_fp8, f"e4m3 dense = bf16 {src} x 2 (nominal ratio)"
     elif info.form == oz.Form.INT8:
         peak, peak_note = 151.3, "IMMA mma.sync s8 microbenchmark on this GB300 (no MEASURED_PEAKS entry)"
@@ -314,7 +314,7 @@ def main():
     line = {
         "metric": metric, "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "e4m3 digits / f32 acc" if info.form == oz.Form.FP8 else
+        "vs_baseline": None, "dtype": "e4m3 digits / f32 acc" if info.form in (oz.Form.FP8, oz.Form.FP8_MMA) else
         ("s8 digits / s32 acc" if info.form == oz.Form.INT8 else "f64 digits / f64 acc"),
         "data": "synthetic (Eq. 1, seeded)",
         "config": {"workload": workload, "prec": prec, "form": oz.Form(info.form).name.lower(), "m": m, "n": n,
@@ -322,7 +322,8 @@ def main():
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 gpu",
                    "l2": "inputs larger than L2 (A, B and the digit workspace each exceed 129 MB)"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_gemm_b1/k_gemm_f64 (slice products)",
+                     "frac": achieved / peak, "traffic": None, "kernel": {oz.Form.FP8: "k_gemm_tc (tcgen05)", oz.Form.FP8_MMA: "k_gemm_b1<FP8> (mma.sync)",
+                                oz.Form.INT8: "k_gemm_b1<INT8> (mma.sync)"}.get(oz.Form(info.form), "k_gemm_f64 (DMMA)"),
                      "peak_source": peak_note},
         "splitter": {"ms": split_ms, "bytes": sbytes, "achieved_gbs": sbytes / (split_ms * 1e-3) / 1e9,
                      "peak_gbs": hbm, "frac": sbytes / (split_ms * 1e-3) / 1e9 / hbm},
@@ -359,7 +360,8 @@ def main():
         del Ad, Bd, C, Ad2, Bd2, Cd2
         torch.cuda.empty_cache()
         var = []
-        for vp, vf in [("dd", "int8"), ("dd", "fp64"), ("qd", "fp8"), ("qd", "int8"), ("qd", "fp64")]:
+        for vp, vf in [("dd", "fp8mma"), ("dd", "int8"), ("dd", "fp64"), ("qd", "fp8"), ("qd", "fp8mma"),
+                       ("qd", "int8"), ("qd", "fp64")]:
             try:
                 var.append(run_variant(oz, torch, vp, vf, args.n, args.phi, 1, 1))
             except Exception as ex:  # report, do not hide

@@ -65,10 +65,11 @@ typedef enum { OZMP_DD = 2, OZMP_TD = 3, OZMP_QD = 4, OZMP_TS = 103 } ozmp_prec;
 
 /* digit form of the slice products */
 typedef enum {
-    OZMP_FORM_AUTO = 0,  /* fastest exact form on this GPU (FP8 digits) */
-    OZMP_FORM_FP64 = 1,  /* binary64 digits, beta = max{b: k (2^b - 1)^2 <= 2^53}, DMMA */
-    OZMP_FORM_INT8 = 2,  /* int8 digits, beta = 7, IMMA int32 accumulation */
-    OZMP_FORM_FP8  = 3   /* e4m3 digits, beta = 4, QMMA binary32 accumulation */
+    OZMP_FORM_AUTO = 0,     /* fastest exact form on this GPU (FP8 digits on tcgen05) */
+    OZMP_FORM_FP64 = 1,     /* binary64 digits, beta = max{b: k (2^b - 1)^2 <= 2^53}, DMMA */
+    OZMP_FORM_INT8 = 2,     /* int8 digits, beta = 7, IMMA int32 accumulation */
+    OZMP_FORM_FP8  = 3,     /* e4m3 digits, beta = 4, tcgen05 kind::f8f6f4, binary32 accumulation in TMEM */
+    OZMP_FORM_FP8_MMA = 4   /* the same e4m3 digits on the legacy mma.sync QMMA path */
 } ozmp_form;
 
 /* all-zero row/column exponent */

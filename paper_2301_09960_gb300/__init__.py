@@ -54,10 +54,12 @@ class Form(IntEnum):
     FP64 = 1
     INT8 = 2
     FP8 = 3
+    FP8_MMA = 4
 
 
 PREC_BY_NAME = {"dd": Prec.DD, "td": Prec.TD, "qd": Prec.QD, "ts": Prec.TS}
-FORM_BY_NAME = {"auto": Form.AUTO, "fp64": Form.FP64, "int8": Form.INT8, "fp8": Form.FP8}
+FORM_BY_NAME = {"auto": Form.AUTO, "fp64": Form.FP64, "int8": Form.INT8, "fp8": Form.FP8,
+                "fp8mma": Form.FP8_MMA}
 NCOMP = {Prec.DD: 2, Prec.TD: 3, Prec.QD: 4, Prec.TS: 3}
 
 

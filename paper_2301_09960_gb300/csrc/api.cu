@@ -151,7 +151,7 @@ ozmp_status ozmp_set_stream(ozmp_stream stream) {
 }
 
 ozmp_status ozmp_set_form(ozmp_form form) {
-    if (form < OZMP_FORM_AUTO || form > OZMP_FORM_FP8) return OZMP_ERR_INVALID_ARG;
+    if (form < OZMP_FORM_AUTO || form > OZMP_FORM_FP8_MMA) return OZMP_ERR_INVALID_ARG;
     tl_form = form;
     return OZMP_OK;
 }

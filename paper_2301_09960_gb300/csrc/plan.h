@@ -14,6 +14,7 @@ struct ozmp_plan_s {
     int ppd;
     uint64_t group_start;
     int ngroups, acc_words;
+    int nlimbs;   // carry-save limbs of the tcgen05 epilogue (FORM_FP8)
     size_t ws_bytes, off_E, off_F, off_status, off_Adig, off_Bdig, off_acc;
     void* ws;
     bool ws_owned;
@@ -75,8 +76,9 @@ inline int bitlen128(unsigned __int128 x) {
 
 inline ozmp_status fill_schedule(ozmp_plan_s* p) {
     // largest digit magnitude and the exact-accumulation limit of the engine
-    uint64_t dmax = (p->form == OZMP_FORM_FP8) ? 15u : ((1u << p->beta) - 1u);
-    unsigned __int128 limit = (p->form == OZMP_FORM_FP8) ? ((unsigned __int128)1 << 24)
+    const bool e4m3 = (p->form == OZMP_FORM_FP8 || p->form == OZMP_FORM_FP8_MMA);
+    uint64_t dmax = e4m3 ? 15u : ((1u << p->beta) - 1u);
+    unsigned __int128 limit = e4m3 ? ((unsigned __int128)1 << 24)
                             : (p->form == OZMP_FORM_INT8) ? (unsigned __int128)2147483647u
                             : ((unsigned __int128)1 << 53);
     int64_t kk = p->k > 0 ? p->k : 1;
@@ -119,6 +121,7 @@ inline ozmp_status fill_schedule(ozmp_plan_s* p) {
     p->acc_words = (bits + 63) / 64;
     if (p->acc_words < 2) p->acc_words = 2;
     if (p->acc_words > 7) return OZMP_ERR_UNSUPPORTED;
+    p->nlimbs = 4 * p->acc_words + 1;
     return OZMP_OK;
 }
 
@@ -130,7 +133,8 @@ inline void fill_layout(ozmp_plan_s* p) {
     p->off_Adig = off; off = align256(off + (size_t)p->s * p->mp * p->kp * p->db);
     p->off_Bdig = off; off = align256(off + (size_t)p->s * p->np * p->kp * p->db);
     p->off_acc = off;
-    if (p->ngroups > 1) off = align256(off + (size_t)p->acc_words * p->mp * p->np * 8);
+    if (p->form == OZMP_FORM_FP8) off = align256(off + (size_t)p->nlimbs * p->mp * p->np * 8);
+    else if (p->ngroups > 1) off = align256(off + (size_t)p->acc_words * p->mp * p->np * 8);
     p->ws_bytes = off;
 }
 
@@ -191,7 +195,7 @@ inline GemmArgs gemm_args(ozmp_plan_s* p) {
     g.Bdig = w + p->off_Bdig;
     g.s = p->s; g.beta = p->beta; g.ppd = p->ppd; g.group_start = p->group_start;
     g.acc_words = p->acc_words; g.ngroups = p->ngroups;
-    g.acc = p->ngroups > 1 ? (int64_t*)(w + p->off_acc) : nullptr;
+    g.acc = (p->ngroups > 1 || p->form == OZMP_FORM_FP8) ? (int64_t*)(w + p->off_acc) : nullptr;
     g.status = (uint32_t*)(w + p->off_status);
     return g;
 }
@@ -212,7 +216,7 @@ inline ozmp_status plan_init(ozmp_plan_s* p, int prec, int64_t m, int64_t n, int
                              ozmp_stream stream) {
     int q = prec_q(prec);
     if (!q || m < 0 || n < 0 || k < 0 || nslices < 0 || nslices > OZMP_MAX_SLICES) return OZMP_ERR_INVALID_ARG;
-    if (form < OZMP_FORM_AUTO || form > OZMP_FORM_FP8) return OZMP_ERR_INVALID_ARG;
+    if (form < OZMP_FORM_AUTO || form > OZMP_FORM_FP8_MMA) return OZMP_ERR_INVALID_ARG;
     memset(p, 0, sizeof(*p));
     p->prec = prec;
     p->q = q;
@@ -231,8 +235,8 @@ inline ozmp_status plan_init(ozmp_plan_s* p, int prec, int64_t m, int64_t n, int
     if (nslices > maxs || nslices * p->beta > 376) return OZMP_ERR_UNSUPPORTED;
     p->s = nslices;
     p->mp = roundup(m, 128);
-    p->np = roundup(n, 128);
-    p->kp = roundup(k, 64);
+    p->np = roundup(n, p->form == OZMP_FORM_FP8 ? 256 : 128);
+    p->kp = roundup(k, 128);
     ozmp_status st = fill_schedule(p);
     if (st != OZMP_OK) return st;
     fill_layout(p);

@@ -30,7 +30,7 @@ cudaError_t launch_split(const SplitArgs& g, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     if (g.form == OZMP_FORM_FP64) return launch_digits_fp64(g, st);
     if (g.form == OZMP_FORM_INT8) return launch_digits_int8(g, st);
-    return launch_digits_fp8(g, st);
+    return launch_digits_fp8(g, st);   // FORM_FP8 and FORM_FP8_MMA share the e4m3 digits
 }
 
 }  // namespace ozmp

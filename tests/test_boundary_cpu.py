@@ -33,7 +33,7 @@ def test_library_exports_every_declared_symbol():
     assert "sm_103a" in oz.ozmp_version()
 
 
-@pytest.mark.parametrize("form,beta", [("fp64", None), ("int8", 7), ("fp8", 4)])
+@pytest.mark.parametrize("form,beta", [("fp64", None), ("int8", 7), ("fp8", 4), ("fp8mma", 4)])
 @pytest.mark.parametrize("k", [1, 128, 1000, 4096, 16384])
 def test_plan_digit_width_and_schedule(form, beta, k):
     h = oz.ozmp_plan_create(oz.Prec.QD, 300, 200, k, oz.FORM_BY_NAME[form], 0, None)
@@ -41,12 +41,12 @@ def test_plan_digit_width_and_schedule(form, beta, k):
         i = oz.ozmp_plan_get_info(h)
         b = O.beta_fp64(k) if form == "fp64" else beta
         assert i.beta == b
-        dmax = 15 if form == "fp8" else 2 ** b - 1
-        limit = {"fp64": 2 ** 53, "int8": 2 ** 31 - 1, "fp8": 2 ** 24}[form]
+        dmax = 15 if form.startswith("fp8") else 2 ** b - 1
+        limit = {"fp64": 2 ** 53, "int8": 2 ** 31 - 1, "fp8": 2 ** 24, "fp8mma": 2 ** 24}[form]
         # pairs summed in the tensor-core accumulator stay exact
         assert i.pairs_per_drain * k * dmax ** 2 <= limit < (i.pairs_per_drain + 1) * k * dmax ** 2
         assert i.npairs == i.nslices * (i.nslices + 1) // 2
-        assert i.mp % 128 == 0 and i.np % 128 == 0 and i.kp % 64 == 0 and i.kp >= k
+        assert i.mp % 128 == 0 and i.np % (256 if form == "fp8" else 128) == 0 and i.kp % 128 == 0 and i.kp >= k
         # slice count from the target 2^-200 with log2(k) + 16 guard bits
         import math
         want = math.ceil((200 + math.ceil(math.log2(k)) + 16) / b)

@@ -58,9 +58,9 @@ def test_split_bit_exact(prec, form):
     _split_check(prec, form, 150, 140, 130, phi=1.0, seed=1, nslices=6 if form == "fp64" else 14)
 
 
-@pytest.mark.parametrize("form", ["fp8", "int8", "fp64"])
+@pytest.mark.parametrize("form", ["fp8", "fp8mma", "int8", "fp64"])
 def test_diagonals_bit_exact(form):
-    s = {"fp8": 20, "int8": 12, "fp64": 5}[form]
+    s = {"fp8": 20, "fp8mma": 20, "int8": 12, "fp64": 5}[form]
     p, A, B, Ad, Bd, dA, dB = _split_check("dd", form, 200, 150, 130, phi=1.0, seed=2, nslices=s)
     T = O.slice_products(dA, dB)
     for d in sorted({2, 3, s // 2 + 1, s + 1}):
@@ -89,7 +89,8 @@ def _canonical_check(A, B, Cg, p, prec):
     return r
 
 
-CASES = [("dd", "fp8", 130, 140, 150), ("dd", "int8", 200, 150, 130), ("dd", "fp64", 150, 130, 140),
+CASES = [("dd", "fp8", 130, 140, 150), ("dd", "fp8mma", 140, 130, 150), ("dd", "int8", 200, 150, 130),
+         ("dd", "fp64", 150, 130, 140), ("dd", "fp8", 300, 520, 260), ("ts", "fp8mma", 130, 120, 100),
          ("td", "fp8", 130, 70, 100), ("td", "int8", 140, 130, 70), ("td", "fp64", 130, 140, 70),
          ("qd", "fp8", 70, 130, 64), ("qd", "int8", 130, 70, 90), ("qd", "fp64", 140, 70, 70),
          ("ts", "fp8", 150, 140, 130), ("ts", "int8", 140, 130, 150), ("ts", "fp64", 130, 150, 140)]
