@@ -60,41 +60,28 @@ __device__ __forceinline__ int bitlen(uint64_t x) { return 64 - __clzll((long lo
 // ----------------------------------------------------------------------------
 template <int NW>
 __device__ __forceinline__ void mw_add(uint64_t (&w)[NW], const uint64_t (&p)[NW]) {
-    uint64_t c = 0;
+    asm("add.cc.u64 %0, %0, %1;" : "+l"(w[0]) : "l"(p[0]));
 #pragma unroll
-    for (int j = 0; j < NW; ++j) {
-        uint64_t s = w[j] + p[j];
-        uint64_t c1 = (s < w[j]);
-        uint64_t s2 = s + c;
-        uint64_t c2 = (s2 < s);
-        w[j] = s2;
-        c = c1 | c2;
-    }
+    for (int j = 1; j < NW - 1; ++j) asm("addc.cc.u64 %0, %0, %1;" : "+l"(w[j]) : "l"(p[j]));
+    asm("addc.u64 %0, %0, %1;" : "+l"(w[NW - 1]) : "l"(p[NW - 1]));
 }
 
 template <int NW>
 __device__ __forceinline__ void mw_sub(uint64_t (&w)[NW], const uint64_t (&p)[NW]) {
-    uint64_t b = 0;
+    asm("sub.cc.u64 %0, %0, %1;" : "+l"(w[0]) : "l"(p[0]));
 #pragma unroll
-    for (int j = 0; j < NW; ++j) {
-        uint64_t d = w[j] - p[j];
-        uint64_t b1 = (w[j] < p[j]);
-        uint64_t d2 = d - b;
-        uint64_t b2 = (d < b);
-        w[j] = d2;
-        b = b1 | b2;
-    }
+    for (int j = 1; j < NW - 1; ++j) asm("subc.cc.u64 %0, %0, %1;" : "+l"(w[j]) : "l"(p[j]));
+    asm("subc.u64 %0, %0, %1;" : "+l"(w[NW - 1]) : "l"(p[NW - 1]));
 }
 
 template <int NW>
 __device__ __forceinline__ void mw_neg(uint64_t (&w)[NW]) {
-    uint64_t c = 1;
+    uint64_t z[NW];
 #pragma unroll
-    for (int j = 0; j < NW; ++j) {
-        uint64_t x = ~w[j] + c;
-        c = (c && x == 0) ? 1ull : 0ull;
-        w[j] = x;
-    }
+    for (int j = 0; j < NW; ++j) z[j] = 0;
+    mw_sub<NW>(z, w);
+#pragma unroll
+    for (int j = 0; j < NW; ++j) w[j] = z[j];
 }
 
 template <int NW>
@@ -177,13 +164,13 @@ __device__ __forceinline__ void mw_shr(uint64_t (&w)[NW], int n) {
 // into the two's complement window w.  Returns true if some component has a
 // non-zero bit below the window (then w is not the exact sum).
 template <int NW>
-__device__ __forceinline__ bool window_sum(uint64_t (&w)[NW], const Comp* c, int q, int L) {
+__device__ __forceinline__ bool window_sum(uint64_t (&w)[NW], const Comp (&c)[4], int q, int L) {
     bool tail = false;
 #pragma unroll
     for (int j = 0; j < NW; ++j) w[j] = 0;
-#pragma unroll 4
-    for (int i = 0; i < q; ++i) {
-        if (c[i].M == 0) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (i >= q || c[i].M == 0) continue;
         int sh = c[i].e - L;
         if (sh < 0) {
             int r = -sh;
@@ -233,11 +220,13 @@ template <> __device__ __forceinline__ int mant_bits<float>() { return 24; }
 
 // Decode q components (q <= 4) of type T; returns false on a non-finite one.
 template <typename T>
-__device__ __forceinline__ bool decode_all(const T* v, int q, Comp* c, int& Ptop) {
+__device__ __forceinline__ bool decode_all(const T (&v)[4], int q, Comp (&c)[4], int& Ptop) {
     bool ok = true;
     Ptop = -100000;
-#pragma unroll 4
-    for (int i = 0; i < q; ++i) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        c[i].M = 0; c[i].e = 0; c[i].neg = 0;
+        if (i >= q) continue;
         ok &= decode(v[i], c[i]);
         if (c[i].M) {
             int p = c[i].e + bitlen(c[i].M);
@@ -247,35 +236,107 @@ __device__ __forceinline__ bool decode_all(const T* v, int q, Comp* c, int& Ptop
     return ok;
 }
 
-// Slow paths (a component has bits below the 384-bit window): exact sums
-// over the whole binary64 range in local memory; kept out of line so the
-// common path stays in registers.
-static __device__ __noinline__ Exact exact_exponent_slow(const Comp* c, int q) {
-    uint64_t W[SLOW_NW];
-    window_sum<SLOW_NW>(W, c, q, SLOW_L);
-    return window_magnitude<SLOW_NW>(W, SLOW_L);
-}
-
-static __device__ __noinline__ int aligned_slow(const Comp* c, int q, int Erow, uint64_t* out) {
-    uint64_t W[SLOW_NW];
-    window_sum<SLOW_NW>(W, c, q, SLOW_L);
-    Exact ex = window_magnitude<SLOW_NW>(W, SLOW_L);
-    if (ex.sign == 0) return 0;
-    int top = Erow - 1 - SLOW_L;         // bit index of weight 2^(Erow - 1) in W
-    int lo = top - 383;                  // bit index that becomes out bit 0
-    for (int j = 0; j < FAST_NW; ++j) {
-        int b = lo + 64 * j;
-        int li = b >> 6;                 // floor division (b may be negative)
-        int sh = b - 64 * li;
-        uint64_t a0 = (li >= 0 && li < SLOW_NW) ? W[li] : 0ull;
-        uint64_t a1 = (li + 1 >= 0 && li + 1 < SLOW_NW) ? W[li + 1] : 0ull;
-        out[j] = sh ? ((a0 >> sh) | (a1 << (64 - sh))) : a0;
+// Slow paths (a component has bits below the fast window): exact sums over
+// the whole binary64 range in a local-memory array, with rolled loops so
+// their register footprint stays small.  They take the component values
+// (binary32 ones widened exactly) so the common path never takes the address
+// of its register-resident component array.
+static __device__ __noinline__ int slow_sum(double v0, double v1, double v2, double v3, int q, uint64_t* W) {
+    const double v[4] = {v0, v1, v2, v3};
+#pragma unroll 1
+    for (int j = 0; j < SLOW_NW; ++j) W[j] = 0;
+#pragma unroll 1
+    for (int i = 0; i < q; ++i) {
+        Comp c;
+        decode(v[i], c);
+        if (c.M == 0) continue;
+        const int sh = c.e - SLOW_L;          // >= 0 for every finite double
+        const int wi = sh >> 6, b = sh & 63;
+        const uint64_t lo = c.M << b, hi = b ? (c.M >> (64 - b)) : 0ull;
+        uint64_t carry = 0;
+#pragma unroll 1
+        for (int j = wi; j < SLOW_NW; ++j) {
+            const uint64_t a = (j == wi) ? lo : ((j == wi + 1) ? hi : 0ull);
+            if (!c.neg) {
+                const uint64_t t = W[j] + a;
+                const uint64_t c1 = t < a;
+                const uint64_t t2 = t + carry;
+                carry = c1 | (t2 < t);
+                W[j] = t2;
+            } else {
+                const uint64_t t = W[j] - a;
+                const uint64_t b1 = W[j] < a;
+                const uint64_t t2 = t - carry;
+                carry = b1 | (t < carry);
+                W[j] = t2;
+            }
+            if (j > wi + 1 && carry == 0) break;
+        }
     }
-    return ex.sign;
+    // magnitude and sign
+    int sign = 0;
+#pragma unroll 1
+    for (int j = 0; j < SLOW_NW; ++j) if (W[j]) sign = 1;
+    if (!sign) return 0;
+    if (W[SLOW_NW - 1] >> 63) {
+        uint64_t c = 1;
+#pragma unroll 1
+        for (int j = 0; j < SLOW_NW; ++j) {
+            const uint64_t x = ~W[j] + c;
+            c = (c && x == 0) ? 1ull : 0ull;
+            W[j] = x;
+        }
+        return -1;
+    }
+    return 1;
 }
 
-// Exact exponent E(x) and sign of the sum of the decoded components.
-__device__ __forceinline__ Exact exact_exponent(const Comp* c, int q, int Ptop) {
+static __device__ __noinline__ Exact exact_exponent_slow(double v0, double v1, double v2, double v3, int q) {
+    uint64_t W[SLOW_NW];
+    Exact r;
+    r.sign = slow_sum(v0, v1, v2, v3, q, W);
+    r.E = OZMP_EXP_ZERO;
+    if (r.sign) {
+        int top = -1;
+#pragma unroll 1
+        for (int j = SLOW_NW - 1; j >= 0 && top < 0; --j)
+            if (W[j]) top = 64 * j + 63 - __clzll((long long)W[j]);
+        r.E = SLOW_L + top + 1;
+    }
+    return r;
+}
+
+// NW words of |x| with the bit of weight 2^(Erow - 1) at bit `toppos`
+static __device__ __noinline__ int slow_window(double v0, double v1, double v2, double v3, int q, int Erow, int nw,
+                                               int toppos, uint64_t* out) {
+    uint64_t W[SLOW_NW];
+    const int sign = slow_sum(v0, v1, v2, v3, q, W);
+    const int lo = (Erow - 1 - SLOW_L) - toppos;   // bit of W that becomes bit 0
+#pragma unroll 1
+    for (int j = 0; j < nw; ++j) {
+        const int b = lo + 64 * j;
+        const int li = b >> 6;
+        const int sh = b - 64 * li;
+        const uint64_t a0 = (li >= 0 && li < SLOW_NW) ? W[li] : 0ull;
+        const uint64_t a1 = (li + 1 >= 0 && li + 1 < SLOW_NW) ? W[li + 1] : 0ull;
+        out[j] = sign ? (sh ? ((a0 >> sh) | (a1 << (64 - sh))) : a0) : 0ull;
+    }
+    return sign;
+}
+
+static __device__ __noinline__ int aligned_slow(double v0, double v1, double v2, double v3, int q, int Erow,
+                                                uint64_t* out) {
+    return slow_window(v0, v1, v2, v3, q, Erow, FAST_NW, 383, out);
+}
+
+// the component values, widened to binary64 (exact)
+template <typename T>
+__device__ __forceinline__ double comp_value(const T (&v)[4], int i) { return (double)v[i]; }
+
+// Exact exponent E(x) and sign of the sum of the decoded components (v are
+// the raw component values, used only by the slow path).
+template <typename T>
+__device__ __forceinline__ Exact exact_exponent(const Comp (&c)[4], const T (&v)[4], int q, int Ptop) {
     Exact r;
     r.sign = 0;
     r.E = OZMP_EXP_ZERO;
@@ -284,12 +345,13 @@ __device__ __forceinline__ Exact exact_exponent(const Comp* c, int q, int Ptop) 
     uint64_t w[FAST_NW];
     bool tail = window_sum<FAST_NW>(w, c, q, L);
     if (!tail) return window_magnitude<FAST_NW>(w, L);
-    return exact_exponent_slow(c, q);
+    return exact_exponent_slow((double)v[0], (double)v[1], (double)v[2], (double)v[3], q);
 }
 
 // Exact |x| placed so that weight 2^(Erow - 1) is window bit 383 (bits
 // below bit 0 truncated).  Erow must satisfy |x| < 2^Erow.  Returns sign.
-__device__ __forceinline__ int aligned_magnitude(const Comp* c, int q, int Ptop, int Erow,
+template <typename T>
+__device__ __forceinline__ int aligned_magnitude(const Comp (&c)[4], const T (&v)[4], int q, int Ptop, int Erow,
                                                  uint64_t (&out)[FAST_NW]) {
 #pragma unroll
     for (int j = 0; j < FAST_NW; ++j) out[j] = 0;
@@ -305,10 +367,123 @@ __device__ __forceinline__ int aligned_magnitude(const Comp* c, int q, int Ptop,
         return ex.sign;
     }
     uint64_t tmp[FAST_NW];
-    int sg = aligned_slow(c, q, Erow, tmp);
+    int sg = aligned_slow((double)v[0], (double)v[1], (double)v[2], (double)v[3], q, Erow, tmp);
 #pragma unroll
     for (int j = 0; j < FAST_NW; ++j) out[j] = tmp[j];
     return sg;
+}
+
+// ----------------------------------------------------------------------------
+// exponent E(x) with a 128-bit window anchored at the largest component
+// ----------------------------------------------------------------------------
+// Components are added, truncated toward zero at the window LSB 2^L, into a
+// two's complement 128-bit integer V (L = Ptop - 125 leaves room for the
+// carries of four terms).  Without bits below the window V is exact.  With
+// them, x = V 2^L + T, |T| < q 2^L, and the top bit of |x| is that of |V|
+// unless |V| is within q of a power of two (or |V| < 2^64); those rare cases
+// take the exact full-range path.
+template <typename T>
+__device__ __forceinline__ int exponent_of(const Comp (&c)[4], const T (&v)[4], int q, int Ptop) {
+    if (Ptop == -100000) return OZMP_EXP_ZERO;
+    const int L = Ptop - 125;
+    unsigned __int128 V = 0;
+    bool tail = false;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (i >= q || c[i].M == 0) continue;
+        int sh = c[i].e - L;                      // <= 125 - bitlen(M)
+        unsigned __int128 part;
+        if (sh >= 0) {
+            part = (unsigned __int128)c[i].M << sh;
+        } else {
+            int r = -sh;
+            uint64_t mask = (r >= 64) ? ~0ull : ((1ull << r) - 1ull);
+            if (c[i].M & mask) tail = true;
+            part = (unsigned __int128)((r >= 64) ? 0ull : (c[i].M >> r));
+        }
+        V = c[i].neg ? V - part : V + part;
+    }
+    const bool negv = (uint64_t)(V >> 127) != 0;
+    unsigned __int128 A = negv ? (unsigned __int128)0 - V : V;
+    const uint64_t hi = (uint64_t)(A >> 64), lo = (uint64_t)A;
+    int top = hi ? 64 + 63 - __clzll((long long)hi) : (lo ? 63 - __clzll((long long)lo) : -1);
+    if (!tail) return top < 0 ? OZMP_EXP_ZERO : L + top + 1;
+    if (top >= 64) {
+        unsigned __int128 pw = (unsigned __int128)1 << top;
+        unsigned __int128 below = A - pw;                                  // >= 0
+        unsigned __int128 above = (top < 127) ? ((unsigned __int128)1 << (top + 1)) - A : (unsigned __int128)1;
+        if (below >= (unsigned __int128)q && above > (unsigned __int128)q) return L + top + 1;
+    }
+    return exact_exponent_slow((double)v[0], (double)v[1], (double)v[2], (double)v[3], q).E;
+}
+
+// ----------------------------------------------------------------------------
+// digit window anchored at the row exponent
+// ----------------------------------------------------------------------------
+// NW words; weight 2^(Erow - 1) sits at bit 64 NW - 2 (the top bit is the
+// sign), so digit t occupies bits [64 NW - 1 - beta t, 64 NW - 1 - beta (t-1))
+// at positions known at compile time.  Word 0 lies below every digit
+// (64 NW >= beta s + 65) and absorbs truncation: with bits of some component
+// below the window the truncated |x| differs from |V| only by a borrow or
+// carry out of word 0, which can reach the digits only when word 0 is
+// within q of 0 or of 2^64 -- those cases take the exact full-range path.
+template <int NW, typename T>
+__device__ __forceinline__ int digit_window(const Comp (&c)[4], const T (&v)[4], int q, int Erow,
+                                            uint64_t (&w)[NW]) {
+    const int L = Erow - (64 * NW - 1);
+    bool tail = window_sum<NW>(w, c, q, L);
+    bool neg = (w[NW - 1] >> 63) != 0;
+    if (neg) mw_neg<NW>(w);
+    if (!tail) return mw_is_zero<NW>(w) ? 0 : (neg ? -1 : 1);
+    if (w[0] >= (uint64_t)q && w[0] <= ~0ull - (uint64_t)q) return neg ? -1 : 1;
+    uint64_t tmp[NW];
+    int sg = slow_window((double)v[0], (double)v[1], (double)v[2], (double)v[3], q, Erow, NW, 64 * NW - 2, tmp);
+#pragma unroll
+    for (int j = 0; j < NW; ++j) w[j] = tmp[j];
+    return sg;
+}
+
+// digit t (1-based) of a digit window (BETA known at compile time)
+template <int NW, int BETA>
+__device__ __forceinline__ uint32_t digit_of(const uint64_t (&w)[NW], int t) {
+    const int p = 64 * NW - 1 - BETA * t;
+    const int wi = p >> 6, off = p & 63;
+    uint64_t x = w[wi] >> off;
+    if (off + BETA > 64 && wi + 1 < NW) x |= w[wi + 1] << (64 - off);
+    return (uint32_t)(x & ((1ull << BETA) - 1ull));
+}
+
+// digit t with a run-time beta (binary64 digits)
+template <int NW>
+__device__ __forceinline__ uint32_t digit_of_rt(const uint64_t (&w)[NW], int t, int beta) {
+    const int p = 64 * NW - 1 - beta * t;
+    const int wi = p >> 6, off = p & 63;
+    uint64_t a0 = 0, a1 = 0;
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+        if (j == wi) a0 = w[j];
+        if (j == wi + 1) a1 = w[j];
+    }
+    uint64_t x = (a0 >> off) | (off ? (a1 << (64 - off)) : 0ull);
+    return (uint32_t)(x & ((1ull << beta) - 1ull));
+}
+
+// four e4m3 codes of four magnitudes 0..15 (one per byte of m4), signs in
+// negmask (0x80 per negative byte; zero digits stay +0)
+__device__ __forceinline__ uint32_t e4m3x4(uint32_t m4, uint32_t negmask) {
+    // codes of 0..7 and 8..15 (integers below 16 are exact in e4m3)
+    const uint32_t lo0 = 0x44403800u, lo1 = 0x4E4C4A48u, hi0 = 0x53525150u, hi1 = 0x57565554u;
+    const uint32_t sel = (m4 & 7u) | ((m4 >> 4) & 0x70u) | ((m4 >> 8) & 0x700u) | ((m4 >> 12) & 0x7000u);
+    const uint32_t a = __byte_perm(lo0, lo1, sel), b = __byte_perm(hi0, hi1, sel);
+    const uint32_t big = ((m4 >> 3) & 0x01010101u) * 0xFFu;
+    const uint32_t code = (a & ~big) | (b & big);
+    return code | (negmask & __vcmpne4(code, 0u));
+}
+
+// four int8 digits (two's complement) of four magnitudes 0..127, sign bytes
+// 0xFF in negmask for negative ones
+__device__ __forceinline__ uint32_t int8x4(uint32_t m4, uint32_t negmask) {
+    return __vsub4(m4 ^ negmask, negmask);
 }
 
 // Digit t (1-based) of the aligned window: bits [384 - beta t, 384 - beta (t-1)).

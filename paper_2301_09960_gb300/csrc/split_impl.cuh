@@ -28,8 +28,7 @@ static __global__ void k_init_exponents(int32_t* E, int64_t mp, int32_t* F, int6
 }
 
 template <typename T>
-__device__ __forceinline__ bool load_elem(const Operand<T>& op, int64_t idx, Comp* c, int& Ptop) {
-    T v[4];
+__device__ __forceinline__ bool load_elem(const Operand<T>& op, int64_t idx, T (&v)[4], Comp (&c)[4], int& Ptop) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) v[i] = (i < op.q) ? op.c[i][idx] : (T)0;
     return decode_all<T>(v, op.q, c, Ptop);
@@ -41,7 +40,8 @@ __device__ __forceinline__ bool load_elem(const Operand<T>& op, int64_t idx, Com
 // rows of a column-major m x k matrix: one thread per row, a chunk of
 // columns per block row; consecutive threads read consecutive addresses.
 template <typename T>
-__global__ void k_exp_rows(Operand<T> a, int64_t m, int64_t k, int kchunk, int32_t* E, uint32_t* status) {
+__global__ void __launch_bounds__(256) k_exp_rows(Operand<T> a, int64_t m, int64_t k, int kchunk, int32_t* E,
+                                                  uint32_t* status) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     int64_t p0 = (int64_t)blockIdx.y * kchunk;
@@ -50,10 +50,11 @@ __global__ void k_exp_rows(Operand<T> a, int64_t m, int64_t k, int kchunk, int32
     bool ok = true;
     for (int64_t p = p0; p < p1; ++p) {
         Comp c[4];
+        T v[4];
         int Ptop;
-        ok &= load_elem<T>(a, i + p * a.ld, c, Ptop);
-        Exact ex = exact_exponent(c, a.q, Ptop);
-        emax = ex.E > emax ? ex.E : emax;
+        ok &= load_elem<T>(a, i + p * a.ld, v, c, Ptop);
+        int e = exponent_of<T>(c, v, a.q, Ptop);
+        emax = e > emax ? e : emax;
     }
     if (emax != OZMP_EXP_ZERO) atomicMax(&E[i], emax);
     if (!ok) atomicOr(status, ST_NONFINITE);
@@ -62,7 +63,7 @@ __global__ void k_exp_rows(Operand<T> a, int64_t m, int64_t k, int kchunk, int32
 // columns of a column-major k x n matrix (contiguous): one warp per column,
 // warp-shuffle max reduction.
 template <typename T>
-__global__ void k_exp_cols(Operand<T> b, int64_t k, int64_t n, int32_t* F, uint32_t* status) {
+__global__ void __launch_bounds__(256) k_exp_cols(Operand<T> b, int64_t k, int64_t n, int32_t* F, uint32_t* status) {
     int warps = blockDim.x >> 5;
     int64_t j = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5);
     int lane = threadIdx.x & 31;
@@ -71,10 +72,11 @@ __global__ void k_exp_cols(Operand<T> b, int64_t k, int64_t n, int32_t* F, uint3
     bool ok = true;
     for (int64_t p = lane; p < k; p += 32) {
         Comp c[4];
+        T v[4];
         int Ptop;
-        ok &= load_elem<T>(b, p + j * b.ld, c, Ptop);
-        Exact ex = exact_exponent(c, b.q, Ptop);
-        emax = ex.E > emax ? ex.E : emax;
+        ok &= load_elem<T>(b, p + j * b.ld, v, c, Ptop);
+        int e = exponent_of<T>(c, v, b.q, Ptop);
+        emax = e > emax ? e : emax;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -91,133 +93,143 @@ __global__ void k_exp_cols(Operand<T> b, int64_t k, int64_t n, int32_t* F, uint3
 // ---------------------------------------------------------------------------
 // K2: digits
 // ---------------------------------------------------------------------------
-// digit encodings: FORM_INT8 -> two's complement int8, FORM_FP8 -> e4m3,
+// encodings: FORM_INT8 -> two's complement int8, FORM_FP8 -> e4m3,
 // FORM_FP64 -> binary64 integer value.
 template <int FORM>
 struct DigitTraits;
-template <> struct DigitTraits<OZMP_FORM_INT8> { typedef uint8_t T; static constexpr int BETA = 7; static constexpr int MAXS = 36; };
-template <> struct DigitTraits<OZMP_FORM_FP8> { typedef uint8_t T; static constexpr int BETA = 4; static constexpr int MAXS = 64; };
-template <> struct DigitTraits<OZMP_FORM_FP64> { typedef double T; static constexpr int BETA = 0; static constexpr int MAXS = 64; };
+template <> struct DigitTraits<OZMP_FORM_INT8> { static constexpr int BETA = 7; static constexpr int MAXS = 36; };
+template <> struct DigitTraits<OZMP_FORM_FP8> { static constexpr int BETA = 4; static constexpr int MAXS = 64; };
 
-template <int FORM>
-__device__ __forceinline__ uint8_t encode_byte(int sign, uint32_t d) {
-    int v = sign < 0 ? -(int)d : (int)d;
-    if (FORM == OZMP_FORM_INT8) return (uint8_t)(int8_t)v;
-    return (uint8_t)e4m3_of_int(v);
+// the digit windows of four elements -> one 32-bit word of slice t
+template <int FORM, int NW>
+__device__ __forceinline__ uint32_t pack4(const uint64_t (&w)[4][NW], const int (&sign)[4], int t) {
+    constexpr int BETA = DigitTraits<FORM>::BETA;
+    uint32_t m4 = 0, neg = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        m4 |= digit_of<NW, BETA>(w[e], t) << (8 * e);
+        if (sign[e] < 0) neg |= (FORM == OZMP_FORM_INT8 ? 0xFFu : 0x80u) << (8 * e);
+    }
+    return (FORM == OZMP_FORM_INT8) ? int8x4(m4, neg) : e4m3x4(m4, neg);
 }
 
-// Rows of A: 32 x 32 element tile (1-byte digits) or 16 x 16 (binary64),
-// digits staged in shared memory [s][TI][TP] and written K-contiguous:
-// Adig[(t * mp + i) * kp + p].
-template <typename T, int FORM, int TI, int TP>
-__global__ void __launch_bounds__(256) k_split_rows(Operand<T> a, int64_t m, int64_t k, const int32_t* E,
-                                                    void* dig, int64_t mp, int64_t kp, int s, int beta) {
-    typedef typename DigitTraits<FORM>::T DT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    DT* sd = reinterpret_cast<DT*>(smem_raw);
-    const int64_t i0 = (int64_t)blockIdx.x * TI;
-    const int64_t p0 = (int64_t)blockIdx.y * TP;
-    constexpr int EPT = (TI * TP) / 256;   // elements per thread
-#pragma unroll 1
-    for (int e = 0; e < EPT; ++e) {
-        int lin = threadIdx.x + 256 * e;
-        int ri = lin % TI, pi = lin / TI;   // consecutive threads: consecutive rows (coalesced reads)
-        int64_t i = i0 + ri, p = p0 + pi;
-        Comp c[4];
-        int Ptop = -100000;
-        if (i < m && p < k) load_elem<T>(a, i + p * a.ld, c, Ptop);
-        int Erow = (i < m) ? E[i] : OZMP_EXP_ZERO;
-        uint64_t w[FAST_NW];
-        int sign = (Erow == OZMP_EXP_ZERO) ? 0 : aligned_magnitude(c, a.q, Ptop, Erow, w);
-        if (FORM == OZMP_FORM_FP64) {
-            for (int t = 1; t <= s; ++t) {
-                uint32_t d = sign ? take_top(w, beta) : 0u;
-                double v = (double)d;
-                ((double*)sd)[((t - 1) * TI + ri) * TP + pi] = sign < 0 ? -v : v;
-            }
-        } else {
-            constexpr int BETA = DigitTraits<FORM>::BETA;
+template <typename T, int NW>
+__device__ __forceinline__ int window_of(const Operand<T>& op, bool inside, int64_t idx, int Erow, uint64_t (&w)[NW]) {
+    Comp c[4];
+    T v[4] = {(T)0, (T)0, (T)0, (T)0};
+    int Ptop = -100000;
+    if (inside) load_elem<T>(op, idx, v, c, Ptop);
+    if (!inside || Ptop == -100000 || Erow == OZMP_EXP_ZERO) {
 #pragma unroll
-            for (int t = 1; t <= DigitTraits<FORM>::MAXS; ++t) {
-                if (t <= s) {
-                    uint32_t d = sign ? digit_at<BETA>(w, t) : 0u;
-                    ((uint8_t*)sd)[((t - 1) * TI + ri) * TP + pi] = encode_byte<FORM>(sign, d);
-                }
-            }
+        for (int j = 0; j < NW; ++j) w[j] = 0;
+        return 0;
+    }
+    return digit_window<NW, T>(c, v, op.q, Erow, w);
+}
+
+// Rows of A (column-major) -> Adig[(t * mp + i) * kp + p], 1-byte digits.
+// Tile: 32 rows x 64 columns, 256 threads; thread (row ri, quad) handles
+// 4 consecutive columns of one row (two quads per thread); the 4 digits of
+// a slice go to shared memory as one word [t][ri][quad], then the tile is
+// written K-contiguous.
+template <typename T, int FORM, int NW>
+__global__ void __launch_bounds__(256) k_split_rows_b1(Operand<T> a, int64_t m, int64_t k, const int32_t* E,
+                                                       uint8_t* dig, int64_t mp, int64_t kp, int s) {
+    constexpr int TI = 32, TP = 64, QW = TP / 4;    // 16 words per tile row
+    extern __shared__ __align__(16) uint32_t sw[];  // [s][TI][QW]
+    const int64_t i0 = (int64_t)blockIdx.x * TI, p0 = (int64_t)blockIdx.y * TP;
+    const int ri = threadIdx.x & 31;
+    const int64_t i = i0 + ri;
+    const int Erow = (i < m) ? E[i] : OZMP_EXP_ZERO;
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        const int qd = (threadIdx.x >> 5) + 8 * h;
+        uint64_t w[4][NW];
+        int sign[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int64_t p = p0 + 4 * qd + e;
+            sign[e] = window_of<T, NW>(a, i < m && p < k, i + p * a.ld, Erow, w[e]);
         }
+#pragma unroll
+        for (int t = 1; t <= DigitTraits<FORM>::MAXS; ++t)
+            if (t <= s) sw[((t - 1) * TI + ri) * QW + qd] = pack4<FORM, NW>(w, sign, t);
     }
     __syncthreads();
-    // write out: each slice is a TI x TP tile, rows of TP digits
-    constexpr int WORD = 4;                                   // bytes per store
-    constexpr int ROWBYTES = TP * (int)sizeof(DT);
-    constexpr int WPR = ROWBYTES / WORD;                      // words per row
-    const int total = s * TI * WPR;
-    for (int w = threadIdx.x; w < total; w += 256) {
-        int t = w / (TI * WPR);
-        int r = (w / WPR) % TI;
-        int c = w % WPR;
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(smem_raw + ((size_t)(t * TI + r) * TP) * sizeof(DT)) + c;
-        unsigned char* dst = (unsigned char*)dig + (((size_t)t * mp + (i0 + r)) * kp + p0) * sizeof(DT) + (size_t)c * WORD;
-        *reinterpret_cast<uint32_t*>(dst) = *src;
+    const int total = s * TI * QW;
+    for (int x = threadIdx.x; x < total; x += 256) {
+        const int t = x / (TI * QW), r = (x / QW) % TI, c = x % QW;
+        *reinterpret_cast<uint32_t*>(dig + ((size_t)t * mp + (i0 + r)) * kp + p0 + 4 * c) = sw[x];
     }
 }
 
-// Columns of B (contiguous along k): 1-byte digits, 4 consecutive k per
-// thread (one 32-bit store per slice); Bdig[(t * np + j) * kp + p].
-template <typename T, int FORM>
+// Columns of B (contiguous along k) -> Bdig[(t * np + j) * kp + p], 1-byte
+// digits: 4 consecutive k per thread, one 32-bit store per slice.
+template <typename T, int FORM, int NW>
 __global__ void __launch_bounds__(256) k_split_cols_b1(Operand<T> b, int64_t k, int64_t n, const int32_t* F,
                                                        uint8_t* dig, int64_t np, int64_t kp, int s) {
-    constexpr int BETA = DigitTraits<FORM>::BETA;
     const int64_t quads = kp / 4;
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= quads * np) return;
-    int64_t j = g / quads;
-    int64_t p0 = (g % quads) * 4;
-    int Ecol = (j < n) ? F[j] : OZMP_EXP_ZERO;
-    uint64_t w[4][FAST_NW];
+    const int64_t j = g / quads;
+    const int64_t p0 = (g % quads) * 4;
+    const int Ecol = (j < n) ? F[j] : OZMP_EXP_ZERO;
+    uint64_t w[4][NW];
     int sign[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-        int64_t p = p0 + e;
-        Comp c[4];
-        int Ptop = -100000;
-        if (j < n && p < k) load_elem<T>(b, p + j * b.ld, c, Ptop);
-        sign[e] = (Ecol == OZMP_EXP_ZERO) ? 0 : aligned_magnitude(c, b.q, Ptop, Ecol, w[e]);
+        const int64_t p = p0 + e;
+        sign[e] = window_of<T, NW>(b, j < n && p < k, p + j * b.ld, Ecol, w[e]);
     }
 #pragma unroll
-    for (int t = 1; t <= DigitTraits<FORM>::MAXS; ++t) {
-        if (t <= s) {
-            uint32_t word = 0;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                uint32_t d = sign[e] ? digit_at<BETA>(w[e], t) : 0u;
-                word |= (uint32_t)encode_byte<FORM>(sign[e], d) << (8 * e);
-            }
-            *reinterpret_cast<uint32_t*>(dig + ((size_t)(t - 1) * np + j) * kp + p0) = word;
-        }
+    for (int t = 1; t <= DigitTraits<FORM>::MAXS; ++t)
+        if (t <= s)
+            *reinterpret_cast<uint32_t*>(dig + ((size_t)(t - 1) * np + j) * kp + p0) = pack4<FORM, NW>(w, sign, t);
+}
+
+// binary64 digits, rows of A: 16 x 16 tile staged in shared memory
+template <typename T, int NW>
+__global__ void __launch_bounds__(256) k_split_rows_f64(Operand<T> a, int64_t m, int64_t k, const int32_t* E,
+                                                        double* dig, int64_t mp, int64_t kp, int s, int beta) {
+    constexpr int TI = 16, TP = 16;
+    extern __shared__ __align__(16) double sd[];    // [s][TI][TP]
+    const int64_t i0 = (int64_t)blockIdx.x * TI, p0 = (int64_t)blockIdx.y * TP;
+    const int ri = threadIdx.x % TI, pi = threadIdx.x / TI;
+    const int64_t i = i0 + ri, p = p0 + pi;
+    const int Erow = (i < m) ? E[i] : OZMP_EXP_ZERO;
+    uint64_t w[NW];
+    const int sign = window_of<T, NW>(a, i < m && p < k, i + p * a.ld, Erow, w);
+    for (int t = 1; t <= s; ++t) {
+        const double d = (double)digit_of_rt<NW>(w, t, beta);
+        sd[((t - 1) * TI + ri) * TP + pi] = sign < 0 ? -d : d;
+    }
+    __syncthreads();
+    const int total = s * TI * TP;
+    for (int x = threadIdx.x; x < total; x += 256) {
+        const int t = x / (TI * TP), r = (x / TP) % TI, c = x % TP;
+        dig[((size_t)t * mp + (i0 + r)) * kp + p0 + c] = sd[x];
     }
 }
 
-// Columns of B, binary64 digits: one element per thread.
-template <typename T>
+// binary64 digits, columns of B: one element per thread
+template <typename T, int NW>
 __global__ void __launch_bounds__(256) k_split_cols_f64(Operand<T> b, int64_t k, int64_t n, const int32_t* F,
                                                         double* dig, int64_t np, int64_t kp, int s, int beta) {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= kp * np) return;
-    int64_t j = g / kp, p = g % kp;
-    int Ecol = (j < n) ? F[j] : OZMP_EXP_ZERO;
-    Comp c[4];
-    int Ptop = -100000;
-    if (j < n && p < k) load_elem<T>(b, p + j * b.ld, c, Ptop);
-    uint64_t w[FAST_NW];
-    int sign = (Ecol == OZMP_EXP_ZERO) ? 0 : aligned_magnitude(c, b.q, Ptop, Ecol, w);
+    const int64_t j = g / kp, p = g % kp;
+    const int Ecol = (j < n) ? F[j] : OZMP_EXP_ZERO;
+    uint64_t w[NW];
+    const int sign = window_of<T, NW>(b, j < n && p < k, p + j * b.ld, Ecol, w);
     for (int t = 1; t <= s; ++t) {
-        uint32_t d = sign ? take_top(w, beta) : 0u;
-        double v = (double)d;
-        dig[((size_t)(t - 1) * np + j) * kp + p] = sign < 0 ? -v : v;
+        const double d = (double)digit_of_rt<NW>(w, t, beta);
+        dig[((size_t)(t - 1) * np + j) * kp + p] = sign < 0 ? -d : d;
     }
 }
 
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
 template <typename T>
 static inline Operand<T> make_op(const void* const* comps, int q, int64_t ld) {
     Operand<T> o;
@@ -227,31 +239,52 @@ static inline Operand<T> make_op(const void* const* comps, int q, int64_t ld) {
     return o;
 }
 
+// words of the digit window: word 0 below every digit, sign bit on top
+static inline int digit_words(int beta, int s) { return (beta * s + 65 + 63) / 64; }
+
+template <typename T, int FORM, int NW>
+static cudaError_t digits_b1(const SplitArgs& g, cudaStream_t st) {
+    Operand<T> a = make_op<T>(g.A, g.q, g.lda);
+    Operand<T> b = make_op<T>(g.B, g.q, g.ldb);
+    dim3 gr((unsigned)(g.mp / 32), (unsigned)(g.kp / 64));
+    size_t sm = (size_t)g.s * 32 * 16 * 4;
+    auto kr = k_split_rows_b1<T, FORM, NW>;
+    cudaError_t e = cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kr<<<gr, 256, sm, st>>>(a, g.m, g.k, g.E, (uint8_t*)g.Adig, g.mp, g.kp, g.s);
+    int64_t tot = (g.kp / 4) * g.np;
+    k_split_cols_b1<T, FORM, NW><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(b, g.k, g.n, g.F, (uint8_t*)g.Bdig,
+                                                                              g.np, g.kp, g.s);
+    return cudaGetLastError();
+}
+
+template <typename T, int NW>
+static cudaError_t digits_f64(const SplitArgs& g, cudaStream_t st) {
+    Operand<T> a = make_op<T>(g.A, g.q, g.lda);
+    Operand<T> b = make_op<T>(g.B, g.q, g.ldb);
+    dim3 gr((unsigned)(g.mp / 16), (unsigned)(g.kp / 16));
+    size_t sm = (size_t)g.s * 16 * 16 * 8;
+    auto kr = k_split_rows_f64<T, NW>;
+    cudaError_t e = cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kr<<<gr, 256, sm, st>>>(a, g.m, g.k, g.E, (double*)g.Adig, g.mp, g.kp, g.s, g.beta);
+    int64_t tot = g.kp * g.np;
+    k_split_cols_f64<T, NW><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(b, g.k, g.n, g.F, (double*)g.Bdig,
+                                                                          g.np, g.kp, g.s, g.beta);
+    return cudaGetLastError();
+}
+
 // digits of both operands for one form (the padded region gets zero digits)
 template <typename T, int FORM>
 static cudaError_t digits_impl(const SplitArgs& g, cudaStream_t st) {
-    Operand<T> a = make_op<T>(g.A, g.q, g.lda);
-    Operand<T> b = make_op<T>(g.B, g.q, g.ldb);
-    if (FORM == OZMP_FORM_FP64) {
-        dim3 gr((unsigned)(g.mp / 16), (unsigned)(g.kp / 16));
-        size_t sm = (size_t)g.s * 16 * 16 * 8;
-        auto kr = k_split_rows<T, OZMP_FORM_FP64, 16, 16>;
-        cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        kr<<<gr, 256, sm, st>>>(a, g.m, g.k, g.E, g.Adig, g.mp, g.kp, g.s, g.beta);
-        int64_t tot = g.kp * g.np;
-        k_split_cols_f64<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(b, g.k, g.n, g.F, (double*)g.Bdig,
-                                                                         g.np, g.kp, g.s, g.beta);
+    const int nw = digit_words(g.beta, g.s);
+    if constexpr (FORM == OZMP_FORM_FP64) {
+        if (nw <= 4) return digits_f64<T, 4>(g, st);
+        return digits_f64<T, 7>(g, st);
     } else {
-        dim3 gr((unsigned)(g.mp / 32), (unsigned)(g.kp / 32));
-        size_t sm = (size_t)g.s * 32 * 32;
-        int64_t tot = (g.kp / 4) * g.np;
-        auto kr = k_split_rows<T, FORM, 32, 32>;
-        cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        kr<<<gr, 256, sm, st>>>(a, g.m, g.k, g.E, g.Adig, g.mp, g.kp, g.s, g.beta);
-        k_split_cols_b1<T, FORM><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
-            b, g.k, g.n, g.F, (uint8_t*)g.Bdig, g.np, g.kp, g.s);
+        if (nw <= 4) return digits_b1<T, FORM, 4>(g, st);
+        return digits_b1<T, FORM, 6>(g, st);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace ozmp

@@ -236,3 +236,54 @@ def test_nondefault_stream_and_repeat():
     s.synchronize()
     for x, y in zip(C1, C2):
         assert torch.equal(x, y)
+
+
+def _adversarial(q, rows, cols, seed, dtype=np.float64):
+    """Components at exact powers of two with tiny tails of either sign,
+    spans far beyond 128 bits, cancelling leading pairs and zeros: every
+    fast/slow boundary of the exponent and digit windows."""
+    rng = np.random.default_rng(seed)
+    tiny = 2.0 ** -140 if dtype == np.float32 else 2.0 ** -1000
+    comps = [np.zeros((rows, cols)) for _ in range(q)]
+    for i in range(rows):
+        for j in range(cols):
+            kind = rng.integers(0, 6)
+            e = int(rng.integers(-30, 30))
+            hi = float(rng.choice([-1.0, 1.0])) * 2.0 ** e
+            if kind == 1:
+                hi *= 1.0 + float(rng.integers(1, 2 ** 20)) * 2.0 ** -52 if dtype == np.float64 else 1.0
+            vals = [hi]
+            for t in range(1, q):
+                gap = int(rng.integers(1, 400 if dtype == np.float64 else 100))
+                v = float(rng.choice([-1.0, 1.0])) * 2.0 ** (e - gap)
+                if kind == 2:
+                    v = -vals[-1] if t == 1 else v          # cancelling pair
+                if kind == 3:
+                    v = max(v, tiny) if v > 0 else min(v, -tiny)
+                vals.append(v)
+            if kind == 4:
+                vals = [0.0] * q
+            for t in range(q):
+                comps[t][i, j] = vals[t]
+    return [np.asfortranarray(c.astype(dtype)) for c in comps]
+
+
+@pytest.mark.parametrize("form", ["fp8", "int8", "fp64"])
+@pytest.mark.parametrize("prec", ["dd", "qd", "ts"])
+def test_split_adversarial_boundaries(prec, form):
+    q = {"dd": 2, "qd": 4, "ts": 3}[prec]
+    dt = np.float32 if prec == "ts" else np.float64
+    m, n, k = 40, 36, 33
+    A = _adversarial(q, m, k, 11, dt)
+    B = _adversarial(q, k, n, 12, dt)
+    p = oz.Plan(prec, m, n, k, form, 6 if form == "fp64" else 20)
+    p.split(to_dev(A), to_dev(B))
+    torch.cuda.synchronize()
+    i = p.info
+    E, F = [t.cpu().numpy() for t in p.exponents()]
+    ga, gb = [t.cpu().numpy() for t in p.digits()]
+    Eo, dA = O.split(A, i.beta, i.nslices)
+    Fo, dB = O.split([np.asfortranarray(b.T) for b in B], i.beta, i.nslices)
+    assert list(E) == Eo and list(F) == Fo
+    np.testing.assert_array_equal(digits_to_int(ga[:, :m, :k], form), dA)
+    np.testing.assert_array_equal(digits_to_int(gb[:, :n, :k], form), dB)
