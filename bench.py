@@ -154,6 +154,73 @@ def run_variant(oz, torch, prec, form, n, phi, steps, warmup, nslices=0):
     return out
 
 
+def config2(oz, torch):
+    """TD and QD 1024^3, binary64 slices (and e4m3 slices), with the simple
+    multi-component GEMM as the side baseline (one timed pass each)."""
+    out = []
+    n = 1024
+    for prec in ("td", "qd"):
+        for form in ("fp64", "fp8"):
+            try:
+                out.append(run_variant(oz, torch, prec, form, n, 1.0, 1, 1))
+            except Exception as ex:
+                out.append({"prec": prec, "form": form, "error": repr(ex)[:200]})
+        A, B = _host_operands(prec, n, n, n, 1.0, 0)
+        Ad = [oz.colmajor(a) for a in A]
+        Bd = [oz.colmajor(b) for b in B]
+        C = [torch.empty((n, n), dtype=torch.float64, device="cuda").T for _ in A]
+        oz.ozmp_gemm_naive(prec, Ad, Bd, C)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        oz.ozmp_gemm_naive(prec, Ad, Bd, C)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out.append({"prec": prec, "form": "naive (multi-component triple loop)", "ms_per_step": ms,
+                    "gflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e9})
+    return out
+
+
+def config4(oz, torch):
+    """512 uneven DD/TD problems (m, n, k log-uniform in [32, 768], seed 1):
+    one graph replay of the batched plan vs a loop of single calls."""
+    from ozmp_inputs import batched_problem_shapes, gen_problem
+    shapes = batched_problem_shapes(512, seed=1)
+    probs = []
+    flops = 0.0
+    for idx, (m, n, k, prec) in enumerate(shapes):
+        A, B = gen_problem(prec, m, n, k, phi=1.0, seed=1000 + idx)
+        C = [torch.empty((n, m), dtype=torch.float64, device="cuda").T for _ in A]
+        probs.append((prec, [oz.colmajor(a) for a in A], [oz.colmajor(b) for b in B], C, 0))
+        flops += 2.0 * m * n * k
+    plan = oz.ozmp_gemm_batched(probs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record()
+    for _ in range(reps):
+        oz.ozmp_gemm_batched(probs, plan=plan)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1) / reps
+    st = oz.ozmp_plan_get_status(plan)
+    oz.ozmp_plan_destroy(plan)
+    plans = [oz.Plan(p[0], p[1][0].shape[0], p[2][0].shape[1], p[1][0].shape[1], "auto", 0) for p in probs]
+    for pl, p in zip(plans, probs):
+        pl.execute(p[1], p[2], p[3])
+    torch.cuda.synchronize()
+    e0.record()
+    for pl, p in zip(plans, probs):
+        pl.execute(p[1], p[2], p[3])
+    e1.record()
+    torch.cuda.synchronize()
+    ms_l = e0.elapsed_time(e1)
+    return {"problems": len(probs), "gflops_total": flops / 1e9, "batched_ms": ms_b,
+            "batched_gflops": flops / (ms_b * 1e-3) / 1e9, "loop_ms": ms_l,
+            "loop_gflops": flops / (ms_l * 1e-3) / 1e9, "status": st.name}
+
+
 def splitter_bytes(q, w, m, n, k, s, db):
     # K1 reads both operands, K2 reads them again and writes the digits
     return 2 * q * w * (m * k + k * n) + s * db * (m * k + k * n)
@@ -367,6 +434,8 @@ def main():
             except Exception as ex:  # report, do not hide
                 var.append({"prec": vp, "form": vf, "error": repr(ex)[:200]})
         line["variants"] = var
+        line["config2_td_qd_1024"] = config2(oz, torch)
+        line["config4_batched512"] = config4(oz, torch)
 
     if rank == 0:
         print(json.dumps(line))

@@ -179,6 +179,49 @@ ozmp_status ozmp_gemm_dd_noalloc(int64_t m, int64_t n, int64_t k, const double* 
                                  const double* const B[2], int64_t ldb, double* const C[2], int64_t ldc,
                                  int nslices, ozmp_stream stream);
 
+/*
+ * Batched products (the paper computes one product at a time, Sec. 3;
+ * batching is this library's addition): count independent problems
+ * C_i := A_i B_i, each with its own precision, shape, leading dimensions and
+ * slice count (0 = automatic), run as one captured CUDA graph.  For
+ * FORM_FP8 / FORM_AUTO the graph holds one batched exponent launch, one
+ * batched digit launch per operand and ONE persistent tcgen05 product launch
+ * whose CTAs walk a load-balanced list of (problem, tile) items; the tile
+ * width of each problem (128 or 256 columns) comes from an autotuner that
+ * times both widths once per process (cached in the file named by the
+ * environment variable OZMP_AUTOTUNE_CACHE, if set).  Other forms run the
+ * problems one after another inside the graph.
+ *   *plan == NULL: build a batched plan (workspace, schedule, graph), store it
+ *   in *plan and run it.  *plan from an earlier call with the same count,
+ *   precisions and shapes: run it again; the A/B/C pointers may change
+ *   between calls.  Destroy with ozmp_plan_destroy; status with
+ *   ozmp_plan_get_status (one word for the whole batch).
+ * The problem array and the component-pointer arrays it points to are read
+ * during the call only.
+ */
+typedef struct {
+    ozmp_prec prec;
+    int64_t m, n, k, lda, ldb, ldc;
+    const void* const* A;   /* q component pointers (double* or float* for TS) */
+    const void* const* B;
+    void* const* C;
+    int nslices;            /* 0 = automatic */
+} ozmp_problem;
+ozmp_status ozmp_gemm_batched(const ozmp_problem* problems, int count, ozmp_form form, ozmp_stream stream,
+                              ozmp_plan* plan);
+
+/*
+ * ozmp_gemm_naive -- the paper's "simple matrix multiplication" baseline
+ * (Sec. 4; its GPU form with shared memory, Sec. 4.4): the triple loop in
+ * multi-component arithmetic (TwoProd / TwoSum per word product, the q-word
+ * accumulator renormalised after every multiply-add), 16 x 16 shared-memory
+ * tiles.  Not an Ozaki-scheme product and not exact; it is the yardstick the
+ * paper compares the scheme with.  Arguments as ozmp_plan_execute, on
+ * `stream`.
+ */
+ozmp_status ozmp_gemm_naive(ozmp_prec prec, int64_t m, int64_t n, int64_t k, const void* const* A, int64_t lda,
+                            const void* const* B, int64_t ldb, void* const* C, int64_t ldc, ozmp_stream stream);
+
 /* Stream and digit form used by the plain entry points of this thread. */
 ozmp_status ozmp_set_stream(ozmp_stream stream);
 ozmp_status ozmp_set_form(ozmp_form form);

@@ -24,7 +24,7 @@ __all__ = [
     "Status", "Prec", "Form", "OzmpError", "PlanInfo", "Plan", "load", "colmajor",
     "ozmp_plan_create", "ozmp_plan_destroy", "ozmp_plan_get_info", "ozmp_plan_set_workspace",
     "ozmp_plan_set_stream", "ozmp_plan_execute", "ozmp_plan_get_status", "ozmp_plan_split",
-    "ozmp_plan_diagonal", "ozmp_plan_multiply", "ozmp_gemm_dd", "ozmp_gemm_td", "ozmp_gemm_qd", "ozmp_gemm_ts", "ozmp_gemm_dd_noalloc",
+    "ozmp_plan_diagonal", "ozmp_plan_multiply", "ozmp_gemm_dd", "ozmp_gemm_td", "ozmp_gemm_qd", "ozmp_gemm_ts", "ozmp_gemm_dd_noalloc", "ozmp_gemm_batched", "Problem", "ozmp_gemm_naive",
     "ozmp_set_stream", "ozmp_set_form", "ozmp_last_status", "ozmp_version", "gemm", "EXP_ZERO",
 ]
 
@@ -86,6 +86,13 @@ class PlanInfo(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class Problem(ctypes.Structure):
+    """ozmp_problem: one product of a batch."""
+    _fields_ = [("prec", ctypes.c_int), ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("lda", ctypes.c_int64), ("ldb", ctypes.c_int64), ("ldc", ctypes.c_int64),
+                ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("C", ctypes.c_void_p), ("nslices", ctypes.c_int)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -114,6 +121,8 @@ SIGNATURES = {
     "ozmp_set_form": [ctypes.c_int],
     "ozmp_last_status": [ctypes.POINTER(ctypes.c_int)],
     "ozmp_version": [],
+    "ozmp_gemm_naive": [ctypes.c_int, _I64, _I64, _I64, _PP, _I64, _PP, _I64, _PP, _I64, _VP],
+    "ozmp_gemm_batched": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _VP, ctypes.POINTER(_VP)],
 }
 
 
@@ -273,6 +282,43 @@ def ozmp_gemm_dd_noalloc(A, B, C, nslices=0, stream=None):
     st = load().ozmp_gemm_dd_noalloc(m, n, k, pa, _ld(A[0]), pb, _ld(B[0]), pc, _ld(C[0]), nslices,
                                      _stream_handle(stream))
     _check(st, "ozmp_gemm_dd_noalloc")
+
+
+def ozmp_gemm_batched(problems, form=Form.AUTO, stream=None, plan=None):
+    """Run a batch of products; problems is a list of (prec, A, B, C, nslices)
+    with column-major torch operands.  Returns the (reusable) batched plan."""
+    n = len(problems)
+    arr = (Problem * n)()
+    keep = []
+    for i, (prec, A, B, C, ns) in enumerate(problems):
+        prec = PREC_BY_NAME[prec] if isinstance(prec, str) else Prec(prec)
+        m, k = A[0].shape
+        nn = B[0].shape[1]
+        pa, ka = _ptrs(A)
+        pb, kb = _ptrs(B)
+        pc, kc = _ptrs(C)
+        keep += [ka, kb, kc]
+        arr[i] = Problem(int(prec), m, nn, k, _ld(A[0]), _ld(B[0]), _ld(C[0]),
+                         ctypes.cast(ka, ctypes.c_void_p), ctypes.cast(kb, ctypes.c_void_p),
+                         ctypes.cast(kc, ctypes.c_void_p), ns)
+    h = plan if plan is not None else ctypes.c_void_p()
+    st = load().ozmp_gemm_batched(ctypes.cast(arr, ctypes.c_void_p), n, int(form), _stream_handle(stream),
+                                  ctypes.byref(h))
+    _check(st, "ozmp_gemm_batched")
+    return h
+
+
+def ozmp_gemm_naive(prec, A, B, C, stream=None):
+    """The triple-loop multi-component product (the paper's baseline)."""
+    prec = PREC_BY_NAME[prec] if isinstance(prec, str) else Prec(prec)
+    m, k = A[0].shape
+    n = B[0].shape[1]
+    pa, ka = _ptrs(A)
+    pb, kb = _ptrs(B)
+    pc, kc = _ptrs(C)
+    st = load().ozmp_gemm_naive(int(prec), m, n, k, pa, _ld(A[0]), pb, _ld(B[0]), pc, _ld(C[0]),
+                                _stream_handle(stream))
+    _check(st, "ozmp_gemm_naive")
 
 
 def ozmp_set_stream(stream=None):

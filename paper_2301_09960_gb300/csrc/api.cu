@@ -31,6 +31,12 @@ ozmp_status ozmp_plan_create(ozmp_plan* plan, ozmp_prec prec, int64_t m, int64_t
 
 ozmp_status ozmp_plan_destroy(ozmp_plan p) {
     if (!p) return OZMP_ERR_INVALID_ARG;
+    if (p->batch) {
+        cudaStreamSynchronize(p->stream);
+        ozmp_batch::destroy(p->batch);
+        delete p;
+        return OZMP_OK;
+    }
     if (p->ws && p->ws_owned) {
         cudaStreamSynchronize(p->stream);
         cudaFree(p->ws);

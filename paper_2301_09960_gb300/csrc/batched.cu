@@ -1,0 +1,591 @@
+// Batched products: many uneven problems, each at its own precision and
+// slice count, in one captured CUDA graph -- one batched exponent launch,
+// one batched digit launch per operand and one persistent tcgen05 product
+// launch whose CTAs each walk a precomputed, load-balanced list of
+// (problem, tile) items.
+//
+// The paper computes one product at a time (Sec. 3, Algorithm 1); batching is
+// this library's addition.  The autotuner picks each problem's tile width
+// (128 or 256 columns of C) from a per-process measurement of the two widths
+// and balances the items over the CTAs (longest processing time first).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <queue>
+#include <vector>
+#include "gemm_tc_impl.cuh"
+#include "plan.h"
+#include "split_impl.cuh"
+
+using namespace ozmp;
+using namespace ozmp_plan_detail;
+
+namespace ozmp {
+
+// per problem split descriptor (device memory)
+struct BSplit {
+    const void* A[4];
+    const void* B[4];
+    int64_t lda, ldb, m, n, k, mp, np, kp;
+    int32_t* E;
+    int32_t* F;
+    uint8_t* Adig;
+    uint8_t* Bdig;
+    int q, s;
+};
+
+// problem of batched block b: the last p with pre[p] <= b
+__device__ __forceinline__ int find_prob(const int* pre, int count, int b) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ Operand<T> opA(const BSplit& s) {
+    Operand<T> o;
+    for (int i = 0; i < 4; ++i) o.c[i] = (const T*)s.A[i];
+    o.ld = s.lda;
+    o.q = s.q;
+    return o;
+}
+template <typename T>
+__device__ __forceinline__ Operand<T> opB(const BSplit& s) {
+    Operand<T> o;
+    for (int i = 0; i < 4; ++i) o.c[i] = (const T*)s.B[i];
+    o.ld = s.ldb;
+    o.q = s.q;
+    return o;
+}
+
+__global__ void k_b_init(const BSplit* P, const int* pre, int count) {
+    const int p = find_prob(pre, count, blockIdx.x);
+    const BSplit& s = P[p];
+    const int64_t i = (int64_t)(blockIdx.x - pre[p]) * blockDim.x + threadIdx.x;
+    if (i < s.mp) s.E[i] = OZMP_EXP_ZERO;
+    if (i < s.np) s.F[i] = OZMP_EXP_ZERO;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_exp_rows(const BSplit* P, const int* pre, int count, uint32_t* status) {
+    const int p = find_prob(pre, count, blockIdx.x);
+    const BSplit& s = P[p];
+    const int lb = blockIdx.x - pre[p];
+    const int nbx = (int)((s.m + 255) / 256);
+    exp_rows_body(opA<T>(s), s.m, s.k, 256, s.E, status, (int64_t)(lb % nbx), (int64_t)(lb / nbx));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_exp_cols(const BSplit* P, const int* pre, int count, uint32_t* status) {
+    const int p = find_prob(pre, count, blockIdx.x);
+    const BSplit& s = P[p];
+    exp_cols_body(opB<T>(s), s.k, s.n, s.F, status, (int64_t)(blockIdx.x - pre[p]), (int64_t)0);
+}
+
+template <typename T, int NW>
+__global__ void __launch_bounds__(256) k_b_split_rows(const BSplit* P, const int* pre, int count) {
+    const int p = find_prob(pre, count, blockIdx.x);
+    const BSplit& s = P[p];
+    const int lb = blockIdx.x - pre[p];
+    const int nbx = (int)(s.mp / 32);
+    split_rows_b1_body<T, OZMP_FORM_FP8, NW>(opA<T>(s), s.m, s.k, s.E, s.Adig, s.mp, s.kp, s.s,
+                                             (int64_t)(lb % nbx), (int64_t)(lb / nbx));
+}
+
+template <typename T, int NW>
+__global__ void __launch_bounds__(256) k_b_split_cols(const BSplit* P, const int* pre, int count) {
+    const int p = find_prob(pre, count, blockIdx.x);
+    const BSplit& s = P[p];
+    split_cols_b1_body<T, OZMP_FORM_FP8, NW>(opB<T>(s), s.k, s.n, s.F, s.Bdig, s.np, s.kp, s.s,
+                                             (int64_t)(blockIdx.x - pre[p]), (int64_t)0);
+}
+
+}  // namespace ozmp
+
+// ----------------------------------------------------------------------------
+// host: batched plan
+// ----------------------------------------------------------------------------
+namespace {
+
+struct Group {              // problems sharing a component type (batched split launches)
+    std::vector<int> ids;
+    int is_f32 = 0;
+    int nw = 4;
+    int s_max = 1;
+    // device offsets (bytes into meta) of BSplit[] and prefix arrays; block totals
+    size_t off_split = 0, off_pre[5] = {0, 0, 0, 0, 0};
+    int blocks[5] = {0, 0, 0, 0, 0};   // init, exp rows, exp cols, split rows, split cols
+};
+
+struct Batch {
+    int count = 0, form = 0;
+    std::vector<ozmp_plan_s> subs;
+    std::vector<size_t> ws_off;
+    std::vector<int> bn;
+    std::vector<Group> groups;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    void* meta = nullptr;          // device: splits, probs, maps, prefixes, items, offsets, status
+    size_t meta_bytes = 0;
+    void* pinned = nullptr;        // host mirror of the pointer-carrying descriptors
+    size_t pinned_bytes = 0;
+    size_t off_probs = 0, off_maps = 0, off_items = 0, off_cta = 0, off_status = 0;
+    int grid = 0;
+    std::vector<int> q;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t stream = nullptr;
+    std::vector<const void*> baked;   // caller pointers captured into the graph (forms other than FP8)
+    cudaEvent_t launched = nullptr;    // recorded after every replay: the pinned mirror is free again
+};
+
+// calibrated cost (relative) of one (tile, pair, k-chunk) step for 128- and
+// 256-column tiles; measured once per process
+std::mutex g_tune_mu;
+bool g_tuned = false;
+double g_cost128 = 0.55, g_cost256 = 1.0;
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+void calibrate_once(cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (g_tuned) return;
+    g_tuned = true;
+    const char* env = getenv("OZMP_AUTOTUNE_CACHE");
+    if (env) {
+        FILE* f = fopen(env, "r");
+        if (f) {
+            double a = 0, b = 0;
+            if (fscanf(f, "%lf %lf", &a, &b) == 2 && a > 0 && b > 0) { g_cost128 = a; g_cost256 = b; fclose(f); return; }
+            fclose(f);
+        }
+    }
+    // synthetic problem: digits all e4m3 1.0, E = F = 0, s = 8, 256 x 512 x 1024
+    const int64_t m = 256, n = 512, k = 1024;
+    const int s = 8;
+    const size_t dig = (size_t)s * (m + n) * k, limbs = (size_t)(4 * 3 + 1) * m * n * 8;
+    char* buf = nullptr;
+    if (cudaMalloc(&buf, a256(dig) + a256(limbs) + a256(m * 4) + a256(n * 4) + a256(m * n * 8 * 2) + 256) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    char* Ad = buf;
+    char* Bd = Ad + (size_t)s * m * k;
+    int64_t* acc = (int64_t*)(buf + a256(dig));
+    int32_t* E = (int32_t*)((char*)acc + a256(limbs));
+    int32_t* F = (int32_t*)((char*)E + a256(m * 4));
+    double* C0 = (double*)((char*)F + a256(n * 4));
+    double* C1 = C0 + m * n;
+    uint32_t* status = (uint32_t*)((char*)C1 + (size_t)m * n * 8);
+    cudaMemsetAsync(Ad, 0x38, dig, st);
+    cudaMemsetAsync(E, 0, m * 4, st);
+    cudaMemsetAsync(F, 0, n * 4, st);
+    double t[2] = {0, 0};
+    for (int w = 0; w < 2; ++w) {
+        const int bnv = w ? 256 : 128;
+        CUtensorMap ma, mb;
+        tc_make_map(&ma, Ad, (uint64_t)s * m, (uint64_t)k, tc::BM);
+        tc_make_map(&mb, Bd, (uint64_t)s * n, (uint64_t)k, (uint32_t)bnv);
+        tc::Prob p;
+        memset(&p, 0, sizeof(p));
+        p.E = E; p.F = F; p.acc = acc; p.C[0] = C0; p.C[1] = C1;
+        p.m = m; p.n = n; p.mp = m; p.np = n; p.kp = k; p.ldc = m;
+        p.q = 2; p.s = s; p.beta = 4; p.ppd = (int)((1u << 24) / (k * 225)); p.acc_words = 3; p.bn = bnv;
+        tc::Sched sc;
+        memset(&sc, 0, sizeof(sc));
+        sc.ntiles = (int)((m / tc::BM) * (n / bnv));
+        tc_set_smem();
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        tc_launch(sc, p, ma, mb, status, sc.ntiles, st);   // warm-up
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; ++r) tc_launch(sc, p, ma, mb, status, sc.ntiles, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        // per (tile, pair, k-chunk) step; one CTA per tile runs concurrently
+        const double steps = (double)(s * (s + 1) / 2) * (k / tc::BK);
+        t[w] = ms / steps;
+    }
+    cudaFree(buf);
+    cudaGetLastError();
+    if (t[0] > 0 && t[1] > 0) { g_cost128 = t[0] / t[1]; g_cost256 = 1.0; }
+    if (env) {
+        FILE* f = fopen(env, "w");
+        if (f) { fprintf(f, "%.6f %.6f\n", g_cost128, g_cost256); fclose(f); }
+    }
+}
+
+void destroy_batch(Batch* b) {
+    if (!b) return;
+    if (b->launched) { cudaEventSynchronize(b->launched); cudaEventDestroy(b->launched); }
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->ws) cudaFree(b->ws);
+    if (b->meta) cudaFree(b->meta);
+    if (b->pinned) cudaFreeHost(b->pinned);
+    delete b;
+}
+
+}  // namespace
+
+namespace ozmp_batch {
+void destroy(void* b) { destroy_batch((Batch*)b); }
+}
+
+extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, ozmp_form form, ozmp_stream stream,
+                                         ozmp_plan* plan) {
+    if (!probs || count <= 0 || !plan) return OZMP_ERR_INVALID_ARG;
+    if (form < OZMP_FORM_AUTO || form > OZMP_FORM_FP8_MMA) return OZMP_ERR_INVALID_ARG;
+    const int fm = (form == OZMP_FORM_AUTO) ? OZMP_FORM_FP8 : form;
+    // argument checks of every problem
+    for (int i = 0; i < count; ++i) {
+        const ozmp_problem& r = probs[i];
+        int q = prec_q(r.prec);
+        if (!q || r.m < 0 || r.n < 0 || r.k < 0 || r.nslices < 0 || r.nslices > OZMP_MAX_SLICES)
+            return OZMP_ERR_INVALID_ARG;
+        if (r.lda < (r.m > 1 ? r.m : 1) || r.ldb < (r.k > 1 ? r.k : 1) || r.ldc < (r.m > 1 ? r.m : 1))
+            return OZMP_ERR_INVALID_ARG;
+        if (r.m > 0 && r.n > 0) {
+            if (!ptrs_ok(r.C, q)) return OZMP_ERR_INVALID_ARG;
+            if (r.k > 0 && (!ptrs_ok(r.A, q) || !ptrs_ok(r.B, q))) return OZMP_ERR_INVALID_ARG;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    ozmp_plan_s* P = *plan;
+    Batch* b = nullptr;
+    if (P) {
+        b = (Batch*)P->batch;
+        if (!b || b->count != count || b->form != fm) return OZMP_ERR_INVALID_ARG;
+        for (int i = 0; i < count; ++i) {
+            const ozmp_plan_s& s = b->subs[i];
+            if (s.prec != probs[i].prec || s.m != probs[i].m || s.n != probs[i].n || s.k != probs[i].k)
+                return OZMP_ERR_INVALID_ARG;
+        }
+    } else {
+        // ------------------------------------------------------------ build
+        if (fm == OZMP_FORM_FP8) calibrate_once(st);
+        b = new (std::nothrow) Batch;
+        if (!b) return OZMP_ERR_NOMEM;
+        b->count = count;
+        b->form = fm;
+        b->subs.resize(count);
+        b->ws_off.resize(count);
+        b->bn.resize(count, 256);
+        b->q.resize(count);
+        size_t off = 0;
+        for (int i = 0; i < count; ++i) {
+            const ozmp_problem& r = probs[i];
+            ozmp_plan_s& s = b->subs[i];
+            ozmp_status e = plan_init(&s, r.prec, r.m, r.n, r.k, fm, r.nslices, stream);
+            if (e != OZMP_OK) { destroy_batch(b); return e; }
+            b->q[i] = s.q;
+            if (fm == OZMP_FORM_FP8) {
+                // tile width: the cheaper of 128 / 256 columns under the measured step costs
+                const double t128 = (double)((r.n + 127) / 128) * g_cost128;
+                const double t256 = (double)((r.n + 255) / 256) * g_cost256;
+                b->bn[i] = (t128 < t256) ? 128 : 256;
+                s.np = roundup(r.n, b->bn[i]);
+                fill_layout(&s);
+            }
+            b->ws_off[i] = off;
+            off = a256(off + s.ws_bytes);
+        }
+        b->ws_bytes = off;
+        if (cudaMalloc(&b->ws, b->ws_bytes ? b->ws_bytes : 256) != cudaSuccess) {
+            cudaGetLastError();
+            destroy_batch(b);
+            return OZMP_ERR_NOMEM;
+        }
+        // groups by component type
+        for (int t = 0; t < 2; ++t) {
+            Group g;
+            g.is_f32 = t;
+            for (int i = 0; i < count; ++i)
+                if (b->subs[i].is_f32 == t && b->subs[i].m > 0 && b->subs[i].n > 0 && b->subs[i].k > 0) {
+                    g.ids.push_back(i);
+                    g.s_max = std::max(g.s_max, b->subs[i].s);
+                    if ((4 * b->subs[i].s + 65 + 63) / 64 > 4) g.nw = 6;
+                }
+            if (!g.ids.empty()) b->groups.push_back(g);
+        }
+        // items of the persistent product launch (FP8) and their balance
+        std::vector<int2> items;
+        std::vector<int> cta_off;
+        if (fm == OZMP_FORM_FP8) {
+            struct It { int p, tile; double cost; };
+            std::vector<It> all;
+            for (int i = 0; i < count; ++i) {
+                const ozmp_plan_s& s = b->subs[i];
+                if (s.m == 0 || s.n == 0 || s.k == 0) continue;
+                const int tiles = (int)((s.mp / tc::BM) * (s.np / b->bn[i]));
+                const double c = (double)(s.s * (s.s + 1) / 2) * (double)(s.kp / tc::BK) *
+                                 (b->bn[i] == 128 ? g_cost128 : g_cost256) + 4.0;
+                for (int t = 0; t < tiles; ++t) all.push_back({i, t, c});
+            }
+            std::stable_sort(all.begin(), all.end(), [](const It& x, const It& y) { return x.cost > y.cost; });
+            b->grid = (int)std::min<size_t>(all.size(), (size_t)tc_num_sms());
+            std::vector<std::vector<int2>> per(b->grid > 0 ? b->grid : 1);
+            typedef std::pair<double, int> Load;
+            std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+            for (int c = 0; c < b->grid; ++c) heap.push({0.0, c});
+            for (const It& x : all) {
+                Load l = heap.top();
+                heap.pop();
+                per[l.second].push_back(make_int2(x.p, x.tile));
+                heap.push({l.first + x.cost, l.second});
+            }
+            cta_off.push_back(0);
+            for (int c = 0; c < b->grid; ++c) {
+                for (const int2& w : per[c]) items.push_back(w);
+                cta_off.push_back((int)items.size());
+            }
+        }
+        // device meta layout
+        size_t mo = 0;
+        std::vector<std::vector<int>> pre_host;
+        for (Group& g : b->groups) {
+            g.off_split = mo;
+            mo = a256(mo + sizeof(BSplit) * g.ids.size());
+            for (int kx = 0; kx < 5; ++kx) {
+                g.off_pre[kx] = mo;
+                mo = a256(mo + sizeof(int) * (g.ids.size() + 1));
+            }
+        }
+        b->off_probs = mo; mo = a256(mo + sizeof(tc::Prob) * count);
+        b->off_maps = mo; mo = a256(mo + sizeof(CUtensorMap) * 2 * count);
+        b->off_items = mo; mo = a256(mo + sizeof(int2) * (items.size() + 1));
+        b->off_cta = mo; mo = a256(mo + sizeof(int) * (cta_off.size() + 1));
+        b->off_status = mo; mo = a256(mo + 16);
+        b->meta_bytes = mo;
+        if (cudaMalloc(&b->meta, b->meta_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            destroy_batch(b);
+            return OZMP_ERR_NOMEM;
+        }
+        // pinned mirror: the splits and probs (they carry the caller's pointers)
+        b->pinned_bytes = b->off_maps;
+        if (cudaMallocHost(&b->pinned, b->pinned_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            destroy_batch(b);
+            return OZMP_ERR_NOMEM;
+        }
+        memset(b->pinned, 0, b->pinned_bytes);
+        // prefix arrays, maps, items: uploaded once
+        std::vector<char> host(b->meta_bytes - b->off_maps, 0);
+        for (Group& g : b->groups) {
+            const int cnt = (int)g.ids.size();
+            std::vector<int> pre[5];
+            for (int kx = 0; kx < 5; ++kx) pre[kx].assign(cnt + 1, 0);
+            for (int x = 0; x < cnt; ++x) {
+                const ozmp_plan_s& s = b->subs[g.ids[x]];
+                const int nb[5] = {(int)((std::max(s.mp, s.np) + 255) / 256),
+                                   (int)(((s.m + 255) / 256) * ((s.k + 255) / 256)), (int)((s.n + 7) / 8),
+                                   (int)((s.mp / 32) * (s.kp / 64)), (int)(((s.kp / 4) * s.np + 255) / 256)};
+                for (int kx = 0; kx < 5; ++kx) pre[kx][x + 1] = pre[kx][x] + nb[kx];
+            }
+            for (int kx = 0; kx < 5; ++kx) {
+                g.blocks[kx] = pre[kx][cnt];
+                // prefix arrays live below off_maps: stage them in the pinned mirror too
+                memcpy((char*)b->pinned + g.off_pre[kx], pre[kx].data(), sizeof(int) * (cnt + 1));
+            }
+        }
+        CUtensorMap* maps = (CUtensorMap*)(host.data());
+        for (int i = 0; i < count; ++i) {
+            const ozmp_plan_s& s = b->subs[i];
+            if (fm != OZMP_FORM_FP8 || s.m == 0 || s.n == 0 || s.k == 0) continue;
+            char* w = (char*)b->ws + b->ws_off[i];
+            if (!tc_make_map(&maps[2 * i], w + s.off_Adig, (uint64_t)s.s * s.mp, (uint64_t)s.kp, tc::BM) ||
+                !tc_make_map(&maps[2 * i + 1], w + s.off_Bdig, (uint64_t)s.s * s.np, (uint64_t)s.kp,
+                             (uint32_t)b->bn[i])) {
+                destroy_batch(b);
+                return OZMP_ERR_CUDA;
+            }
+        }
+        memcpy(host.data() + (b->off_items - b->off_maps), items.data(), sizeof(int2) * items.size());
+        memcpy(host.data() + (b->off_cta - b->off_maps), cta_off.data(), sizeof(int) * cta_off.size());
+        if (cudaMemcpy((char*)b->meta + b->off_maps, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            destroy_batch(b);
+            return OZMP_ERR_CUDA;
+        }
+        // the plan object
+        P = new (std::nothrow) ozmp_plan_s;
+        if (!P) { destroy_batch(b); return OZMP_ERR_NOMEM; }
+        memset(P, 0, sizeof(*P));
+        P->form = fm;
+        P->ws = b->meta;
+        P->ws_owned = false;
+        P->off_status = b->off_status;
+        P->stream = st;
+        P->batch = b;
+    }
+
+    // ---------------------------------------------------------------- descriptors
+    // the previous replay must have read the pinned mirror before it is rewritten
+    if (b->launched) cudaEventSynchronize(b->launched);
+    else if (cudaEventCreateWithFlags(&b->launched, cudaEventDisableTiming) != cudaSuccess) return OZMP_ERR_CUDA;
+    for (Group& g : b->groups) {
+        BSplit* sp = (BSplit*)((char*)b->pinned + g.off_split);
+        for (size_t x = 0; x < g.ids.size(); ++x) {
+            const int i = g.ids[x];
+            const ozmp_problem& r = probs[i];
+            const ozmp_plan_s& s = b->subs[i];
+            char* w = (char*)b->ws + b->ws_off[i];
+            BSplit& d = sp[x];
+            for (int c = 0; c < 4; ++c) { d.A[c] = c < s.q ? r.A[c] : nullptr; d.B[c] = c < s.q ? r.B[c] : nullptr; }
+            d.lda = r.lda; d.ldb = r.ldb; d.m = s.m; d.n = s.n; d.k = s.k; d.mp = s.mp; d.np = s.np; d.kp = s.kp;
+            d.E = (int32_t*)(w + s.off_E); d.F = (int32_t*)(w + s.off_F);
+            d.Adig = (uint8_t*)(w + s.off_Adig); d.Bdig = (uint8_t*)(w + s.off_Bdig);
+            d.q = s.q; d.s = s.s;
+        }
+    }
+    tc::Prob* pr = (tc::Prob*)((char*)b->pinned + b->off_probs);
+    for (int i = 0; i < count; ++i) {
+        const ozmp_problem& r = probs[i];
+        const ozmp_plan_s& s = b->subs[i];
+        char* w = (char*)b->ws + b->ws_off[i];
+        tc::Prob& p = pr[i];
+        memset(&p, 0, sizeof(p));
+        p.E = (const int32_t*)(w + s.off_E); p.F = (const int32_t*)(w + s.off_F);
+        p.acc = (int64_t*)(w + s.off_acc);
+        for (int c = 0; c < 4; ++c) p.C[c] = c < s.q ? r.C[c] : nullptr;
+        p.m = s.m; p.n = s.n; p.mp = s.mp; p.np = s.np; p.kp = s.kp; p.ldc = r.ldc;
+        p.q = s.q; p.is_f32 = s.is_f32; p.s = s.s; p.beta = s.beta; p.ppd = s.ppd; p.acc_words = s.acc_words;
+        p.bn = b->bn[i];
+    }
+
+    // ---------------------------------------------------------------- graph
+    if (b->form != OZMP_FORM_FP8) {
+        // these forms bake the caller's pointers into the graph: re-capture when they change
+        std::vector<const void*> cur;
+        for (int i = 0; i < count; ++i)
+            for (int c = 0; c < b->q[i]; ++c) {
+                cur.push_back(probs[i].k > 0 ? probs[i].A[c] : nullptr);
+                cur.push_back(probs[i].k > 0 ? probs[i].B[c] : nullptr);
+                cur.push_back(probs[i].C[c]);
+            }
+        if (b->gexec && cur != b->baked) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+        b->baked = cur;
+    }
+    // problems with k = 0: C := 0 outside the graph
+    for (int i = 0; i < count; ++i) {
+        ozmp_plan_s s = b->subs[i];
+        if (s.m > 0 && s.n > 0 && s.k == 0) {
+            s.ws = (char*)b->ws + b->ws_off[i];
+            s.stream = st;
+            if (zero_c(&s, probs[i].C, probs[i].ldc) != OZMP_OK) return OZMP_ERR_CUDA;
+        }
+    }
+    if (!b->gexec && b->form == OZMP_FORM_FP8) {
+        for (Group& g : b->groups) {
+            const size_t sm = (size_t)g.s_max * 32 * 16 * 4;
+            if (g.is_f32) {
+                cudaFuncSetAttribute(k_b_split_rows<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                cudaFuncSetAttribute(k_b_split_rows<float, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            } else {
+                cudaFuncSetAttribute(k_b_split_rows<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                cudaFuncSetAttribute(k_b_split_rows<double, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            }
+        }
+        tc_set_smem();
+    }
+    if (!b->gexec) {
+        cudaStream_t cs = nullptr;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return OZMP_ERR_CUDA;
+        cudaGraph_t graph = nullptr;
+        bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        uint32_t* status = (uint32_t*)((char*)b->meta + b->off_status);
+        if (ok) {
+            // 1. the caller's pointers (read from the pinned mirror at every replay)
+            cudaMemcpyAsync(b->meta, b->pinned, b->pinned_bytes, cudaMemcpyHostToDevice, cs);
+            cudaMemsetAsync(status, 0, 16, cs);
+            if (b->form == OZMP_FORM_FP8) {
+                for (Group& g : b->groups) {
+                    const BSplit* sp = (const BSplit*)((char*)b->meta + g.off_split);
+                    const int* pre[5];
+                    for (int kx = 0; kx < 5; ++kx) pre[kx] = (const int*)((char*)b->meta + g.off_pre[kx]);
+                    const int cnt = (int)g.ids.size();
+                    k_b_init<<<g.blocks[0], 256, 0, cs>>>(sp, pre[0], cnt);
+                    const size_t sm = (size_t)g.s_max * 32 * 16 * 4;
+                    if (g.is_f32) {
+                        k_b_exp_rows<float><<<g.blocks[1], 256, 0, cs>>>(sp, pre[1], cnt, status);
+                        k_b_exp_cols<float><<<g.blocks[2], 256, 0, cs>>>(sp, pre[2], cnt, status);
+                        if (g.nw == 4) {
+                            k_b_split_rows<float, 4><<<g.blocks[3], 256, sm, cs>>>(sp, pre[3], cnt);
+                            k_b_split_cols<float, 4><<<g.blocks[4], 256, 0, cs>>>(sp, pre[4], cnt);
+                        } else {
+                            k_b_split_rows<float, 6><<<g.blocks[3], 256, sm, cs>>>(sp, pre[3], cnt);
+                            k_b_split_cols<float, 6><<<g.blocks[4], 256, 0, cs>>>(sp, pre[4], cnt);
+                        }
+                    } else {
+                        k_b_exp_rows<double><<<g.blocks[1], 256, 0, cs>>>(sp, pre[1], cnt, status);
+                        k_b_exp_cols<double><<<g.blocks[2], 256, 0, cs>>>(sp, pre[2], cnt, status);
+                        if (g.nw == 4) {
+                            k_b_split_rows<double, 4><<<g.blocks[3], 256, sm, cs>>>(sp, pre[3], cnt);
+                            k_b_split_cols<double, 4><<<g.blocks[4], 256, 0, cs>>>(sp, pre[4], cnt);
+                        } else {
+                            k_b_split_rows<double, 6><<<g.blocks[3], 256, sm, cs>>>(sp, pre[3], cnt);
+                            k_b_split_cols<double, 6><<<g.blocks[4], 256, 0, cs>>>(sp, pre[4], cnt);
+                        }
+                    }
+                }
+                if (b->grid > 0) {
+                    tc::Sched sc;
+                    sc.probs = (const tc::Prob*)((char*)b->meta + b->off_probs);
+                    sc.maps = (const CUtensorMap*)((char*)b->meta + b->off_maps);
+                    sc.items = (const int2*)((char*)b->meta + b->off_items);
+                    sc.off = (const int*)((char*)b->meta + b->off_cta);
+                    sc.ntiles = 0;
+                    tc::Prob dummy;
+                    memset(&dummy, 0, sizeof(dummy));
+                    CUtensorMap m0;
+                    memset(&m0, 0, sizeof(m0));
+                    tc_launch(sc, dummy, m0, m0, status, b->grid, cs);
+                }
+            } else {
+                // other forms: the problems one after another inside the graph
+                for (int i = 0; i < count; ++i) {
+                    ozmp_plan_s s = b->subs[i];
+                    if (s.m == 0 || s.n == 0) continue;
+                    s.ws = (char*)b->ws + b->ws_off[i];
+                    s.stream = cs;
+                    const ozmp_problem& r = probs[i];
+                    if (s.k == 0) continue;
+                    SplitArgs sa = split_args(&s, r.A, r.lda, r.B, r.ldb);
+                    sa.status = status;
+                    launch_split(sa, cs);
+                    GemmArgs g = gemm_args(&s);
+                    for (int c = 0; c < 4; ++c) g.C[c] = (c < s.q) ? r.C[c] : nullptr;
+                    g.ldc = r.ldc;
+                    g.status = status;
+                    launch_gemm(g, cs);
+                }
+            }
+        }
+        cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+        ok = ok && ce == cudaSuccess && graph;
+        if (ok && cudaGraphInstantiate(&b->gexec, graph, 0) != cudaSuccess) ok = false;
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        if (!ok) {
+            cudaGetLastError();
+            if (!*plan) { P->batch = nullptr; delete P; destroy_batch(b); }
+            return OZMP_ERR_CUDA;
+        }
+    }
+    P->stream = st;
+    *plan = P;
+    if (cudaGraphLaunch(b->gexec, st) != cudaSuccess) return OZMP_ERR_CUDA;
+    if (cudaEventRecord(b->launched, st) != cudaSuccess) return OZMP_ERR_CUDA;
+    return OZMP_OK;
+}

@@ -1,0 +1,280 @@
+// Slice-pair products on the 5th-generation tensor cores (tcgen05), e4m3
+// digits, binary32 accumulation in tensor memory -- the GB300-native form of
+// the e4m3 engine.  Shared by the single-problem launch (gemm_tc.cu) and the
+// persistent batched launch (batched.cu).
+//
+// Paper, Sec. 3, Algorithm 1: C_{alpha beta} := A_alpha B_beta over the pair
+// triangle, then the L-bit sum.  One CTA owns a 128 x 256 tile of C and walks
+// the triangle by anti-diagonal d = s+1 .. 2 exactly as the mma.sync kernels.
+//
+// Roles (192 threads):
+//   warp 0      TMA producer: 128x128-byte A tile + 256x128-byte B tile per
+//               stage (SWIZZLE_128B), 4 stages, mbarrier full/empty ring;
+//   warp 1      TMEM owner (512 columns) and MMA issuer: per stage four
+//               tcgen05.mma.kind::f8f6f4 (M=128, N=256, K=32) into one of two
+//               256-column binary32 accumulators;
+//   warps 2..5  epilogue: per drain, tcgen05.ld the accumulator (integers
+//               below 2^24, exact), convert, and add v * 2^off into ONE int64
+//               carry-save limb per element (limb l weighs 2^(16 l), off < 16,
+//               so each limb stays below 2^48 for every k the form allows); the
+//               last drain normalises the limbs to a two's complement integer
+//               and rounds it canonically into the q output components.
+// The two accumulator buffers let the MMAs of the next pairs run while the
+// epilogue drains the previous ones.  Every wait is bounded: on timeout the
+// kernel records OZMP_ERR_TIMEOUT in the status word, all roles leave their
+// loops, and the TMEM is released before returning.
+#pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include "kernels.h"
+#include "ozmp_internal.cuh"
+
+namespace ozmp {
+namespace tc {
+
+constexpr int BM = 128, BN = 256, BK = 128, NST = 4, NT = 192;   // BN: widest tile
+constexpr unsigned STAGE_A = BM * BK, STAGE_B = BN * BK;
+constexpr unsigned TX_BYTES = STAGE_A + STAGE_B;
+constexpr size_t SMEM = 1024 + (size_t)NST * (STAGE_A + STAGE_B) + 256;
+constexpr long long WAIT_LIMIT = 1ll << 26;   // try_wait polls before giving up (seconds)
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(saddr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(saddr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(saddr(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(saddr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for the phase of parity `parity`; false on timeout or abort
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, volatile int* abort_flag) {
+    for (long long it = 0; it < WAIT_LIMIT; ++it) {
+        if (mbar_try(b, parity)) return true;
+        if ((it & 255) == 255 && *abort_flag) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];\n" ::"r"(
+            saddr(dst)),
+        "l"((uint64_t)map), "r"(saddr(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// shared memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
+// 1024 bytes (stride byte offset), version bits 46-48 = 0b001
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t smem) {
+    uint64_t d = 0;
+    d |= (uint64_t)((smem & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                 // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024u >> 4) << 32;      // stride byte offset
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+    return d;
+}
+
+// instruction descriptor, kind::f8f6f4: D = f32, A = B = e4m3, both K-major
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_e4m3_tc(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(saddr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+// walk of the pair triangle shared by the three roles
+struct Walk {
+    int d, t;
+    __device__ __forceinline__ bool next_pair() {   // advance; false when past the end
+        if (++t == d) { --d; t = 1; }
+        return true;
+    }
+};
+
+// Limb accumulator of one element: NL int64 limbs, limb l weighs 2^(16 l),
+// layout [l][np][mp] (consecutive rows contiguous).  `zero` skips the load
+// (first and last drain of a tile coincide).
+template <int NW>
+__device__ __forceinline__ void finish_element(const GemmArgs& g, int nl, int64_t i, int64_t j, int64_t x, int li,
+                                               bool zero) {
+    const size_t plane = (size_t)g.mp * g.np;
+    const size_t idx = (size_t)j * g.mp + i;
+    constexpr int NLMAX = 4 * NW + 1;
+    int64_t L[NLMAX];
+#pragma unroll
+    for (int l = 0; l < NLMAX; ++l) L[l] = (!zero && l < nl) ? g.acc[l * plane + idx] : 0;
+#pragma unroll
+    for (int l = 0; l < NLMAX; ++l)
+        if (l == li) L[l] += x;
+    // carry-save limbs -> two's complement words (the value fits 64 NW bits)
+    uint64_t w[NW];
+#pragma unroll
+    for (int x2 = 0; x2 < NW; ++x2) w[x2] = 0;
+    int64_t carry = 0;
+#pragma unroll
+    for (int l = 0; l < 4 * NW; ++l) {
+        int64_t t = L[l] + carry;                 // |L| < 2^48, |carry| < 2^48
+        w[l >> 2] |= ((uint64_t)t & 0xffffull) << (16 * (l & 3));
+        carry = t >> 16;                           // arithmetic shift: floor division
+    }
+    if (i >= g.m || j >= g.n) return;
+    if (g.d_only) {
+        g.T[i + j * g.m] = (int64_t)w[0];
+        return;
+    }
+    int Ei = g.E[i], Fj = g.F[j];
+    bool ok = true;
+    if (g.is_f32) {
+        float out[4] = {0.f, 0.f, 0.f, 0.f};
+        if (Ei != OZMP_EXP_ZERO && Fj != OZMP_EXP_ZERO)
+            ok = canonical_round<NW, float>(w, Ei + Fj - g.beta * (g.s + 1), g.q, out);
+        for (int c = 0; c < g.q; ++c) ((float*)g.C[c])[i + j * g.ldc] = out[c];
+    } else {
+        double out[4] = {0.0, 0.0, 0.0, 0.0};
+        if (Ei != OZMP_EXP_ZERO && Fj != OZMP_EXP_ZERO)
+            ok = canonical_round<NW, double>(w, Ei + Fj - g.beta * (g.s + 1), g.q, out);
+        for (int c = 0; c < g.q; ++c) ((double*)g.C[c])[i + j * g.ldc] = out[c];
+    }
+    if (!ok) atomicOr(g.status, ST_RANGE);
+}
+
+__device__ __forceinline__ void finish_dispatch(const GemmArgs& g, int nl, int64_t i, int64_t j, int64_t x, int li,
+                                                bool zero) {
+    switch (g.acc_words) {
+        case 2: finish_element<2>(g, nl, i, j, x, li, zero); break;
+        case 3: finish_element<3>(g, nl, i, j, x, li, zero); break;
+        case 4: finish_element<4>(g, nl, i, j, x, li, zero); break;
+        case 5: finish_element<5>(g, nl, i, j, x, li, zero); break;
+        case 6: finish_element<6>(g, nl, i, j, x, li, zero); break;
+        default: finish_element<7>(g, nl, i, j, x, li, zero); break;
+    }
+}
+
+
+// One problem of a launch.  The tensor maps are those of the problem's digit
+// arrays (box 128 x 128 bytes for A, bn x 128 bytes for B).
+struct Prob {
+    const int32_t* E;
+    const int32_t* F;
+    int64_t* acc;          // [nlimbs][np][mp] carry-save limbs
+    void* C[4];
+    int64_t* T;            // diagnostic output (d_only)
+    int64_t m, n, mp, np, kp, ldc;
+    int q, is_f32, s, beta, ppd, acc_words, bn, d_only;
+};
+
+// adapter: the fields of one problem the limb epilogue reads, in GemmArgs form
+__device__ __forceinline__ GemmArgs as_gemm_args(const Prob& p, uint32_t* status) {
+    GemmArgs g;
+    g.form = OZMP_FORM_FP8;
+    g.q = p.q;
+    g.is_f32 = p.is_f32;
+    g.m = p.m; g.n = p.n; g.k = 0; g.mp = p.mp; g.np = p.np; g.kp = p.kp;
+    g.E = p.E; g.F = p.F; g.Adig = nullptr; g.Bdig = nullptr;
+    g.s = p.s; g.beta = p.beta; g.ppd = p.ppd; g.group_start = 0; g.acc_words = p.acc_words; g.ngroups = 0;
+    g.acc = p.acc;
+    for (int c = 0; c < 4; ++c) g.C[c] = p.C[c];
+    g.ldc = p.ldc;
+    g.status = status;
+    g.d_only = p.d_only;
+    g.T = p.T;
+    return g;
+}
+
+// Work of one CTA: items [off[cta], off[cta + 1]) of `items` (prob, tile);
+// without an item list (single problem) tiles cta, cta + G, cta + 2G, ...
+struct Sched {
+    const Prob* probs;         // batched mode: one per problem (global memory)
+    const CUtensorMap* maps;   // batched mode: A and B maps of problem p at 2p, 2p + 1
+    const int2* items;
+    const int* off;
+    int ntiles;                // single-problem mode: tiles of the one problem
+};
+
+struct Item {
+    const Prob* p;
+    const CUtensorMap* ma;
+    const CUtensorMap* mb;
+    int64_t i0, j0;
+    int KT, dhi, dlo, bn;
+};
+
+__device__ __forceinline__ bool item_at(const Sched& sc, const Prob* single, const CUtensorMap* ma,
+                                        const CUtensorMap* mb, int idx, Item& it) {
+    int pi, tile;
+    if (sc.items) {
+        const int2 w = sc.items[idx];
+        pi = w.x;
+        tile = w.y;
+        it.p = &sc.probs[pi];
+        it.ma = &sc.maps[2 * pi];
+        it.mb = &sc.maps[2 * pi + 1];
+    } else {
+        tile = idx;
+        it.p = single;
+        it.ma = ma;
+        it.mb = mb;
+    }
+    const Prob& p = *it.p;
+    const int tm = (int)(p.mp / BM);
+    it.i0 = (int64_t)(tile % tm) * BM;
+    it.j0 = (int64_t)(tile / tm) * p.bn;
+    it.KT = (int)(p.kp / BK);
+    it.dhi = p.d_only ? p.d_only : p.s + 1;
+    it.dlo = p.d_only ? p.d_only : 2;
+    it.bn = p.bn;
+    return true;
+}
+
+}  // namespace tc
+
+// host helpers shared by the launches (gemm_tc.cu)
+bool tc_make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t kp, uint32_t box_rows);
+int tc_num_sms();
+// launch of the tcgen05 product kernel: `grid` CTAs over the schedule; in
+// single-problem mode (sc.items == nullptr) `single`, `ma`, `mb` describe it
+cudaError_t tc_launch(const tc::Sched& sc, const tc::Prob& single, const CUtensorMap& ma, const CUtensorMap& mb,
+                      uint32_t* status, int grid, cudaStream_t st);
+cudaError_t tc_set_smem();
+
+}  // namespace ozmp

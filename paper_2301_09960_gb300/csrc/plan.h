@@ -19,7 +19,12 @@ struct ozmp_plan_s {
     void* ws;
     bool ws_owned;
     cudaStream_t stream;
+    void* batch;   // batched plan data (ozmp_gemm_batched), else null
 };
+
+namespace ozmp_batch {
+void destroy(void* b);
+}
 
 namespace ozmp_plan_detail {
 using namespace ozmp;

@@ -40,11 +40,11 @@ __device__ __forceinline__ bool load_elem(const Operand<T>& op, int64_t idx, T (
 // rows of a column-major m x k matrix: one thread per row, a chunk of
 // columns per block row; consecutive threads read consecutive addresses.
 template <typename T>
-__global__ void __launch_bounds__(256) k_exp_rows(Operand<T> a, int64_t m, int64_t k, int kchunk, int32_t* E,
-                                                  uint32_t* status) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void exp_rows_body(Operand<T> a, int64_t m, int64_t k, int kchunk, int32_t* E,
+                                                  uint32_t* status, int64_t bx, int64_t by) {
+    int64_t i = bx * blockDim.x + threadIdx.x;
     if (i >= m) return;
-    int64_t p0 = (int64_t)blockIdx.y * kchunk;
+    int64_t p0 = by * kchunk;
     int64_t p1 = p0 + kchunk < k ? p0 + kchunk : k;
     int emax = OZMP_EXP_ZERO;
     bool ok = true;
@@ -60,12 +60,18 @@ __global__ void __launch_bounds__(256) k_exp_rows(Operand<T> a, int64_t m, int64
     if (!ok) atomicOr(status, ST_NONFINITE);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_exp_rows(Operand<T> a, int64_t m, int64_t k, int kchunk, int32_t* E,
+                                                  uint32_t* status) {
+    exp_rows_body(a, m, k, kchunk, E, status, (int64_t)blockIdx.x, (int64_t)blockIdx.y);
+}
+
 // columns of a column-major k x n matrix (contiguous): one warp per column,
 // warp-shuffle max reduction.
 template <typename T>
-__global__ void __launch_bounds__(256) k_exp_cols(Operand<T> b, int64_t k, int64_t n, int32_t* F, uint32_t* status) {
+__device__ __forceinline__ void exp_cols_body(Operand<T> b, int64_t k, int64_t n, int32_t* F, uint32_t* status, int64_t bx, int64_t by) {
     int warps = blockDim.x >> 5;
-    int64_t j = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5);
+    int64_t j = bx * warps + (threadIdx.x >> 5);
     int lane = threadIdx.x & 31;
     if (j >= n) return;
     int emax = OZMP_EXP_ZERO;
@@ -88,6 +94,11 @@ __global__ void __launch_bounds__(256) k_exp_cols(Operand<T> b, int64_t k, int64
         F[j] = emax;
         if (bad) atomicOr(status, ST_NONFINITE);
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_exp_cols(Operand<T> b, int64_t k, int64_t n, int32_t* F, uint32_t* status) {
+    exp_cols_body(b, k, n, F, status, (int64_t)blockIdx.x, (int64_t)blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -133,11 +144,11 @@ __device__ __forceinline__ int window_of(const Operand<T>& op, bool inside, int6
 // a slice go to shared memory as one word [t][ri][quad], then the tile is
 // written K-contiguous.
 template <typename T, int FORM, int NW>
-__global__ void __launch_bounds__(256) k_split_rows_b1(Operand<T> a, int64_t m, int64_t k, const int32_t* E,
-                                                       uint8_t* dig, int64_t mp, int64_t kp, int s) {
+__device__ __forceinline__ void split_rows_b1_body(Operand<T> a, int64_t m, int64_t k, const int32_t* E,
+                                                       uint8_t* dig, int64_t mp, int64_t kp, int s, int64_t bx, int64_t by) {
     constexpr int TI = 32, TP = 64, QW = TP / 4;    // 16 words per tile row
     extern __shared__ __align__(16) uint32_t sw[];  // [s][TI][QW]
-    const int64_t i0 = (int64_t)blockIdx.x * TI, p0 = (int64_t)blockIdx.y * TP;
+    const int64_t i0 = bx * TI, p0 = by * TP;
     const int ri = threadIdx.x & 31;
     const int64_t i = i0 + ri;
     const int Erow = (i < m) ? E[i] : OZMP_EXP_ZERO;
@@ -163,13 +174,19 @@ __global__ void __launch_bounds__(256) k_split_rows_b1(Operand<T> a, int64_t m, 
     }
 }
 
+template <typename T, int FORM, int NW>
+__global__ void __launch_bounds__(256) k_split_rows_b1(Operand<T> a, int64_t m, int64_t k, const int32_t* E,
+                                                       uint8_t* dig, int64_t mp, int64_t kp, int s) {
+    split_rows_b1_body<T, FORM, NW>(a, m, k, E, dig, mp, kp, s, (int64_t)blockIdx.x, (int64_t)blockIdx.y);
+}
+
 // Columns of B (contiguous along k) -> Bdig[(t * np + j) * kp + p], 1-byte
 // digits: 4 consecutive k per thread, one 32-bit store per slice.
 template <typename T, int FORM, int NW>
-__global__ void __launch_bounds__(256) k_split_cols_b1(Operand<T> b, int64_t k, int64_t n, const int32_t* F,
-                                                       uint8_t* dig, int64_t np, int64_t kp, int s) {
+__device__ __forceinline__ void split_cols_b1_body(Operand<T> b, int64_t k, int64_t n, const int32_t* F,
+                                                       uint8_t* dig, int64_t np, int64_t kp, int s, int64_t bx, int64_t by) {
     const int64_t quads = kp / 4;
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t g = bx * blockDim.x + threadIdx.x;
     if (g >= quads * np) return;
     const int64_t j = g / quads;
     const int64_t p0 = (g % quads) * 4;
@@ -185,6 +202,12 @@ __global__ void __launch_bounds__(256) k_split_cols_b1(Operand<T> b, int64_t k, 
     for (int t = 1; t <= DigitTraits<FORM>::MAXS; ++t)
         if (t <= s)
             *reinterpret_cast<uint32_t*>(dig + ((size_t)(t - 1) * np + j) * kp + p0) = pack4<FORM, NW>(w, sign, t);
+}
+
+template <typename T, int FORM, int NW>
+__global__ void __launch_bounds__(256) k_split_cols_b1(Operand<T> b, int64_t k, int64_t n, const int32_t* F,
+                                                       uint8_t* dig, int64_t np, int64_t kp, int s) {
+    split_cols_b1_body<T, FORM, NW>(b, k, n, F, dig, np, kp, s, (int64_t)blockIdx.x, (int64_t)blockIdx.y);
 }
 
 // binary64 digits, rows of A: 16 x 16 tile staged in shared memory

@@ -1,0 +1,78 @@
+"""Batched products (ozmp_gemm_batched) against single products.
+
+Every product is exact up to one canonical rounding, so a batched result
+must equal the single-problem result bit for bit, whatever tile widths the
+autotuner chose and however the persistent schedule ordered the tiles.  A
+second call reuses the plan with new data and new pointers.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2301_09960_gb300 as oz
+from ozmp_inputs import batched_problem_shapes, gen_problem
+
+from _util import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _make(shapes, seed0):
+    out = []
+    for idx, (m, n, k, prec) in enumerate(shapes):
+        A, B = gen_problem(prec, m, n, k, phi=1.0, seed=seed0 + idx)
+        dt = torch.float32 if prec == "ts" else torch.float64
+        q = len(A)
+        C = [torch.full((n, m), 7.0, dtype=dt, device="cuda").T for _ in range(q)]
+        out.append((prec, to_dev(A) if k > 0 else [oz.colmajor(np.zeros((m, 0)))] * q,
+                    to_dev(B) if k > 0 else [oz.colmajor(np.zeros((0, n)))] * q, C, 0))
+    return out
+
+
+def _single(prec, A, B, form):
+    C, p = oz.gemm(A, B, prec, form, 0)
+    return C
+
+
+@pytest.mark.parametrize("form", ["fp8", "int8"])
+def test_batched_equals_single_products(form):
+    shapes = batched_problem_shapes(24, seed=1, lo=16, hi=300)
+    shapes += [(70, 40, 0, "dd"), (0, 5, 9, "td"), (33, 290, 45, "qd"), (130, 260, 70, "ts"), (1, 1, 1, "dd")]
+    probs = _make(shapes, 1000)
+    plan = oz.ozmp_gemm_batched(probs, oz.FORM_BY_NAME[form])
+    torch.cuda.synchronize()
+    assert oz.ozmp_plan_get_status(plan) == oz.Status.OK
+    for (prec, A, B, C, ns), (m, n, k, _) in zip(probs, shapes):
+        if m == 0 or n == 0:
+            continue
+        if k == 0:
+            assert all(float(c.abs().max()) == 0.0 for c in C)
+            continue
+        ref = _single(prec, A, B, form)
+        for x, y in zip(C, ref):
+            assert torch.equal(x, y), (prec, m, n, k)
+    # replay with new data and new pointers
+    probs2 = _make(shapes, 5000)
+    plan2 = oz.ozmp_gemm_batched(probs2, oz.FORM_BY_NAME[form], plan=plan)
+    torch.cuda.synchronize()
+    for (prec, A, B, C, ns), (m, n, k, _) in zip(probs2, shapes):
+        if m == 0 or n == 0 or k == 0:
+            continue
+        ref = _single(prec, A, B, form)
+        for x, y in zip(C, ref):
+            assert torch.equal(x, y), (prec, m, n, k)
+    oz.ozmp_plan_destroy(plan)
+
+
+def test_batched_plan_rejects_a_different_batch():
+    shapes = [(40, 30, 20, "dd"), (20, 30, 40, "td")]
+    probs = _make(shapes, 7)
+    plan = oz.ozmp_gemm_batched(probs)
+    other = _make([(41, 30, 20, "dd"), (20, 30, 40, "td")], 8)
+    with pytest.raises(oz.OzmpError) as e:
+        oz.ozmp_gemm_batched(other, plan=plan)
+    assert e.value.status == oz.Status.ERR_INVALID_ARG
+    oz.ozmp_plan_destroy(plan)
