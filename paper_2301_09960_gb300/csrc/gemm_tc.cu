@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
             for (int idx = it_begin; ok && idx < it_end; idx += it_step) {
                 Item it;
                 item_at(sc, &single, &tmA, &tmB, idx, it);
-                const Prob& p = *it.p;
+                const Prob p = *it.p;
                 const unsigned tx = STAGE_A + (unsigned)it.bn * BK;
                 Walk w{it.dhi, 1};
                 while (ok && w.d >= it.dlo) {
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
             for (int idx = it_begin; ok && idx < it_end; idx += it_step) {
                 Item it;
                 item_at(sc, &single, &tmA, &tmB, idx, it);
-                const Prob& p = *it.p;
+                const Prob p = *it.p;
                 const uint32_t idesc = idesc_e4m3(BM, it.bn);
                 Walk w{it.dhi, 1};
                 int since = 0;
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
         for (int idx = it_begin; ok && idx < it_end; idx += it_step) {
             Item it;
             item_at(sc, &single, &tmA, &tmB, idx, it);
-            const Prob& p = *it.p;
+            const Prob p = *it.p;
             const GemmArgs g = as_gemm_args(p, status);
             const int64_t i = it.i0 + quarter * 32 + lane;
             const size_t plane = (size_t)p.mp * p.np;
