@@ -24,7 +24,8 @@ ozmp_status ozmp_plan_create(ozmp_plan* plan, ozmp_prec prec, int64_t m, int64_t
     ozmp_plan_s* p = new (std::nothrow) ozmp_plan_s;
     if (!p) return OZMP_ERR_NOMEM;
     ozmp_status st = plan_init(p, prec, m, n, k, form, nslices, stream);
-    if (st != OZMP_OK) { delete p; return st; }
+    if (st == OZMP_OK) st = plan_schedule(p);
+    if (st != OZMP_OK) { delete[] p->sched_host; delete p; return st; }
     *plan = p;
     return OZMP_OK;
 }
@@ -41,6 +42,7 @@ ozmp_status ozmp_plan_destroy(ozmp_plan p) {
         cudaStreamSynchronize(p->stream);
         cudaFree(p->ws);
     }
+    delete[] p->sched_host;
     delete p;
     return OZMP_OK;
 }
@@ -101,6 +103,7 @@ ozmp_status ozmp_plan_execute(ozmp_plan p, const void* const* A, int64_t lda, co
     if (p->k == 0) return zero_c(p, C, ldc);
     SplitArgs a = split_args(p, A, lda, B, ldb);
     if (launch_split(a, p->stream) != cudaSuccess) return OZMP_ERR_CUDA;
+    if (plan_upload_schedule(p) != OZMP_OK) return OZMP_ERR_CUDA;
     GemmArgs g = gemm_args(p);
     for (int c = 0; c < 4; ++c) g.C[c] = (c < p->q) ? C[c] : nullptr;
     g.ldc = ldc;
@@ -114,6 +117,7 @@ ozmp_status ozmp_plan_multiply(ozmp_plan p, void* const* C, int64_t ldc) {
     if (p->m == 0 || p->n == 0) return OZMP_OK;
     if (!ptrs_ok(C, p->q)) return OZMP_ERR_INVALID_ARG;
     if (p->k == 0) return zero_c(p, C, ldc);
+    if (plan_upload_schedule(p) != OZMP_OK) return OZMP_ERR_CUDA;
     GemmArgs g = gemm_args(p);
     for (int c = 0; c < 4; ++c) g.C[c] = (c < p->q) ? C[c] : nullptr;
     g.ldc = ldc;
@@ -126,6 +130,7 @@ ozmp_status ozmp_plan_diagonal(ozmp_plan p, int d, int64_t* T) {
     GemmArgs g = gemm_args(p);
     g.d_only = d;
     g.T = T;
+    g.sched_items = nullptr;   // the diagnostic walks one diagonal, one whole tile per CTA
     return launch_gemm(g, p->stream) == cudaSuccess ? OZMP_OK : OZMP_ERR_CUDA;
 }
 

@@ -320,7 +320,7 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
             if (!g.ids.empty()) b->groups.push_back(g);
         }
         // items of the persistent product launch (FP8) and their balance
-        std::vector<int2> items;
+        std::vector<tc::WorkItem> items;
         std::vector<int> cta_off;
         if (fm == OZMP_FORM_FP8) {
             struct It { int p, tile; double cost; };
@@ -335,19 +335,20 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
             }
             std::stable_sort(all.begin(), all.end(), [](const It& x, const It& y) { return x.cost > y.cost; });
             b->grid = (int)std::min<size_t>(all.size(), (size_t)tc_num_sms());
-            std::vector<std::vector<int2>> per(b->grid > 0 ? b->grid : 1);
+            std::vector<std::vector<tc::WorkItem>> per(b->grid > 0 ? b->grid : 1);
             typedef std::pair<double, int> Load;
             std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
             for (int c = 0; c < b->grid; ++c) heap.push({0.0, c});
             for (const It& x : all) {
                 Load l = heap.top();
                 heap.pop();
-                per[l.second].push_back(make_int2(x.p, x.tile));
+                const ozmp_plan_s& sx = b->subs[x.p];
+                per[l.second].push_back(tc::WorkItem{x.p, x.tile, 0, sx.s * (sx.s + 1) / 2, -1, 1});
                 heap.push({l.first + x.cost, l.second});
             }
             cta_off.push_back(0);
             for (int c = 0; c < b->grid; ++c) {
-                for (const int2& w : per[c]) items.push_back(w);
+                for (const tc::WorkItem& w : per[c]) items.push_back(w);
                 cta_off.push_back((int)items.size());
             }
         }
@@ -364,7 +365,7 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
         }
         b->off_probs = mo; mo = a256(mo + sizeof(tc::Prob) * count);
         b->off_maps = mo; mo = a256(mo + sizeof(CUtensorMap) * 2 * count);
-        b->off_items = mo; mo = a256(mo + sizeof(int2) * (items.size() + 1));
+        b->off_items = mo; mo = a256(mo + sizeof(tc::WorkItem) * (items.size() + 1));
         b->off_cta = mo; mo = a256(mo + sizeof(int) * (cta_off.size() + 1));
         b->off_status = mo; mo = a256(mo + 16);
         b->meta_bytes = mo;
@@ -412,7 +413,7 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
                 return OZMP_ERR_CUDA;
             }
         }
-        memcpy(host.data() + (b->off_items - b->off_maps), items.data(), sizeof(int2) * items.size());
+        memcpy(host.data() + (b->off_items - b->off_maps), items.data(), sizeof(tc::WorkItem) * items.size());
         memcpy(host.data() + (b->off_cta - b->off_maps), cta_off.data(), sizeof(int) * cta_off.size());
         if (cudaMemcpy((char*)b->meta + b->off_maps, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
             destroy_batch(b);
@@ -543,7 +544,7 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
                     tc::Sched sc;
                     sc.probs = (const tc::Prob*)((char*)b->meta + b->off_probs);
                     sc.maps = (const CUtensorMap*)((char*)b->meta + b->off_maps);
-                    sc.items = (const int2*)((char*)b->meta + b->off_items);
+                    sc.items = (const tc::WorkItem*)((char*)b->meta + b->off_items);
                     sc.off = (const int*)((char*)b->meta + b->off_cta);
                     sc.ntiles = 0;
                     tc::Prob dummy;

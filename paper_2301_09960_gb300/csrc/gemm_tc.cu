@@ -1,5 +1,6 @@
 // Single-problem launch of the tcgen05 e4m3 slice-product kernel (the
 // kernel itself is in gemm_tc_impl.cuh) and the tensor-map helpers.
+#include <vector>
 #include "gemm_tc_impl.cuh"
 
 namespace ozmp {
@@ -19,6 +20,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
     uint64_t* done = acce + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    volatile int* fin_flag = reinterpret_cast<volatile int*>(tmem_slot + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -54,8 +56,8 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                 item_at(sc, &single, &tmA, &tmB, idx, it);
                 const Prob p = *it.p;
                 const unsigned tx = STAGE_A + (unsigned)it.bn * BK;
-                Walk w{it.dhi, 1};
-                while (ok && w.d >= it.dlo) {
+                Walk w = Walk::at(it.dhi, it.pa);
+                for (int pi = it.pa; ok && pi < it.pb; ++pi) {
                     const int u = w.d - w.t;
                     const int ya = (w.t - 1) * (int)p.mp + (int)it.i0;
                     const int yb = (u - 1) * (int)p.np + (int)it.j0;
@@ -90,10 +92,10 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                 item_at(sc, &single, &tmA, &tmB, idx, it);
                 const Prob p = *it.p;
                 const uint32_t idesc = idesc_e4m3(BM, it.bn);
-                Walk w{it.dhi, 1};
+                Walk w = Walk::at(it.dhi, it.pa);
                 int since = 0;
                 bool fresh = true;
-                while (ok && w.d >= it.dlo) {
+                for (int pi = it.pa; ok && pi < it.pb; ++pi) {
                     const uint32_t dcol = tmem + (uint32_t)(buf * BN);
                     for (int kc = 0; kc < it.KT; ++kc, ++n) {
                         const int st = (int)(n % NST);
@@ -113,7 +115,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                     if (!ok) break;
                     ++since;
                     const bool diag_end = (w.t == w.d - 1);
-                    if (since == p.ppd || diag_end) {
+                    if (since == p.ppd || diag_end || pi == it.pb - 1) {
                         mma_commit(&accf[buf]);
                         uses[buf]++;
                         buf ^= 1;
@@ -143,17 +145,22 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
             const Prob p = *it.p;
             const GemmArgs g = as_gemm_args(p, status);
             const int64_t i = it.i0 + quarter * 32 + lane;
+            const int ii = quarter * 32 + lane;
             const size_t plane = (size_t)p.mp * p.np;
             const int nl = 4 * p.acc_words + 1;
-            Walk w{it.dhi, 1};
+            const bool split = it.slot >= 0;
+            // split tiles: limb l of tile column jj, row ii at sbase[l * sstride + jj * BM + ii]
+            const size_t sstride = (size_t)it.bn * BM;
+            int64_t* sbase = split ? p.sacc + (size_t)it.slot * nl * sstride : nullptr;
+            Walk w = Walk::at(it.dhi, it.pa);
             int since = 0;
-            bool first = true;
-            while (ok && w.d >= it.dlo) {
+            int top_li = -1;   // highest limb stored so far for this tile (whole tiles)
+            for (int pi = it.pa; ok && pi < it.pb; ++pi) {
                 ++since;
                 const bool diag_end = (w.t == w.d - 1);
-                if (since == p.ppd || diag_end) {
+                if (since == p.ppd || diag_end || pi == it.pb - 1) {
                     since = 0;
-                    const bool last = diag_end && (w.d == it.dlo);
+                    const bool last = (pi == it.pb - 1);
                     const int buf = ev & 1;
                     const unsigned par = (unsigned)((ev >> 1) & 1);
                     ++ev;
@@ -173,19 +180,29 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                             if (lane == 0) mbar_arrive(&acce[buf]);
                         }
                         const int64_t jb = it.j0 + c * 32;
-                        if (last) {
+                        if (split) {
+                            // exact, order-independent: add into the tile's shared limbs
+                            unsigned long long* lp = (unsigned long long*)(sbase + li * sstride + (size_t)(c * 32) * BM + ii);
+#pragma unroll
+                            for (int x = 0; x < 32; ++x) {
+                                const int64_t v = (int64_t)__float2int_rn(__uint_as_float(r[x]));
+                                atomicAdd(lp + (size_t)x * BM, (unsigned long long)((uint64_t)v << off));
+                            }
+                        } else if (last) {
+                            // limbs 0 .. top_li hold data; li may open one more (li == top_li + 1)
 #pragma unroll 1
                             for (int x = 0; x < 32; ++x) {
                                 const int64_t v = (int64_t)__float2int_rn(__uint_as_float(r[x]));
-                                finish_dispatch(g, nl, i, jb + x, (int64_t)((uint64_t)v << off), li, first);
+                                finish_dispatch(g, top_li + 1, p.acc, plane, (size_t)(jb + x) * p.mp + i, i, jb + x,
+                                                (int64_t)((uint64_t)v << off), li, top_li < 0);
                             }
-                        } else if (first) {
-#pragma unroll 4
+                        } else if (li > top_li) {
+                            // first touch of this limb: store (limb indices only grow along the walk,
+                            // so every limb below it has been stored already and none above is read)
+#pragma unroll
                             for (int x = 0; x < 32; ++x) {
                                 const int64_t v = (int64_t)__float2int_rn(__uint_as_float(r[x]));
-                                const size_t idx2 = (size_t)(jb + x) * p.mp + i;
-                                const int64_t val = (int64_t)((uint64_t)v << off);
-                                for (int l = 0; l < nl; ++l) p.acc[l * plane + idx2] = (l == li) ? val : 0;
+                                p.acc[li * plane + (size_t)(jb + x) * p.mp + i] = (int64_t)((uint64_t)v << off);
                             }
                         } else {
                             int64_t cur[32];
@@ -198,7 +215,23 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                             }
                         }
                     }
-                    first = false;
+                    if (li > top_li) top_li = li;
+                    if (split && last) {
+                        // the last chunk of the tile to finish rounds it: publish this chunk's
+                        // additions, count it, and let the finisher read every chunk's
+                        __threadfence();
+                        asm volatile("bar.sync 1, 128;\n" ::: "memory");
+                        if (warp == 2 && lane == 0) *fin_flag = atomicAdd(&p.cnt[it.slot], 1) == it.nchunks - 1;
+                        asm volatile("bar.sync 1, 128;\n" ::: "memory");
+                        if (*fin_flag) {
+                            __threadfence();
+#pragma unroll 1
+                            for (int jj = 0; jj < it.bn; ++jj)
+                                finish_dispatch(g, nl, sbase, sstride, (size_t)jj * BM + ii, i, it.j0 + jj, 0, 0,
+                                                false);
+                        }
+                        asm volatile("bar.sync 1, 128;\n" ::: "memory");
+                    }
                 }
                 w.next_pair();
             }
@@ -255,6 +288,53 @@ bool tc_make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t kp, u
     return r == CUDA_SUCCESS;
 }
 
+int tc_schedule(int ntiles, int pairs, int sms, int* items, int* off, int* nitems, int* nslots) {
+    if (sms < 1) sms = 1;
+    const int waves = ntiles / sms, r = ntiles % sms;
+    // chunks per tail tile: minimise waves + ceil(r c / sms) / c (+ a small per-chunk cost)
+    int best_c = 1;
+    double best = 1e30;
+    for (int c = 1; c <= 8 && c <= pairs; ++c) {
+        if (r == 0 && c > 1) break;
+        const double span = waves + (r ? (double)((r * c + sms - 1) / sms) / c : 0.0) + 0.002 * c;
+        if (span < best - 1e-9) { best = span; best_c = c; }
+    }
+    const int c = r ? best_c : 1;
+    const int grid = waves > 0 ? sms : (r * c < sms ? r * c : sms);
+    std::vector<std::vector<int>> per(grid);
+    int n = 0, slots = 0;
+    auto put = [&](int cta, int tile, int pa, int pb, int slot, int nch) {
+        int* w = items + 6 * n;
+        w[0] = 0; w[1] = tile; w[2] = pa; w[3] = pb; w[4] = slot; w[5] = nch;
+        per[cta].push_back(n++);
+    };
+    for (int t = 0; t < waves * sms; ++t) put(t % sms, t, 0, pairs, -1, 1);
+    int next = 0;
+    for (int t = waves * sms; t < ntiles; ++t) {
+        if (c == 1) { put(next, t, 0, pairs, -1, 1); next = (next + 1) % grid; continue; }
+        const int slot = slots++;
+        for (int x = 0; x < c; ++x) {
+            const int pa = (int)((int64_t)pairs * x / c), pb = (int)((int64_t)pairs * (x + 1) / c);
+            put(next, t, pa, pb, slot, c);
+            next = (next + 1) % grid;
+        }
+    }
+    // items regrouped per CTA
+    std::vector<int> tmp(items, items + 6 * n);
+    int pos = 0;
+    for (int cta = 0; cta < grid; ++cta) {
+        off[cta] = pos;
+        for (int id : per[cta]) {
+            for (int f = 0; f < 6; ++f) items[6 * pos + f] = tmp[6 * id + f];
+            ++pos;
+        }
+    }
+    off[grid] = pos;
+    *nitems = n;
+    *nslots = slots;
+    return grid;
+}
+
 int tc_num_sms() {
     static int sms = 0;
     if (!sms) {
@@ -281,13 +361,19 @@ cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t st) {
     p.q = g.q; p.is_f32 = g.is_f32; p.s = g.s; p.beta = g.beta; p.ppd = g.ppd; p.acc_words = g.acc_words;
     p.bn = tc::BN;
     p.d_only = g.d_only;
+    p.sacc = g.sacc;
+    p.cnt = g.cnt;
     tc::Sched sc;
     sc.probs = nullptr;
     sc.maps = nullptr;
-    sc.items = nullptr;
-    sc.off = nullptr;
+    sc.items = (const tc::WorkItem*)g.sched_items;
+    sc.off = g.sched_off;
     sc.ntiles = (int)((g.mp / tc::BM) * (g.np / tc::BN));
-    return tc_launch(sc, p, ma, mb, g.status, sc.ntiles, st);
+    if (sc.items && g.split_bytes) {
+        e = cudaMemsetAsync(g.sacc, 0, g.split_bytes, st);
+        if (e != cudaSuccess) return e;
+    }
+    return tc_launch(sc, p, ma, mb, g.status, sc.items ? g.sched_grid : sc.ntiles, st);
 }
 
 }  // namespace ozmp

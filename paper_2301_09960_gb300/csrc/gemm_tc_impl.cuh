@@ -129,20 +129,26 @@ struct Walk {
         if (++t == d) { --d; t = 1; }
         return true;
     }
+    // position of pair index `idx` of the walk starting at diagonal dhi
+    __device__ __forceinline__ static Walk at(int dhi, int idx) {
+        Walk w{dhi, 1};
+        while (idx >= w.d - 1) { idx -= w.d - 1; --w.d; }
+        w.t = 1 + idx;
+        return w;
+    }
 };
 
 // Limb accumulator of one element: NL int64 limbs, limb l weighs 2^(16 l),
-// layout [l][np][mp] (consecutive rows contiguous).  `zero` skips the load
-// (first and last drain of a tile coincide).
+// limb l of the element at base[l * lstride + idx].  `zero` skips the load
+// (first and last drain of a tile coincide).  Writes C(i, j) (or T in the
+// diagnostic mode).
 template <int NW>
-__device__ __forceinline__ void finish_element(const GemmArgs& g, int nl, int64_t i, int64_t j, int64_t x, int li,
-                                               bool zero) {
-    const size_t plane = (size_t)g.mp * g.np;
-    const size_t idx = (size_t)j * g.mp + i;
+__device__ __forceinline__ void finish_element(const GemmArgs& g, int nl, const int64_t* base, size_t lstride,
+                                               size_t idx, int64_t i, int64_t j, int64_t x, int li, bool zero) {
     constexpr int NLMAX = 4 * NW + 1;
     int64_t L[NLMAX];
 #pragma unroll
-    for (int l = 0; l < NLMAX; ++l) L[l] = (!zero && l < nl) ? g.acc[l * plane + idx] : 0;
+    for (int l = 0; l < NLMAX; ++l) L[l] = (!zero && l < nl) ? __ldcg(base + l * lstride + idx) : 0;
 #pragma unroll
     for (int l = 0; l < NLMAX; ++l)
         if (l == li) L[l] += x;
@@ -178,15 +184,15 @@ __device__ __forceinline__ void finish_element(const GemmArgs& g, int nl, int64_
     if (!ok) atomicOr(g.status, ST_RANGE);
 }
 
-__device__ __forceinline__ void finish_dispatch(const GemmArgs& g, int nl, int64_t i, int64_t j, int64_t x, int li,
-                                                bool zero) {
+__device__ __forceinline__ void finish_dispatch(const GemmArgs& g, int nl, const int64_t* base, size_t lstride,
+                                                size_t idx, int64_t i, int64_t j, int64_t x, int li, bool zero) {
     switch (g.acc_words) {
-        case 2: finish_element<2>(g, nl, i, j, x, li, zero); break;
-        case 3: finish_element<3>(g, nl, i, j, x, li, zero); break;
-        case 4: finish_element<4>(g, nl, i, j, x, li, zero); break;
-        case 5: finish_element<5>(g, nl, i, j, x, li, zero); break;
-        case 6: finish_element<6>(g, nl, i, j, x, li, zero); break;
-        default: finish_element<7>(g, nl, i, j, x, li, zero); break;
+        case 2: finish_element<2>(g, nl, base, lstride, idx, i, j, x, li, zero); break;
+        case 3: finish_element<3>(g, nl, base, lstride, idx, i, j, x, li, zero); break;
+        case 4: finish_element<4>(g, nl, base, lstride, idx, i, j, x, li, zero); break;
+        case 5: finish_element<5>(g, nl, base, lstride, idx, i, j, x, li, zero); break;
+        case 6: finish_element<6>(g, nl, base, lstride, idx, i, j, x, li, zero); break;
+        default: finish_element<7>(g, nl, base, lstride, idx, i, j, x, li, zero); break;
     }
 }
 
@@ -199,6 +205,8 @@ struct Prob {
     int64_t* acc;          // [nlimbs][np][mp] carry-save limbs
     void* C[4];
     int64_t* T;            // diagnostic output (d_only)
+    int64_t* sacc;         // split tiles: [slot][nlimbs][bn][BM] limbs, zeroed before the launch
+    int* cnt;              // split tiles: chunks finished per slot, zeroed before the launch
     int64_t m, n, mp, np, kp, ldc;
     int q, is_f32, s, beta, ppd, acc_words, bn, d_only;
 };
@@ -223,12 +231,19 @@ __device__ __forceinline__ GemmArgs as_gemm_args(const Prob& p, uint32_t* status
 
 // Work of one CTA: items [off[cta], off[cta + 1]) of `items` (prob, tile);
 // without an item list (single problem) tiles cta, cta + G, cta + 2G, ...
+// One work item: pairs [pa, pb) (in the walk order) of one tile of one
+// problem.  slot < 0: the item is the whole tile; else the tile is split into
+// nchunks items that add into split-limb slot `slot`.
+struct WorkItem {
+    int prob, tile, pa, pb, slot, nchunks;
+};
+
 struct Sched {
-    const Prob* probs;         // batched mode: one per problem (global memory)
+    const Prob* probs;         // batched mode: one per problem (global memory); else null
     const CUtensorMap* maps;   // batched mode: A and B maps of problem p at 2p, 2p + 1
-    const int2* items;
-    const int* off;
-    int ntiles;                // single-problem mode: tiles of the one problem
+    const WorkItem* items;     // null: tiles cta, cta + G, ... of the one problem, whole
+    const int* off;            // items [off[cta], off[cta + 1]) belong to CTA cta
+    int ntiles;                // no item list: tiles of the one problem
 };
 
 struct Item {
@@ -237,23 +252,37 @@ struct Item {
     const CUtensorMap* mb;
     int64_t i0, j0;
     int KT, dhi, dlo, bn;
+    int pa, pb, slot, nchunks;
 };
+
+// pairs of the walk d = dhi .. dlo, t = 1 .. d-1
+__host__ __device__ __forceinline__ int walk_pairs(int dhi, int dlo) {
+    return (dhi - dlo + 1) * (dlo - 1 + dhi - 1) / 2;
+}
 
 __device__ __forceinline__ bool item_at(const Sched& sc, const Prob* single, const CUtensorMap* ma,
                                         const CUtensorMap* mb, int idx, Item& it) {
     int pi, tile;
     if (sc.items) {
-        const int2 w = sc.items[idx];
-        pi = w.x;
-        tile = w.y;
-        it.p = &sc.probs[pi];
-        it.ma = &sc.maps[2 * pi];
-        it.mb = &sc.maps[2 * pi + 1];
+        const WorkItem w = sc.items[idx];
+        pi = w.prob;
+        tile = w.tile;
+        it.pa = w.pa;
+        it.pb = w.pb;
+        it.slot = w.slot;
+        it.nchunks = w.nchunks;
+        it.p = sc.probs ? &sc.probs[pi] : single;
+        it.ma = sc.probs ? &sc.maps[2 * pi] : ma;
+        it.mb = sc.probs ? &sc.maps[2 * pi + 1] : mb;
     } else {
         tile = idx;
         it.p = single;
         it.ma = ma;
         it.mb = mb;
+        it.pa = 0;
+        it.pb = -1;   // set below
+        it.slot = -1;
+        it.nchunks = 1;
     }
     const Prob& p = *it.p;
     const int tm = (int)(p.mp / BM);
@@ -263,6 +292,7 @@ __device__ __forceinline__ bool item_at(const Sched& sc, const Prob* single, con
     it.dhi = p.d_only ? p.d_only : p.s + 1;
     it.dlo = p.d_only ? p.d_only : 2;
     it.bn = p.bn;
+    if (it.pb < 0) it.pb = walk_pairs(it.dhi, it.dlo);
     return true;
 }
 

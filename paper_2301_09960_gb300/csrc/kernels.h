@@ -43,7 +43,21 @@ struct GemmArgs {
     uint32_t* status;
     int d_only;            // diagnostic: only diagonal d_only, raw int64 T_d written to T
     int64_t* T;
+    // tcgen05 form: precomputed tile schedule (null: one whole tile per CTA)
+    const void* sched_items;   // tc::WorkItem[]
+    const int* sched_off;      // items of CTA c: [off[c], off[c + 1])
+    int sched_grid;
+    int64_t* sacc;             // split-tile limbs, zeroed before every launch
+    int* cnt;                  // split-tile chunk counters (follow sacc)
+    size_t split_bytes;        // bytes of sacc + cnt
 };
+
+// Tile schedule of one tcgen05 problem (host): whole tiles in full waves over
+// `sms` CTAs; the tiles of a partial last wave (or of a problem with fewer
+// tiles than CTAs) split into pair-range chunks.  Writes items (6 ints each:
+// prob, tile, pa, pb, slot, nchunks) and CTA offsets; returns the grid.
+int tc_schedule(int ntiles, int pairs, int sms, int* items, int* off, int* nitems, int* nslots);
+int tc_num_sms();
 
 cudaError_t launch_split(const SplitArgs& a, cudaStream_t st);
 cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t st);

@@ -4,6 +4,7 @@
 #pragma once
 #include <cstdint>
 #include <cstring>
+#include <new>
 #include "kernels.h"
 #include "ozmp_internal.cuh"
 
@@ -20,6 +21,12 @@ struct ozmp_plan_s {
     bool ws_owned;
     cudaStream_t stream;
     void* batch;   // batched plan data (ozmp_gemm_batched), else null
+    // tcgen05 tile schedule (plans made by ozmp_plan_create): host copy, sizes,
+    // workspace regions, and the workspace it was last uploaded to
+    int* sched_host;
+    int sched_items, sched_slots, sched_grid;
+    size_t off_items, off_soff, off_sacc, split_bytes;
+    void* sched_ws;
 };
 
 namespace ozmp_batch {
@@ -202,7 +209,54 @@ inline GemmArgs gemm_args(ozmp_plan_s* p) {
     g.acc_words = p->acc_words; g.ngroups = p->ngroups;
     g.acc = (p->ngroups > 1 || p->form == OZMP_FORM_FP8) ? (int64_t*)(w + p->off_acc) : nullptr;
     g.status = (uint32_t*)(w + p->off_status);
+    if (p->sched_host) {
+        g.sched_items = w + p->off_items;
+        g.sched_off = (const int*)(w + p->off_soff);
+        g.sched_grid = p->sched_grid;
+        g.sacc = p->sched_slots ? (int64_t*)(w + p->off_sacc) : nullptr;
+        g.cnt = p->sched_slots ? (int*)(w + p->off_sacc + (size_t)p->sched_slots * p->nlimbs * 256 * 128 * 8)
+                               : nullptr;
+        g.split_bytes = p->split_bytes;
+    }
     return g;
+}
+
+// tcgen05 form: build the tile schedule and append its workspace regions
+// (items, CTA offsets, split-tile limbs + counters)
+inline ozmp_status plan_schedule(ozmp_plan_s* p) {
+    if (p->form != OZMP_FORM_FP8 || p->m == 0 || p->n == 0 || p->k == 0) return OZMP_OK;
+    const int ntiles = (int)((p->mp / 128) * (p->np / 256));
+    const int pairs = p->s * (p->s + 1) / 2;
+    const int sms = tc_num_sms();
+    p->sched_host = new (std::nothrow) int[(size_t)6 * ntiles * 8 + sms + 1];
+    if (!p->sched_host) return OZMP_ERR_NOMEM;
+    int* items = p->sched_host;
+    int* off = p->sched_host + (size_t)6 * ntiles * 8;
+    p->sched_grid = tc_schedule(ntiles, pairs, sms, items, off, &p->sched_items, &p->sched_slots);
+    // CTA offsets right after the items in the host copy
+    int* off2 = items + 6 * p->sched_items;
+    for (int c = 0; c <= p->sched_grid; ++c) off2[c] = off[c];
+    size_t o = p->ws_bytes;
+    p->off_items = o; o = align256(o + (size_t)p->sched_items * 24);
+    p->off_soff = o; o = align256(o + (size_t)(p->sched_grid + 1) * 4);
+    p->off_sacc = o;
+    p->split_bytes = (size_t)p->sched_slots * p->nlimbs * 256 * 128 * 8 + (size_t)p->sched_slots * 4;
+    o = align256(o + p->split_bytes);
+    p->ws_bytes = o;
+    return OZMP_OK;
+}
+
+// copy the schedule into the current workspace (once per workspace)
+inline ozmp_status plan_upload_schedule(ozmp_plan_s* p) {
+    if (!p->sched_host || p->sched_ws == p->ws) return OZMP_OK;
+    const size_t bytes = (size_t)p->sched_items * 24;
+    if (cudaMemcpyAsync((char*)p->ws + p->off_items, p->sched_host, bytes, cudaMemcpyHostToDevice, p->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync((char*)p->ws + p->off_soff, p->sched_host + 6 * p->sched_items,
+                        (size_t)(p->sched_grid + 1) * 4, cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
+        return OZMP_ERR_CUDA;
+    p->sched_ws = p->ws;
+    return OZMP_OK;
 }
 
 inline ozmp_status zero_c(ozmp_plan_s* p, void* const* C, int64_t ldc) {

@@ -287,3 +287,30 @@ def test_split_adversarial_boundaries(prec, form):
     assert list(E) == Eo and list(F) == Fo
     np.testing.assert_array_equal(digits_to_int(ga[:, :m, :k], form), dA)
     np.testing.assert_array_equal(digits_to_int(gb[:, :n, :k], form), dB)
+
+
+def test_tail_tiles_split_across_ctas_match_other_engine():
+    # 2560 x 2048 -> 20 x 8 = 160 tiles of 128 x 256 on 152 SMs: one full
+    # wave of whole tiles plus tail tiles split into pair-range chunks that
+    # add atomically.  Exactness makes the result independent of the split:
+    # it must equal the mma.sync e4m3 engine bit for bit.
+    m, n, k = 2560, 2048, 192
+    A, B = gen_problem("dd", m, n, k, phi=1.0, seed=13)
+    Ad, Bd = to_dev(A), to_dev(B)
+    C1, p1 = oz.gemm(Ad, Bd, "dd", "fp8", 0)
+    C2, p2 = oz.gemm(Ad, Bd, "dd", "fp8mma", 0)
+    torch.cuda.synchronize()
+    assert p1.status() == oz.Status.OK and p2.status() == oz.Status.OK
+    for x, y in zip(C1, C2):
+        assert torch.equal(x, y)
+    # and a sampled block against the oracle's Ozaki sum
+    rows = list(range(0, m, 397))
+    cols = list(range(0, n, 311))
+    Cg = from_dev(C1)
+    As = [np.asfortranarray(a[rows, :]) for a in A]
+    Bs = [np.asfortranarray(b[:, cols]) for b in B]
+    # exponents are row/column maxima over k, so the sub-block split equals the full one
+    r = O.ozaki_product(As, Bs, p1.info.beta, p1.info.nslices)
+    for a_i, i in enumerate(rows):
+        for b_j, j in enumerate(cols):
+            assert [float(c[i, j]) for c in Cg] == X.to_components(r["S"][a_i][b_j], 2)
