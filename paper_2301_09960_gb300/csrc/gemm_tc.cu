@@ -6,16 +6,25 @@
 namespace ozmp {
 namespace tc {
 
+// CG = 1: one CTA per 128 x bn tile.  CG = 2: a cluster of two CTAs per
+// 256 x 256 tile, one tcgen05.mma.cta_group::2 (M = 256) issued by the leader
+// (rank 0) reading both CTAs' shared memory; the leader's full barrier counts
+// the bytes of both CTAs' copies, its MMA commits release the stage and the
+// accumulator in both CTAs, and both CTAs' epilogues release the accumulator
+// on the leader's barrier.
+template <int CG>
 __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_constant__ Prob single,
                                                     const __grid_constant__ CUtensorMap tmA,
                                                     const __grid_constant__ CUtensorMap tmB, uint32_t* status) {
+    constexpr int NS = CG == 2 ? NST2 : NST;
+    constexpr unsigned SB = CG == 2 ? STAGE_B2 : STAGE_B;   // bytes of B staged per CTA
     extern __shared__ unsigned char smraw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     unsigned char* sA = base;
-    unsigned char* sB = base + (size_t)NST * STAGE_A;
-    uint64_t* full = reinterpret_cast<uint64_t*>(sB + (size_t)NST * STAGE_B);
-    uint64_t* empty = full + NST;
-    uint64_t* accf = empty + NST;
+    unsigned char* sB = base + (size_t)NS * STAGE_A;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + (size_t)NS * SB);
+    uint64_t* empty = full + NS;
+    uint64_t* accf = empty + NS;
     uint64_t* acce = accf + 2;
     uint64_t* done = acce + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
@@ -23,26 +32,47 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
     volatile int* fin_flag = reinterpret_cast<volatile int*>(tmem_slot + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = CG == 2 ? cluster_rank() : 0u;
+    const int cid = CG == 2 ? (int)cluster_id_x() : (int)blockIdx.x;
+    const int ncl = CG == 2 ? (int)cluster_count_x() : (int)gridDim.x;
+    // the leader's full and acc-empty barriers, and the peer's abort flag
+    const uint32_t full_cl = CG == 2 ? map_rank(saddr(full), 0) : saddr(full);
+    const uint32_t acce_cl = CG == 2 ? map_rank(saddr(acce), 0) : saddr(acce);
+    const uint32_t peer_abort = CG == 2 ? map_rank(saddr((const void*)abort_flag), rank ^ 1u) : 0u;
+    auto raise_abort = [&]() {
+        *abort_flag = 1;
+        if (CG == 2) st_cluster_u32(peer_abort, 1u);
+        atomicOr(status, ST_TIMEOUT);
+    };
 
     int it_begin, it_end, it_step;
-    if (sc.items) { it_begin = sc.off[blockIdx.x]; it_end = sc.off[blockIdx.x + 1]; it_step = 1; }
-    else { it_begin = blockIdx.x; it_end = sc.ntiles; it_step = gridDim.x; }
+    if (sc.items) { it_begin = sc.off[cid]; it_end = sc.off[cid + 1]; it_step = 1; }
+    else { it_begin = cid; it_end = sc.ntiles; it_step = ncl; }
 
     if (threadIdx.x == 0) {
-        for (int x = 0; x < NST; ++x) { mbar_init(&full[x], 1); mbar_init(&empty[x], 1); }
-        for (int x = 0; x < 2; ++x) { mbar_init(&accf[x], 1); mbar_init(&acce[x], 4); }
+        for (int x = 0; x < NS; ++x) { mbar_init(&full[x], 1); mbar_init(&empty[x], 1); }
+        for (int x = 0; x < 2; ++x) { mbar_init(&accf[x], 1); mbar_init(&acce[x], 4 * CG); }
         mbar_init(done, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" ::"r"(saddr(tmem_slot))
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+        if (CG == 2) {
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], 512;\n" ::"r"(
+                             saddr(tmem_slot))
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;\n" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" ::"r"(
+                             saddr(tmem_slot))
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+        }
     }
     tc_fence_before();
     __syncthreads();
+    if (CG == 2) cluster_sync();   // the peer's barriers are initialised before any remote arrive
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -53,85 +83,103 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
             bool ok = true;
             for (int idx = it_begin; ok && idx < it_end; idx += it_step) {
                 Item it;
-                item_at(sc, &single, &tmA, &tmB, idx, it);
+                item_at<CG>(sc, &single, &tmA, &tmB, idx, it, rank);
                 const Prob p = *it.p;
-                const unsigned tx = STAGE_A + (unsigned)it.bn * BK;
+                const unsigned tx = CG == 2 ? 2u * (STAGE_A + SB) : STAGE_A + (unsigned)it.bn * BK;
+                const int jb = (int)it.j0 + (CG == 2 ? (int)rank * (BN / 2) : 0);
                 Walk w = Walk::at(it.dhi, it.pa);
                 for (int pi = it.pa; ok && pi < it.pb; ++pi) {
                     const int u = w.d - w.t;
                     const int ya = (w.t - 1) * (int)p.mp + (int)it.i0;
-                    const int yb = (u - 1) * (int)p.np + (int)it.j0;
+                    const int yb = (u - 1) * (int)p.np + jb;
                     for (int kc = 0; kc < it.KT; ++kc, ++n) {
-                        const int st = (int)(n % NST);
-                        const unsigned ph = (unsigned)((n / NST) & 1);
-                        if (!mbar_wait(&empty[st], ph ^ 1u, abort_flag)) { ok = false; break; }
-                        mbar_expect_tx(&full[st], tx);
-                        tma_load_2d(sA + (size_t)st * STAGE_A, it.ma, &full[st], kc * BK, ya);
-                        tma_load_2d(sB + (size_t)st * STAGE_B, it.mb, &full[st], kc * BK, yb);
+                        const int st = (int)(n % NS);
+                        const unsigned ph = (unsigned)((n / NS) & 1);
+                        if (!mbar_wait<CG == 2>(&empty[st], ph ^ 1u, abort_flag)) { ok = false; break; }
+                        if (rank == 0) mbar_expect_tx(&full[st], tx);
+                        if (CG == 2) {
+                            tma_load_2d_pair(sA + (size_t)st * STAGE_A, it.ma, full_cl + 8u * st, kc * BK, ya);
+                            tma_load_2d_pair(sB + (size_t)st * SB, it.mb, full_cl + 8u * st, kc * BK, yb);
+                        } else {
+                            tma_load_2d(sA + (size_t)st * STAGE_A, it.ma, &full[st], kc * BK, ya);
+                            tma_load_2d(sB + (size_t)st * SB, it.mb, &full[st], kc * BK, yb);
+                        }
                     }
                     w.next_pair();
                 }
             }
             if (!ok) {
-                *abort_flag = 1;
-                atomicOr(status, ST_TIMEOUT);
-                // let the copies already issued land before the CTA can exit
-                volatile int never = 0;
-                for (long long q = n - 1; q >= 0 && q >= n - NST; --q)
-                    mbar_wait(&full[(int)(q % NST)], (unsigned)((q / NST) & 1), &never);
+                raise_abort();
+                // let the copies already issued land before the CTA can exit (the
+                // leader's full barrier counts the copies of both CTAs)
+                if (rank == 0) {
+                    volatile int never = 0;
+                    for (long long q = n - 1; q >= 0 && q >= n - NS; --q)
+                        mbar_wait<CG == 2>(&full[(int)(q % NS)], (unsigned)((q / NS) & 1), &never, DRAIN_LIMIT);
+                }
             }
         }
     } else if (warp == 1) {
-        // ------------------------------------------------------------ MMA issuer
-        if (lane == 0) {
+        // ------------------------------------------------------------ MMA issuer (the leader's)
+        if (lane == 0 && rank == 0) {
             long long n = 0;
             int buf = 0, uses[2] = {0, 0};
-            bool ok = mbar_wait(&acce[0], 1u, abort_flag);     // first use of buffer 0
+            bool ok = mbar_wait<CG == 2>(&acce[0], 1u, abort_flag);     // first use of buffer 0
             for (int idx = it_begin; ok && idx < it_end; idx += it_step) {
                 Item it;
-                item_at(sc, &single, &tmA, &tmB, idx, it);
+                item_at<CG>(sc, &single, &tmA, &tmB, idx, it, rank);
                 const Prob p = *it.p;
-                const uint32_t idesc = idesc_e4m3(BM, it.bn);
+                const uint32_t idesc = idesc_e4m3(BM * CG, it.bn);
                 Walk w = Walk::at(it.dhi, it.pa);
                 int since = 0;
                 bool fresh = true;
                 for (int pi = it.pa; ok && pi < it.pb; ++pi) {
                     const uint32_t dcol = tmem + (uint32_t)(buf * BN);
                     for (int kc = 0; kc < it.KT; ++kc, ++n) {
-                        const int st = (int)(n % NST);
-                        const unsigned ph = (unsigned)((n / NST) & 1);
-                        if (!mbar_wait(&full[st], ph, abort_flag)) { ok = false; break; }
+                        const int st = (int)(n % NS);
+                        const unsigned ph = (unsigned)((n / NS) & 1);
+                        if (!mbar_wait<CG == 2>(&full[st], ph, abort_flag)) { ok = false; break; }
                         tc_fence_after();
                         const uint64_t ad = desc_sw128(saddr(sA + (size_t)st * STAGE_A));
-                        const uint64_t bd = desc_sw128(saddr(sB + (size_t)st * STAGE_B));
+                        const uint64_t bd = desc_sw128(saddr(sB + (size_t)st * SB));
 #pragma unroll
                         for (int kk = 0; kk < BK / 32; ++kk) {
-                            mma_e4m3_tc(dcol, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc,
-                                        (fresh && kk == 0) ? 0u : 1u);
+                            const uint32_t acc = (fresh && kk == 0) ? 0u : 1u;
+                            if (CG == 2)
+                                mma_e4m3_tc_pair(dcol, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, acc);
+                            else
+                                mma_e4m3_tc(dcol, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, acc);
                         }
                         fresh = false;
-                        mma_commit(&empty[st]);
+                        if (CG == 2) mma_commit_pair(&empty[st]);
+                        else mma_commit(&empty[st]);
                     }
                     if (!ok) break;
                     ++since;
                     const bool diag_end = (w.t == w.d - 1);
                     if (since == p.ppd || diag_end || pi == it.pb - 1) {
-                        mma_commit(&accf[buf]);
+                        if (CG == 2) mma_commit_pair(&accf[buf]);
+                        else mma_commit(&accf[buf]);
                         uses[buf]++;
                         buf ^= 1;
                         since = 0;
                         fresh = true;
-                        // the k-th use of a buffer waits for the epilogue's (k-1)-th release
-                        if (!mbar_wait(&acce[buf], (unsigned)((uses[buf] & 1) ^ 1), abort_flag)) { ok = false; break; }
+                        // the k-th use of a buffer waits for the epilogues' (k-1)-th release
+                        if (!mbar_wait<CG == 2>(&acce[buf], (unsigned)((uses[buf] & 1) ^ 1), abort_flag)) {
+                            ok = false;
+                            break;
+                        }
                     }
                     w.next_pair();
                 }
             }
-            if (!ok) { *abort_flag = 1; atomicOr(status, ST_TIMEOUT); }
-            // every issued MMA has completed before the TMEM can be released
-            mma_commit(done);
+            if (!ok) raise_abort();
+            // every issued MMA (into both CTAs' tensor memory) has completed
+            // before the pair passes the final cluster barrier
+            if (CG == 2) mma_commit_local_pair(done);
+            else mma_commit(done);
             volatile int never = 0;
-            mbar_wait(done, 0u, &never);
+            mbar_wait<CG == 2>(done, 0u, &never, DRAIN_LIMIT);
         }
     } else {
         // ------------------------------------------------------------ epilogue
@@ -141,7 +189,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
         bool ok = true;
         for (int idx = it_begin; ok && idx < it_end; idx += it_step) {
             Item it;
-            item_at(sc, &single, &tmA, &tmB, idx, it);
+            item_at<CG>(sc, &single, &tmA, &tmB, idx, it, rank);
             const Prob p = *it.p;
             const GemmArgs g = as_gemm_args(p, status);
             const int64_t i = it.i0 + quarter * 32 + lane;
@@ -149,9 +197,10 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
             const size_t plane = (size_t)p.mp * p.np;
             const int nl = 4 * p.acc_words + 1;
             const bool split = it.slot >= 0;
+            const int slot = it.slot * CG + (int)rank;   // split-limb slot of this CTA's rows
             // split tiles: limb l of tile column jj, row ii at sbase[l * sstride + jj * BM + ii]
             const size_t sstride = (size_t)it.bn * BM;
-            int64_t* sbase = split ? p.sacc + (size_t)it.slot * nl * sstride : nullptr;
+            int64_t* sbase = split ? p.sacc + (size_t)slot * nl * sstride : nullptr;
             Walk w = Walk::at(it.dhi, it.pa);
             int since = 0;
             int top_li = -1;   // highest limb stored so far for this tile (whole tiles)
@@ -164,7 +213,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                     const int buf = ev & 1;
                     const unsigned par = (unsigned)((ev >> 1) & 1);
                     ++ev;
-                    if (!mbar_wait(&accf[buf], par, abort_flag)) { ok = false; break; }
+                    if (!mbar_wait<CG == 2>(&accf[buf], par, abort_flag)) { ok = false; break; }
                     tc_fence_after();
                     const int fsh = p.d_only ? 0 : p.beta * (p.s + 1 - w.d);
                     const int li = fsh >> 4, off = fsh & 15;
@@ -177,7 +226,10 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                             // the accumulator buffer is free once its last columns are in registers
                             tc_fence_before();
                             __syncwarp();
-                            if (lane == 0) mbar_arrive(&acce[buf]);
+                            if (lane == 0) {
+                                if (CG == 2) mbar_arrive_cluster(acce_cl + 8u * buf);
+                                else mbar_arrive(&acce[buf]);
+                            }
                         }
                         const int64_t jb = it.j0 + c * 32;
                         if (split) {
@@ -221,7 +273,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                         // additions, count it, and let the finisher read every chunk's
                         __threadfence();
                         asm volatile("bar.sync 1, 128;\n" ::: "memory");
-                        if (warp == 2 && lane == 0) *fin_flag = atomicAdd(&p.cnt[it.slot], 1) == it.nchunks - 1;
+                        if (warp == 2 && lane == 0) *fin_flag = atomicAdd(&p.cnt[slot], 1) == it.nchunks - 1;
                         asm volatile("bar.sync 1, 128;\n" ::: "memory");
                         if (*fin_flag) {
                             __threadfence();
@@ -236,28 +288,54 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                 w.next_pair();
             }
         }
-        if (!ok) { *abort_flag = 1; atomicOr(status, ST_TIMEOUT); }
+        if (!ok) raise_abort();
     }
 
     tc_fence_before();
     __syncthreads();
+    if (CG == 2) cluster_sync();   // no MMA, copy or remote arrive of either CTA is outstanding
     tc_fence_after();
     if (warp == 1) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem) : "memory");
+        if (CG == 2)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, 512;\n" ::"r"(tmem) : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem) : "memory");
     }
+    if (CG == 2) cluster_sync();
 }
 
 }  // namespace tc
 
 cudaError_t tc_set_smem() {
-    return cudaFuncSetAttribute(tc::k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(tc::k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(tc::k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM2);
 }
 
 cudaError_t tc_launch(const tc::Sched& sc, const tc::Prob& single, const CUtensorMap& ma, const CUtensorMap& mb,
                       uint32_t* status, int grid, cudaStream_t st) {
     if (grid <= 0) return cudaSuccess;
-    tc::k_gemm_tc<<<grid, tc::NT, tc::SMEM, st>>>(sc, single, ma, mb, status);
+    tc::k_gemm_tc<1><<<grid, tc::NT, tc::SMEM, st>>>(sc, single, ma, mb, status);
     return cudaGetLastError();
+}
+
+cudaError_t tc_launch_pair(const tc::Sched& sc, const tc::Prob& single, const CUtensorMap& ma,
+                           const CUtensorMap& mb, uint32_t* status, int clusters, cudaStream_t st) {
+    if (clusters <= 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)(2 * clusters), 1, 1);
+    cfg.blockDim = dim3(tc::NT, 1, 1);
+    cfg.dynamicSmemBytes = tc::SMEM2;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, tc::k_gemm_tc<2>, sc, single, ma, mb, status);
 }
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -345,11 +423,40 @@ int tc_num_sms() {
     return sms;
 }
 
+// clusters of two CTAs of the pair form that can be resident at once (an SM
+// left over in a GPC with an odd number of free SMs cannot host one)
+int tc_num_pair_slots() {
+    static int slots = 0;
+    if (!slots) {
+        int n = 0;
+        if (tc_set_smem() == cudaSuccess) {
+            cudaLaunchConfig_t cfg;
+            memset(&cfg, 0, sizeof(cfg));
+            cfg.gridDim = dim3(2 * (unsigned)tc_num_sms(), 1, 1);
+            cfg.blockDim = dim3(tc::NT, 1, 1);
+            cfg.dynamicSmemBytes = tc::SMEM2;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 2;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            if (cudaOccupancyMaxActiveClusters(&n, tc::k_gemm_tc<2>, &cfg) != cudaSuccess) n = 0;
+        }
+        cudaGetLastError();
+        slots = n > 0 ? n : (tc_num_sms() / 2 > 0 ? tc_num_sms() / 2 : 1);
+    }
+    return slots;
+}
+
 cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t st) {
     if (g.mp % tc::BM || g.np % tc::BN || g.kp % tc::BK) return cudaErrorInvalidValue;
+    const int cg = (g.tc_cg == 2 && g.mp % (2 * tc::BM) == 0) ? 2 : 1;
+    if (g.tc_cg == 2 && cg != 2) return cudaErrorInvalidValue;   // the schedule counts pair tiles
     CUtensorMap ma, mb;
     if (!tc_make_map(&ma, g.Adig, (uint64_t)g.s * g.mp, (uint64_t)g.kp, tc::BM)) return cudaErrorInvalidValue;
-    if (!tc_make_map(&mb, g.Bdig, (uint64_t)g.s * g.np, (uint64_t)g.kp, tc::BN)) return cudaErrorInvalidValue;
+    if (!tc_make_map(&mb, g.Bdig, (uint64_t)g.s * g.np, (uint64_t)g.kp, tc::BN / cg)) return cudaErrorInvalidValue;
     cudaError_t e = tc_set_smem();
     if (e != cudaSuccess) return e;
     tc::Prob p;
@@ -368,12 +475,14 @@ cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t st) {
     sc.maps = nullptr;
     sc.items = (const tc::WorkItem*)g.sched_items;
     sc.off = g.sched_off;
-    sc.ntiles = (int)((g.mp / tc::BM) * (g.np / tc::BN));
+    sc.ntiles = (int)((g.mp / (tc::BM * cg)) * (g.np / tc::BN));
     if (sc.items && g.split_bytes) {
         e = cudaMemsetAsync(g.sacc, 0, g.split_bytes, st);
         if (e != cudaSuccess) return e;
     }
-    return tc_launch(sc, p, ma, mb, g.status, sc.items ? g.sched_grid : sc.ntiles, st);
+    const int grid = sc.items ? g.sched_grid : sc.ntiles;
+    if (cg == 2) return tc_launch_pair(sc, p, ma, mb, g.status, grid, st);
+    return tc_launch(sc, p, ma, mb, g.status, grid, st);
 }
 
 }  // namespace ozmp

@@ -36,7 +36,14 @@ constexpr int BM = 128, BN = 256, BK = 128, NST = 4, NT = 192;   // BN: widest t
 constexpr unsigned STAGE_A = BM * BK, STAGE_B = BN * BK;
 constexpr unsigned TX_BYTES = STAGE_A + STAGE_B;
 constexpr size_t SMEM = 1024 + (size_t)NST * (STAGE_A + STAGE_B) + 256;
+// CTA-pair form (cta_group::2): a cluster of two CTAs owns a 256 x 256 tile;
+// each CTA stages its 128 rows of A and its half (128 rows) of the B tile,
+// so a stage is 32 KB per CTA and six stages fit
+constexpr int NST2 = 6;
+constexpr unsigned STAGE_B2 = (BN / 2) * BK;
+constexpr size_t SMEM2 = 1024 + (size_t)NST2 * (STAGE_A + STAGE_B2) + 256;
 constexpr long long WAIT_LIMIT = 1ll << 26;   // try_wait polls before giving up (seconds)
+constexpr long long DRAIN_LIMIT = 1ll << 20;  // polls for copies / MMAs already in flight at the end
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -58,13 +65,58 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, unsigned parity) {
         : "memory");
     return ok != 0;
 }
+// the same with cluster-scope acquire (phases completed by the peer CTA of a pair)
+__device__ __forceinline__ bool mbar_try_cl(uint64_t* b, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(saddr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 // bounded wait for the phase of parity `parity`; false on timeout or abort
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, volatile int* abort_flag) {
-    for (long long it = 0; it < WAIT_LIMIT; ++it) {
-        if (mbar_try(b, parity)) return true;
+template <bool CLUSTER = false>
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, volatile int* abort_flag,
+                                          long long limit = WAIT_LIMIT) {
+    for (long long it = 0; it < limit; ++it) {
+        if (CLUSTER ? mbar_try_cl(b, parity) : mbar_try(b, parity)) return true;
         if ((it & 255) == 255 && *abort_flag) return false;
     }
     return false;
+}
+
+// ---- cluster helpers of the CTA-pair form
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;\n" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_count_x() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;\n" : "=r"(r));
+    return r;
+}
+// shared::cluster address of the same shared-memory offset in CTA `rank`
+__device__ __forceinline__ uint32_t map_rank(uint32_t local, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(local), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cl_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];\n" ::"r"(cl_addr) : "memory");
+}
+__device__ __forceinline__ void st_cluster_u32(uint32_t cl_addr, uint32_t v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;\n" ::"r"(cl_addr), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
@@ -72,6 +124,16 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];\n" ::"r"(
             saddr(dst)),
         "l"((uint64_t)map), "r"(saddr(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// pair form: the copy lands in this CTA's shared memory and completes its
+// bytes on the barrier at `bar_cl`, which may be the leader CTA's
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, uint32_t bar_cl, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+        "%4}], [%2];\n" ::"r"(saddr(dst)),
+        "l"((uint64_t)map), "r"(bar_cl), "r"(x), "r"(y)
         : "memory");
 }
 
@@ -106,6 +168,31 @@ __device__ __forceinline__ void mma_e4m3_tc(uint32_t tmem_d, uint64_t adesc, uin
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(saddr(bar))
+                 : "memory");
+}
+
+// pair form: M = 256 over the two CTAs (A rows 0..127 from the leader's
+// shared memory, 128..255 from the peer's; B columns split the same way),
+// each CTA's tensor memory holding its 128 rows of D
+__device__ __forceinline__ void mma_e4m3_tc_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                                 uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// arrive on the barrier at the same offset in both CTAs of the pair once the
+// issuing thread's earlier MMAs are complete
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n" ::"r"(
+            saddr(bar)),
+        "h"((unsigned short)3)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit_local_pair(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(saddr(bar))
                  : "memory");
 }
 
@@ -260,8 +347,11 @@ __host__ __device__ __forceinline__ int walk_pairs(int dhi, int dlo) {
     return (dhi - dlo + 1) * (dlo - 1 + dhi - 1) / 2;
 }
 
+// CG = 2: the tile index counts 256-row tiles of the pair; this CTA (rank)
+// owns rows rank * 128 .. + 127 of it
+template <int CG = 1>
 __device__ __forceinline__ bool item_at(const Sched& sc, const Prob* single, const CUtensorMap* ma,
-                                        const CUtensorMap* mb, int idx, Item& it) {
+                                        const CUtensorMap* mb, int idx, Item& it, uint32_t rank = 0) {
     int pi, tile;
     if (sc.items) {
         const WorkItem w = sc.items[idx];
@@ -285,8 +375,8 @@ __device__ __forceinline__ bool item_at(const Sched& sc, const Prob* single, con
         it.nchunks = 1;
     }
     const Prob& p = *it.p;
-    const int tm = (int)(p.mp / BM);
-    it.i0 = (int64_t)(tile % tm) * BM;
+    const int tm = (int)(p.mp / (BM * CG));
+    it.i0 = (int64_t)(tile % tm) * (BM * CG) + (int64_t)rank * BM;
     it.j0 = (int64_t)(tile / tm) * p.bn;
     it.KT = (int)(p.kp / BK);
     it.dhi = p.d_only ? p.d_only : p.s + 1;
@@ -306,5 +396,8 @@ int tc_num_sms();
 cudaError_t tc_launch(const tc::Sched& sc, const tc::Prob& single, const CUtensorMap& ma, const CUtensorMap& mb,
                       uint32_t* status, int grid, cudaStream_t st);
 cudaError_t tc_set_smem();
+// the CTA-pair form: `clusters` clusters of two CTAs over the schedule
+cudaError_t tc_launch_pair(const tc::Sched& sc, const tc::Prob& single, const CUtensorMap& ma,
+                           const CUtensorMap& mb, uint32_t* status, int clusters, cudaStream_t st);
 
 }  // namespace ozmp

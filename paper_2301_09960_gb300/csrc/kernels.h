@@ -50,6 +50,7 @@ struct GemmArgs {
     int64_t* sacc;             // split-tile limbs, zeroed before every launch
     int* cnt;                  // split-tile chunk counters (follow sacc)
     size_t split_bytes;        // bytes of sacc + cnt
+    int tc_cg;                 // 2: CTA-pair tiles (256 x 256, cta_group::2); else one CTA per tile
 };
 
 // Tile schedule of one tcgen05 problem (host): whole tiles in full waves over
@@ -58,6 +59,7 @@ struct GemmArgs {
 // prob, tile, pa, pb, slot, nchunks) and CTA offsets; returns the grid.
 int tc_schedule(int ntiles, int pairs, int sms, int* items, int* off, int* nitems, int* nslots);
 int tc_num_sms();
+int tc_num_pair_slots();   // co-resident clusters of two CTAs of the tcgen05 pair form
 
 cudaError_t launch_split(const SplitArgs& a, cudaStream_t st);
 cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t st);

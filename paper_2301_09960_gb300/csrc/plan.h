@@ -3,6 +3,7 @@
 // layout and the launch descriptors built from a plan.
 #pragma once
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include "kernels.h"
@@ -24,7 +25,8 @@ struct ozmp_plan_s {
     // tcgen05 tile schedule (plans made by ozmp_plan_create): host copy, sizes,
     // workspace regions, and the workspace it was last uploaded to
     int* sched_host;
-    int sched_items, sched_slots, sched_grid;
+    int sched_items, sched_slots, sched_grid;   // sched_slots: split-limb slots of single CTAs
+    int tc_cg;                                   // 2: the schedule is over CTA-pair tiles
     size_t off_items, off_soff, off_sacc, split_bytes;
     void* sched_ws;
 };
@@ -217,22 +219,29 @@ inline GemmArgs gemm_args(ozmp_plan_s* p) {
         g.cnt = p->sched_slots ? (int*)(w + p->off_sacc + (size_t)p->sched_slots * p->nlimbs * 256 * 128 * 8)
                                : nullptr;
         g.split_bytes = p->split_bytes;
+        g.tc_cg = p->tc_cg;
     }
     return g;
 }
 
 // tcgen05 form: build the tile schedule and append its workspace regions
-// (items, CTA offsets, split-tile limbs + counters)
+// (items, CTA offsets, split-tile limbs + counters).  Tiles are 256 x 256 over
+// a CTA pair when the padded row count allows it (OZMP_TC_PAIR=0 in the
+// environment keeps one 128 x 256 tile per CTA), the schedule then running
+// over clusters (half the SMs) and every split slot holding two CTAs' rows.
 inline ozmp_status plan_schedule(ozmp_plan_s* p) {
     if (p->form != OZMP_FORM_FP8 || p->m == 0 || p->n == 0 || p->k == 0) return OZMP_OK;
-    const int ntiles = (int)((p->mp / 128) * (p->np / 256));
+    const char* env = getenv("OZMP_TC_PAIR");
+    p->tc_cg = (p->mp % 256 == 0 && !(env && env[0] == '0')) ? 2 : 1;
+    const int ntiles = (int)((p->mp / (128 * p->tc_cg)) * (p->np / 256));
     const int pairs = p->s * (p->s + 1) / 2;
-    const int sms = tc_num_sms();
+    const int sms = p->tc_cg == 2 ? tc_num_pair_slots() : tc_num_sms();
     p->sched_host = new (std::nothrow) int[(size_t)6 * ntiles * 8 + sms + 1];
     if (!p->sched_host) return OZMP_ERR_NOMEM;
     int* items = p->sched_host;
     int* off = p->sched_host + (size_t)6 * ntiles * 8;
     p->sched_grid = tc_schedule(ntiles, pairs, sms, items, off, &p->sched_items, &p->sched_slots);
+    p->sched_slots *= p->tc_cg;
     // CTA offsets right after the items in the host copy
     int* off2 = items + 6 * p->sched_items;
     for (int c = 0; c <= p->sched_grid; ++c) off2[c] = off[c];

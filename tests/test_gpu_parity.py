@@ -289,11 +289,14 @@ def test_split_adversarial_boundaries(prec, form):
     np.testing.assert_array_equal(digits_to_int(gb[:, :n, :k], form), dB)
 
 
-def test_tail_tiles_split_across_ctas_match_other_engine():
-    # 2560 x 2048 -> 20 x 8 = 160 tiles of 128 x 256 on 152 SMs: one full
-    # wave of whole tiles plus tail tiles split into pair-range chunks that
-    # add atomically.  Exactness makes the result independent of the split:
-    # it must equal the mma.sync e4m3 engine bit for bit.
+@pytest.mark.parametrize("pair", ["1", "0"])
+def test_tail_tiles_split_across_ctas_match_other_engine(pair, monkeypatch):
+    # 2560 x 2048: 160 tiles of 128 x 256 on 152 SMs, or 80 tiles of 256 x 256
+    # on the CTA pairs (about 76 clusters): a wave of whole tiles plus tail
+    # tiles split into pair-range chunks that add atomically.  Exactness makes
+    # the result independent of the split and of the tile form: it must equal
+    # the mma.sync e4m3 engine bit for bit.
+    monkeypatch.setenv("OZMP_TC_PAIR", pair)
     m, n, k = 2560, 2048, 192
     A, B = gen_problem("dd", m, n, k, phi=1.0, seed=13)
     Ad, Bd = to_dev(A), to_dev(B)
