@@ -547,6 +547,8 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
                     sc.items = (const tc::WorkItem*)((char*)b->meta + b->off_items);
                     sc.off = (const int*)((char*)b->meta + b->off_cta);
                     sc.ntiles = 0;
+                    sc.counter = nullptr;
+                    sc.nitems = 0;
                     tc::Prob dummy;
                     memset(&dummy, 0, sizeof(dummy));
                     CUtensorMap m0;

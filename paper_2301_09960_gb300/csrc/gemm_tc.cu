@@ -6,6 +6,9 @@
 namespace ozmp {
 namespace tc {
 
+// Items come from the per-CTA lists of the schedule, from a fixed stride over
+// the tiles, or (sc.counter set) from the dynamic feed, so that CTAs that run
+// faster take more items.
 // CG = 1: one CTA per 128 x bn tile.  CG = 2: a cluster of two CTAs per
 // 256 x 256 tile, one tcgen05.mma.cta_group::2 (M = 256) issued by the leader
 // (rank 0) reading both CTAs' shared memory; the leader's full barrier counts
@@ -27,7 +30,10 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
     uint64_t* accf = empty + NS;
     uint64_t* acce = accf + 2;
     uint64_t* done = acce + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    uint64_t* ring_full = done + 1;
+    uint64_t* ring_empty = ring_full + RING;
+    volatile int* ring = reinterpret_cast<volatile int*>(ring_empty + RING);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ring_empty + RING) + RING;
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     volatile int* fin_flag = reinterpret_cast<volatile int*>(tmem_slot + 2);
 
@@ -45,14 +51,52 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
         atomicOr(status, ST_TIMEOUT);
     };
 
+    // ---- item feed: the k-th item of this CTA; -1 past the end, -2 on timeout
+    const bool dyn = sc.counter != nullptr;
     int it_begin, it_end, it_step;
-    if (sc.items) { it_begin = sc.off[cid]; it_end = sc.off[cid + 1]; it_step = 1; }
+    if (sc.items) { it_begin = dyn ? 0 : sc.off[cid]; it_end = dyn ? 0 : sc.off[cid + 1]; it_step = 1; }
     else { it_begin = cid; it_end = sc.ntiles; it_step = ncl; }
+    const uint32_t ring_empty_cl = CG == 2 ? map_rank(saddr(ring_empty), 0) : saddr(ring_empty);
+    const uint32_t peer_ring = CG == 2 ? map_rank(saddr((const void*)ring), 1) : 0u;
+    const uint32_t peer_ring_full = CG == 2 ? map_rank(saddr(ring_full), 1) : 0u;
+    auto take = [&](int k, bool publisher, bool warp_wide) -> int {
+        if (!dyn) {
+            const int idx = it_begin + k * it_step;
+            return idx < it_end ? idx : -1;
+        }
+        const int r = k % RING;
+        const unsigned ph = (unsigned)((k / RING) & 1);
+        if (publisher) {
+            if (!mbar_wait<CG == 2>(&ring_empty[r], ph ^ 1u, abort_flag)) return -2;
+            const int idx = atomicAdd(sc.counter, 1);
+            ring[r] = idx;
+            if (CG == 2) {
+                st_cluster_u32(peer_ring + 4u * r, (uint32_t)idx);
+                mbar_arrive_cluster(peer_ring_full + 8u * r);   // release: the store is visible first
+            }
+            mbar_arrive(&ring_full[r]);
+            return idx < sc.nitems ? idx : -1;
+        }
+        // a warp-wide caller waits in lane 0 and broadcasts, so that the lanes
+        // cannot part on a timeout
+        int idx = -2;
+        if (!warp_wide || lane == 0) {
+            if (mbar_wait<CG == 2>(&ring_full[r], ph, abort_flag)) {
+                idx = ring[r];
+                if (CG == 2) mbar_arrive_cluster(ring_empty_cl + 8u * r);
+                else mbar_arrive(&ring_empty[r]);
+            }
+        }
+        if (warp_wide) idx = __shfl_sync(0xffffffffu, idx, 0);
+        if (idx == -2) return -2;
+        return idx < sc.nitems ? idx : -1;
+    };
 
     if (threadIdx.x == 0) {
         for (int x = 0; x < NS; ++x) { mbar_init(&full[x], 1); mbar_init(&empty[x], 1); }
         for (int x = 0; x < 2; ++x) { mbar_init(&accf[x], 1); mbar_init(&acce[x], 4 * CG); }
         mbar_init(done, 1);
+        for (int x = 0; x < RING; ++x) { mbar_init(&ring_full[x], 1); mbar_init(&ring_empty[x], ring_consumers(CG)); }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -81,7 +125,10 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
         if (lane == 0) {
             long long n = 0;
             bool ok = true;
-            for (int idx = it_begin; ok && idx < it_end; idx += it_step) {
+            for (int k = 0; ok; ++k) {
+                const int idx = take(k, rank == 0, false);
+                if (idx == -2) { ok = false; break; }
+                if (idx < 0) break;
                 Item it;
                 item_at<CG>(sc, &single, &tmA, &tmB, idx, it, rank);
                 const Prob p = *it.p;
@@ -125,7 +172,10 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
             long long n = 0;
             int buf = 0, uses[2] = {0, 0};
             bool ok = mbar_wait<CG == 2>(&acce[0], 1u, abort_flag);     // first use of buffer 0
-            for (int idx = it_begin; ok && idx < it_end; idx += it_step) {
+            for (int k = 0; ok; ++k) {
+                const int idx = take(k, false, false);
+                if (idx == -2) { ok = false; break; }
+                if (idx < 0) break;
                 Item it;
                 item_at<CG>(sc, &single, &tmA, &tmB, idx, it, rank);
                 const Prob p = *it.p;
@@ -187,7 +237,10 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
         int ev = 0;
         bool ok = true;
-        for (int idx = it_begin; ok && idx < it_end; idx += it_step) {
+        for (int k = 0; ok; ++k) {
+            const int idx = take(k, false, true);
+            if (idx == -2) { ok = false; break; }
+            if (idx < 0) break;
             Item it;
             item_at<CG>(sc, &single, &tmA, &tmB, idx, it, rank);
             const Prob p = *it.p;
@@ -213,7 +266,10 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                     const int buf = ev & 1;
                     const unsigned par = (unsigned)((ev >> 1) & 1);
                     ++ev;
-                    if (!mbar_wait<CG == 2>(&accf[buf], par, abort_flag)) { ok = false; break; }
+                    int got = 0;
+                    if (lane == 0) got = mbar_wait<CG == 2>(&accf[buf], par, abort_flag) ? 1 : 0;
+                    if (!__shfl_sync(0xffffffffu, got, 0)) { ok = false; break; }
+                    __syncwarp();
                     tc_fence_after();
                     const int fsh = p.d_only ? 0 : p.beta * (p.s + 1 - w.d);
                     const int li = fsh >> 4, off = fsh & 15;
@@ -366,7 +422,7 @@ bool tc_make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t kp, u
     return r == CUDA_SUCCESS;
 }
 
-int tc_schedule(int ntiles, int pairs, int sms, int* items, int* off, int* nitems, int* nslots) {
+int tc_schedule(int ntiles, int pairs, int sms, int* items, int* off, int* nitems, int* nslots, bool regroup) {
     if (sms < 1) sms = 1;
     const int waves = ntiles / sms, r = ntiles % sms;
     // chunks per tail tile: minimise waves + ceil(r c / sms) / c (+ a small per-chunk cost)
@@ -396,6 +452,14 @@ int tc_schedule(int ntiles, int pairs, int sms, int* items, int* off, int* nitem
             put(next, t, pa, pb, slot, c);
             next = (next + 1) % grid;
         }
+    }
+    if (!regroup) {
+        // one list in creation order (whole tiles, then the chunks of the tail
+        // tiles) for the dynamic feed; the CTA offsets are left unused
+        for (int cta = 0; cta <= grid; ++cta) off[cta] = 0;
+        *nitems = n;
+        *nslots = slots;
+        return grid;
     }
     // items regrouped per CTA
     std::vector<int> tmp(items, items + 6 * n);
@@ -476,8 +540,11 @@ cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t st) {
     sc.items = (const tc::WorkItem*)g.sched_items;
     sc.off = g.sched_off;
     sc.ntiles = (int)((g.mp / (tc::BM * cg)) * (g.np / tc::BN));
+    sc.counter = sc.items ? g.counter : nullptr;
+    sc.nitems = g.sched_nitems;
     if (sc.items && g.split_bytes) {
-        e = cudaMemsetAsync(g.sacc, 0, g.split_bytes, st);
+        // split limbs, chunk counters and the feed counter are one region
+        e = cudaMemsetAsync(g.sacc ? (void*)g.sacc : (void*)g.cnt_region, 0, g.split_bytes, st);
         if (e != cudaSuccess) return e;
     }
     const int grid = sc.items ? g.sched_grid : sc.ntiles;

@@ -35,13 +35,13 @@ namespace tc {
 constexpr int BM = 128, BN = 256, BK = 128, NST = 4, NT = 192;   // BN: widest tile
 constexpr unsigned STAGE_A = BM * BK, STAGE_B = BN * BK;
 constexpr unsigned TX_BYTES = STAGE_A + STAGE_B;
-constexpr size_t SMEM = 1024 + (size_t)NST * (STAGE_A + STAGE_B) + 256;
+constexpr size_t SMEM = 1024 + (size_t)NST * (STAGE_A + STAGE_B) + 512;
 // CTA-pair form (cta_group::2): a cluster of two CTAs owns a 256 x 256 tile;
 // each CTA stages its 128 rows of A and its half (128 rows) of the B tile,
 // so a stage is 32 KB per CTA and six stages fit
 constexpr int NST2 = 6;
 constexpr unsigned STAGE_B2 = (BN / 2) * BK;
-constexpr size_t SMEM2 = 1024 + (size_t)NST2 * (STAGE_A + STAGE_B2) + 256;
+constexpr size_t SMEM2 = 1024 + (size_t)NST2 * (STAGE_A + STAGE_B2) + 512;
 constexpr long long WAIT_LIMIT = 1ll << 26;   // try_wait polls before giving up (seconds)
 constexpr long long DRAIN_LIMIT = 1ll << 20;  // polls for copies / MMAs already in flight at the end
 
@@ -331,7 +331,18 @@ struct Sched {
     const WorkItem* items;     // null: tiles cta, cta + G, ... of the one problem, whole
     const int* off;            // items [off[cta], off[cta + 1]) belong to CTA cta
     int ntiles;                // no item list: tiles of the one problem
+    int* counter;              // non-null: items are taken in list order from this counter
+    int nitems;                //   (zeroed before the launch) instead of the per-CTA lists
 };
+
+// Dynamic item feed: the leader's producer takes the next item index from the
+// global counter and publishes it through a ring of RING slots (in both CTAs
+// of a pair); every other role reads it from its own CTA's ring and releases
+// the slot on the leader's `ring_empty` barrier.
+constexpr int RING = 4;
+// slot releases per ring entry: the leader's MMA issuer and 4 epilogue warps,
+// plus the peer's producer and 4 epilogue warps in the pair form
+__host__ __device__ constexpr unsigned ring_consumers(int cg) { return cg == 2 ? 10u : 5u; }
 
 struct Item {
     const Prob* p;

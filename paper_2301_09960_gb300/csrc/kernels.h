@@ -49,15 +49,19 @@ struct GemmArgs {
     int sched_grid;
     int64_t* sacc;             // split-tile limbs, zeroed before every launch
     int* cnt;                  // split-tile chunk counters (follow sacc)
-    size_t split_bytes;        // bytes of sacc + cnt
+    int* counter;              // dynamic item feed counter (follows cnt); null: per-CTA lists
+    int* cnt_region;           // start of the counters (cnt, then the feed counter)
+    int sched_nitems;
+    size_t split_bytes;        // bytes of sacc + cnt + counter
     int tc_cg;                 // 2: CTA-pair tiles (256 x 256, cta_group::2); else one CTA per tile
 };
 
 // Tile schedule of one tcgen05 problem (host): whole tiles in full waves over
 // `sms` CTAs; the tiles of a partial last wave (or of a problem with fewer
 // tiles than CTAs) split into pair-range chunks.  Writes items (6 ints each:
-// prob, tile, pa, pb, slot, nchunks) and CTA offsets; returns the grid.
-int tc_schedule(int ntiles, int pairs, int sms, int* items, int* off, int* nitems, int* nslots);
+// prob, tile, pa, pb, slot, nchunks), regrouped per CTA with CTA offsets when
+// `regroup` (else in creation order for the dynamic feed); returns the grid.
+int tc_schedule(int ntiles, int pairs, int sms, int* items, int* off, int* nitems, int* nslots, bool regroup);
 int tc_num_sms();
 int tc_num_pair_slots();   // co-resident clusters of two CTAs of the tcgen05 pair form
 

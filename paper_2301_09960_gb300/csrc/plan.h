@@ -27,6 +27,7 @@ struct ozmp_plan_s {
     int* sched_host;
     int sched_items, sched_slots, sched_grid;   // sched_slots: split-limb slots of single CTAs
     int tc_cg;                                   // 2: the schedule is over CTA-pair tiles
+    int tc_dyn;                                  // items taken from a counter (else per-CTA lists)
     size_t off_items, off_soff, off_sacc, split_bytes;
     void* sched_ws;
 };
@@ -216,8 +217,11 @@ inline GemmArgs gemm_args(ozmp_plan_s* p) {
         g.sched_off = (const int*)(w + p->off_soff);
         g.sched_grid = p->sched_grid;
         g.sacc = p->sched_slots ? (int64_t*)(w + p->off_sacc) : nullptr;
-        g.cnt = p->sched_slots ? (int*)(w + p->off_sacc + (size_t)p->sched_slots * p->nlimbs * 256 * 128 * 8)
-                               : nullptr;
+        int* cnt = (int*)(w + p->off_sacc + (size_t)p->sched_slots * p->nlimbs * 256 * 128 * 8);
+        g.cnt = p->sched_slots ? cnt : nullptr;
+        g.counter = p->tc_dyn ? cnt + p->sched_slots : nullptr;
+        g.cnt_region = cnt;
+        g.sched_nitems = p->sched_items;
         g.split_bytes = p->split_bytes;
         g.tc_cg = p->tc_cg;
     }
@@ -229,6 +233,8 @@ inline GemmArgs gemm_args(ozmp_plan_s* p) {
 // a CTA pair when the padded row count allows it (OZMP_TC_PAIR=0 in the
 // environment keeps one 128 x 256 tile per CTA), the schedule then running
 // over clusters (half the SMs) and every split slot holding two CTAs' rows.
+// The items are taken from a counter in list order (OZMP_TC_DYNAMIC=0: fixed
+// per-CTA lists).
 inline ozmp_status plan_schedule(ozmp_plan_s* p) {
     if (p->form != OZMP_FORM_FP8 || p->m == 0 || p->n == 0 || p->k == 0) return OZMP_OK;
     const char* env = getenv("OZMP_TC_PAIR");
@@ -240,7 +246,9 @@ inline ozmp_status plan_schedule(ozmp_plan_s* p) {
     if (!p->sched_host) return OZMP_ERR_NOMEM;
     int* items = p->sched_host;
     int* off = p->sched_host + (size_t)6 * ntiles * 8;
-    p->sched_grid = tc_schedule(ntiles, pairs, sms, items, off, &p->sched_items, &p->sched_slots);
+    const char* dyn = getenv("OZMP_TC_DYNAMIC");
+    p->tc_dyn = !(dyn && dyn[0] == '0');
+    p->sched_grid = tc_schedule(ntiles, pairs, sms, items, off, &p->sched_items, &p->sched_slots, !p->tc_dyn);
     p->sched_slots *= p->tc_cg;
     // CTA offsets right after the items in the host copy
     int* off2 = items + 6 * p->sched_items;
@@ -249,7 +257,8 @@ inline ozmp_status plan_schedule(ozmp_plan_s* p) {
     p->off_items = o; o = align256(o + (size_t)p->sched_items * 24);
     p->off_soff = o; o = align256(o + (size_t)(p->sched_grid + 1) * 4);
     p->off_sacc = o;
-    p->split_bytes = (size_t)p->sched_slots * p->nlimbs * 256 * 128 * 8 + (size_t)p->sched_slots * 4;
+    // split limbs, their chunk counters and the item-feed counter, zeroed before each launch
+    p->split_bytes = (size_t)p->sched_slots * p->nlimbs * 256 * 128 * 8 + (size_t)p->sched_slots * 4 + 4;
     o = align256(o + p->split_bytes);
     p->ws_bytes = o;
     return OZMP_OK;
