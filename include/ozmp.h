@@ -247,6 +247,19 @@ ozmp_status ozmp_plan_split(ozmp_plan plan, const void* const* A, int64_t lda,
 ozmp_status ozmp_plan_multiply(ozmp_plan plan, void* const* C, int64_t ldc);
 ozmp_status ozmp_plan_diagonal(ozmp_plan plan, int d, int64_t* T);
 
+/* Kernel timing (instrumentation; the paper has no counterpart).
+ * ozmp_plan_set_timing: with nslots > 0 the plan owns a ring of nslots CUDA
+ *   event pairs and, at every ozmp_plan_execute / ozmp_plan_multiply, records
+ *   one pair on its stream immediately around the slice-product kernel (the
+ *   tcgen05 / mma.sync / DMMA main loop, without the rounding pass or the
+ *   split).  nslots = 0 frees the events.  Errors: INVALID_ARG (null or
+ *   batched plan, nslots < 0 or > 4096), NOMEM, CUDA (event creation failed).
+ * ozmp_plan_read_timing: waits for and writes the durations in milliseconds
+ *   of the last min(n, calls recorded, nslots) product kernels, oldest first,
+ *   into ms[0 .. *count - 1] (host memory, caller-owned). */
+ozmp_status ozmp_plan_set_timing(ozmp_plan plan, int nslots);
+ozmp_status ozmp_plan_read_timing(ozmp_plan plan, float* ms, int n, int* count);
+
 /* Version string of the library build. */
 const char* ozmp_version(void);
 

@@ -24,7 +24,7 @@ __all__ = [
     "Status", "Prec", "Form", "OzmpError", "PlanInfo", "Plan", "load", "colmajor",
     "ozmp_plan_create", "ozmp_plan_destroy", "ozmp_plan_get_info", "ozmp_plan_set_workspace",
     "ozmp_plan_set_stream", "ozmp_plan_execute", "ozmp_plan_get_status", "ozmp_plan_split",
-    "ozmp_plan_diagonal", "ozmp_plan_multiply", "ozmp_gemm_dd", "ozmp_gemm_td", "ozmp_gemm_qd", "ozmp_gemm_ts", "ozmp_gemm_dd_noalloc", "ozmp_gemm_batched", "Problem", "ozmp_gemm_naive",
+    "ozmp_plan_diagonal", "ozmp_plan_multiply", "ozmp_plan_set_timing", "ozmp_plan_read_timing", "ozmp_gemm_dd", "ozmp_gemm_td", "ozmp_gemm_qd", "ozmp_gemm_ts", "ozmp_gemm_dd_noalloc", "ozmp_gemm_batched", "Problem", "ozmp_gemm_naive",
     "ozmp_set_stream", "ozmp_set_form", "ozmp_last_status", "ozmp_version", "gemm", "EXP_ZERO",
 ]
 
@@ -112,6 +112,8 @@ SIGNATURES = {
     "ozmp_plan_split": [_VP, _PP, _I64, _PP, _I64],
     "ozmp_plan_diagonal": [_VP, ctypes.c_int, _VP],
     "ozmp_plan_multiply": [_VP, _PP, _I64],
+    "ozmp_plan_set_timing": [_VP, ctypes.c_int],
+    "ozmp_plan_read_timing": [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "ozmp_gemm_dd": [_I64, _I64, _I64, _PP, _I64, _PP, _I64, _PP, _I64, ctypes.c_int],
     "ozmp_gemm_td": [_I64, _I64, _I64, _PP, _I64, _PP, _I64, _PP, _I64, ctypes.c_int],
     "ozmp_gemm_qd": [_I64, _I64, _I64, _PP, _I64, _PP, _I64, _PP, _I64, ctypes.c_int],
@@ -239,6 +241,18 @@ def ozmp_plan_split(h, A, B):
 def ozmp_plan_multiply(h, C):
     pc, kc = _ptrs(C)
     _check(load().ozmp_plan_multiply(h, pc, _ld(C[0])), "ozmp_plan_multiply")
+
+
+def ozmp_plan_set_timing(h, nslots: int):
+    _check(load().ozmp_plan_set_timing(h, nslots), "ozmp_plan_set_timing")
+
+
+def ozmp_plan_read_timing(h, n: int):
+    """Durations (ms) of the last product kernels, oldest first."""
+    buf = (ctypes.c_float * max(n, 1))()
+    cnt = ctypes.c_int(0)
+    _check(load().ozmp_plan_read_timing(h, buf, n, ctypes.byref(cnt)), "ozmp_plan_read_timing")
+    return [float(buf[i]) for i in range(cnt.value)]
 
 
 def ozmp_plan_diagonal(h, d: int, T):
@@ -374,6 +388,12 @@ class Plan:
 
     def multiply(self, C):
         ozmp_plan_multiply(self.h, C)
+
+    def set_timing(self, nslots: int):
+        ozmp_plan_set_timing(self.h, nslots)
+
+    def read_timing(self, n: int):
+        return ozmp_plan_read_timing(self.h, n)
 
     def diagonal(self, d):
         import torch

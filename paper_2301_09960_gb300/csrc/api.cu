@@ -30,6 +30,14 @@ ozmp_status ozmp_plan_create(ozmp_plan* plan, ozmp_prec prec, int64_t m, int64_t
     return OZMP_OK;
 }
 
+static void free_timing(ozmp_plan p) {
+    for (int x = 0; x < 2 * p->tev_n; ++x) cudaEventDestroy(p->tev[x]);
+    delete[] p->tev;
+    p->tev = nullptr;
+    p->tev_n = 0;
+    p->tev_calls = 0;
+}
+
 ozmp_status ozmp_plan_destroy(ozmp_plan p) {
     if (!p) return OZMP_ERR_INVALID_ARG;
     if (p->batch) {
@@ -42,6 +50,7 @@ ozmp_status ozmp_plan_destroy(ozmp_plan p) {
         cudaStreamSynchronize(p->stream);
         cudaFree(p->ws);
     }
+    free_timing(p);
     delete[] p->sched_host;
     delete p;
     return OZMP_OK;
@@ -107,6 +116,7 @@ ozmp_status ozmp_plan_execute(ozmp_plan p, const void* const* A, int64_t lda, co
     GemmArgs g = gemm_args(p);
     for (int c = 0; c < 4; ++c) g.C[c] = (c < p->q) ? C[c] : nullptr;
     g.ldc = ldc;
+    take_timing(p, g);
     return launch_gemm(g, p->stream) == cudaSuccess ? OZMP_OK : OZMP_ERR_CUDA;
 }
 
@@ -121,6 +131,7 @@ ozmp_status ozmp_plan_multiply(ozmp_plan p, void* const* C, int64_t ldc) {
     GemmArgs g = gemm_args(p);
     for (int c = 0; c < 4; ++c) g.C[c] = (c < p->q) ? C[c] : nullptr;
     g.ldc = ldc;
+    take_timing(p, g);
     return launch_gemm(g, p->stream) == cudaSuccess ? OZMP_OK : OZMP_ERR_CUDA;
 }
 
@@ -132,6 +143,39 @@ ozmp_status ozmp_plan_diagonal(ozmp_plan p, int d, int64_t* T) {
     g.T = T;
     g.sched_items = nullptr;   // the diagnostic walks one diagonal, one whole tile per CTA
     return launch_gemm(g, p->stream) == cudaSuccess ? OZMP_OK : OZMP_ERR_CUDA;
+}
+
+
+ozmp_status ozmp_plan_set_timing(ozmp_plan p, int nslots) {
+    if (!p || p->batch || nslots < 0 || nslots > 4096) return OZMP_ERR_INVALID_ARG;
+    free_timing(p);
+    if (!nslots) return OZMP_OK;
+    p->tev = new (std::nothrow) cudaEvent_t[2 * (size_t)nslots];
+    if (!p->tev) return OZMP_ERR_NOMEM;
+    for (int x = 0; x < 2 * nslots; ++x) {
+        if (cudaEventCreate(&p->tev[x]) != cudaSuccess) {
+            for (int y = 0; y < x; ++y) cudaEventDestroy(p->tev[y]);
+            delete[] p->tev;
+            p->tev = nullptr;
+            return OZMP_ERR_CUDA;
+        }
+    }
+    p->tev_n = nslots;
+    return OZMP_OK;
+}
+
+ozmp_status ozmp_plan_read_timing(ozmp_plan p, float* ms, int n, int* count) {
+    if (!p || !count || n < 0 || (n > 0 && !ms)) return OZMP_ERR_INVALID_ARG;
+    const long long have = p->tev_calls < p->tev_n ? p->tev_calls : p->tev_n;
+    const int got = (int)(have < n ? have : n);
+    for (int x = 0; x < got; ++x) {
+        const int slot = (int)((p->tev_calls - got + x) % p->tev_n);
+        if (cudaEventSynchronize(p->tev[2 * slot + 1]) != cudaSuccess ||
+            cudaEventElapsedTime(&ms[x], p->tev[2 * slot], p->tev[2 * slot + 1]) != cudaSuccess)
+            return OZMP_ERR_CUDA;
+    }
+    *count = got;
+    return OZMP_OK;
 }
 
 ozmp_status ozmp_plan_get_status(ozmp_plan p, ozmp_status* device_status) {

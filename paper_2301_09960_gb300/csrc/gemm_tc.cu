@@ -262,7 +262,8 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                 const bool diag_end = (w.t == w.d - 1);
                 if (since == p.ppd || diag_end || pi == it.pb - 1) {
                     since = 0;
-                    const bool last = (pi == it.pb - 1);
+                    // the last drain rounds the tile into C unless a separate pass does
+                    const bool last = (pi == it.pb - 1) && !p.defer;
                     const int buf = ev & 1;
                     const unsigned par = (unsigned)((ev >> 1) & 1);
                     ++ev;
@@ -358,6 +359,29 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
             asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem) : "memory");
     }
     if (CG == 2) cluster_sync();
+}
+
+// Rounding pass of the single-problem path: one thread per element of C
+// normalises the element's carry-save limbs 0 .. nl-1 (from its tile's split
+// slot when the tile was split into chunks, else from acc) and rounds them
+// canonically into the q components.  Bound by the limb reads.
+template <int NW>
+__global__ void __launch_bounds__(256) k_tc_finish(const GemmArgs g, int nl, const int* tile_slot, int tile_rows,
+                                                   int slot_limbs) {
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= g.m) return;
+    const size_t sstride = (size_t)BN * BM;
+    for (int64_t j = blockIdx.y; j < g.n; j += gridDim.y) {
+        const int slot =
+            tile_slot ? tile_slot[(i / tile_rows) + (j / BN) * (g.mp / tile_rows)] : -1;
+        if (slot < 0) {
+            finish_element<NW>(g, nl, g.acc, (size_t)g.mp * g.np, (size_t)j * g.mp + i, i, j, 0, 0, false);
+        } else {
+            const int cta = slot * (tile_rows / BM) + (int)((i % tile_rows) / BM);
+            finish_element<NW>(g, nl, g.sacc + (size_t)cta * slot_limbs * sstride, sstride,
+                               (size_t)(j % BN) * BM + (size_t)(i % BM), i, j, 0, 0, false);
+        }
+    }
 }
 
 }  // namespace tc
@@ -534,6 +558,7 @@ cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t st) {
     p.d_only = g.d_only;
     p.sacc = g.sacc;
     p.cnt = g.cnt;
+    p.defer = 1;
     tc::Sched sc;
     sc.probs = nullptr;
     sc.maps = nullptr;
@@ -548,8 +573,25 @@ cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t st) {
         if (e != cudaSuccess) return e;
     }
     const int grid = sc.items ? g.sched_grid : sc.ntiles;
-    if (cg == 2) return tc_launch_pair(sc, p, ma, mb, g.status, grid, st);
-    return tc_launch(sc, p, ma, mb, g.status, grid, st);
+    if (g.tev_start) cudaEventRecord(g.tev_start, st);
+    e = cg == 2 ? tc_launch_pair(sc, p, ma, mb, g.status, grid, st) : tc_launch(sc, p, ma, mb, g.status, grid, st);
+    if (g.tev_stop) cudaEventRecord(g.tev_stop, st);
+    if (e != cudaSuccess) return e;
+    // the rounding pass: limbs 0 .. (beta (s - 1)) / 16 hold data (the last drain's shift)
+    const int nl = g.d_only ? 1 : (g.beta * (g.s - 1)) / 16 + 1;
+    const int slot_limbs = 4 * g.acc_words + 1;
+    const dim3 fg((unsigned)((g.m + 255) / 256), (unsigned)(g.n < 65535 ? g.n : 65535));
+    const int* ts = sc.items ? g.tile_slot : nullptr;
+    const int rows = tc::BM * cg;
+    switch (g.acc_words) {
+        case 2: tc::k_tc_finish<2><<<fg, 256, 0, st>>>(g, nl, ts, rows, slot_limbs); break;
+        case 3: tc::k_tc_finish<3><<<fg, 256, 0, st>>>(g, nl, ts, rows, slot_limbs); break;
+        case 4: tc::k_tc_finish<4><<<fg, 256, 0, st>>>(g, nl, ts, rows, slot_limbs); break;
+        case 5: tc::k_tc_finish<5><<<fg, 256, 0, st>>>(g, nl, ts, rows, slot_limbs); break;
+        case 6: tc::k_tc_finish<6><<<fg, 256, 0, st>>>(g, nl, ts, rows, slot_limbs); break;
+        default: tc::k_tc_finish<7><<<fg, 256, 0, st>>>(g, nl, ts, rows, slot_limbs); break;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace ozmp

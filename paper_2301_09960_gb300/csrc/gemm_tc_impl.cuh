@@ -296,6 +296,7 @@ struct Prob {
     int* cnt;              // split tiles: chunks finished per slot, zeroed before the launch
     int64_t m, n, mp, np, kp, ldc;
     int q, is_f32, s, beta, ppd, acc_words, bn, d_only;
+    int defer;             // 1: the limbs are rounded into C by a separate pass after the launch
 };
 
 // adapter: the fields of one problem the limb epilogue reads, in GemmArgs form

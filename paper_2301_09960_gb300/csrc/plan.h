@@ -28,7 +28,12 @@ struct ozmp_plan_s {
     int sched_items, sched_slots, sched_grid;   // sched_slots: split-limb slots of single CTAs
     int tc_cg;                                   // 2: the schedule is over CTA-pair tiles
     int tc_dyn;                                  // items taken from a counter (else per-CTA lists)
-    size_t off_items, off_soff, off_sacc, split_bytes;
+    // kernel timing ring (ozmp_plan_set_timing): tev[2 x] / tev[2 x + 1] around call x mod tev_n
+    cudaEvent_t* tev;
+    int tev_n;
+    long long tev_calls;
+    size_t off_items, off_soff, off_tslot, off_sacc, split_bytes;
+    int sched_ntiles;
     void* sched_ws;
 };
 
@@ -221,11 +226,21 @@ inline GemmArgs gemm_args(ozmp_plan_s* p) {
         g.cnt = p->sched_slots ? cnt : nullptr;
         g.counter = p->tc_dyn ? cnt + p->sched_slots : nullptr;
         g.cnt_region = cnt;
+        g.tile_slot = (const int*)(w + p->off_tslot);
         g.sched_nitems = p->sched_items;
         g.split_bytes = p->split_bytes;
         g.tc_cg = p->tc_cg;
     }
     return g;
+}
+
+// the timing pair of the next product launch (none without a timing ring)
+inline void take_timing(ozmp_plan_s* p, GemmArgs& g) {
+    if (!p->tev_n) return;
+    const int x = (int)(p->tev_calls % p->tev_n);
+    g.tev_start = p->tev[2 * x];
+    g.tev_stop = p->tev[2 * x + 1];
+    p->tev_calls++;
 }
 
 // tcgen05 form: build the tile schedule and append its workspace regions
@@ -242,7 +257,8 @@ inline ozmp_status plan_schedule(ozmp_plan_s* p) {
     const int ntiles = (int)((p->mp / (128 * p->tc_cg)) * (p->np / 256));
     const int pairs = p->s * (p->s + 1) / 2;
     const int sms = p->tc_cg == 2 ? tc_num_pair_slots() : tc_num_sms();
-    p->sched_host = new (std::nothrow) int[(size_t)6 * ntiles * 8 + sms + 1];
+    p->sched_host = new (std::nothrow) int[(size_t)6 * ntiles * 8 + sms + 1 + ntiles];
+    p->sched_ntiles = ntiles;
     if (!p->sched_host) return OZMP_ERR_NOMEM;
     int* items = p->sched_host;
     int* off = p->sched_host + (size_t)6 * ntiles * 8;
@@ -253,9 +269,15 @@ inline ozmp_status plan_schedule(ozmp_plan_s* p) {
     // CTA offsets right after the items in the host copy
     int* off2 = items + 6 * p->sched_items;
     for (int c = 0; c <= p->sched_grid; ++c) off2[c] = off[c];
+    // then the split-limb slot of every tile (-1: whole)
+    int* tslot = off2 + p->sched_grid + 1;
+    for (int t = 0; t < ntiles; ++t) tslot[t] = -1;
+    for (int x = 0; x < p->sched_items; ++x)
+        if (items[6 * x + 4] >= 0) tslot[items[6 * x + 1]] = items[6 * x + 4];
     size_t o = p->ws_bytes;
     p->off_items = o; o = align256(o + (size_t)p->sched_items * 24);
     p->off_soff = o; o = align256(o + (size_t)(p->sched_grid + 1) * 4);
+    p->off_tslot = o; o = align256(o + (size_t)ntiles * 4);
     p->off_sacc = o;
     // split limbs, their chunk counters and the item-feed counter, zeroed before each launch
     p->split_bytes = (size_t)p->sched_slots * p->nlimbs * 256 * 128 * 8 + (size_t)p->sched_slots * 4 + 4;
@@ -271,7 +293,9 @@ inline ozmp_status plan_upload_schedule(ozmp_plan_s* p) {
     if (cudaMemcpyAsync((char*)p->ws + p->off_items, p->sched_host, bytes, cudaMemcpyHostToDevice, p->stream) !=
             cudaSuccess ||
         cudaMemcpyAsync((char*)p->ws + p->off_soff, p->sched_host + 6 * p->sched_items,
-                        (size_t)(p->sched_grid + 1) * 4, cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
+                        (size_t)(p->sched_grid + 1) * 4, cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+        cudaMemcpyAsync((char*)p->ws + p->off_tslot, p->sched_host + 6 * p->sched_items + p->sched_grid + 1,
+                        (size_t)p->sched_ntiles * 4, cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
         return OZMP_ERR_CUDA;
     p->sched_ws = p->ws;
     return OZMP_OK;

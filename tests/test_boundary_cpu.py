@@ -73,6 +73,20 @@ def test_plan_rejects_bad_arguments():
     oz.ozmp_plan_destroy(h)
 
 
+def test_timing_ring_argument_checks():
+    # no CUDA call is made on these paths
+    for bad in (-1, 4097):
+        h = oz.ozmp_plan_create(oz.Prec.DD, 64, 64, 64, oz.Form.FP8, 0, None)
+        with pytest.raises(oz.OzmpError) as e:
+            oz.ozmp_plan_set_timing(h, bad)
+        assert e.value.status == oz.Status.ERR_INVALID_ARG
+        oz.ozmp_plan_set_timing(h, 0)
+        assert oz.ozmp_plan_read_timing(h, 4) == []
+        oz.ozmp_plan_destroy(h)
+    with pytest.raises(oz.OzmpError):
+        oz.ozmp_plan_set_timing(None, 1)
+
+
 def test_group_schedule_keeps_horner_value_below_2_62():
     for prec in (oz.Prec.DD, oz.Prec.QD):
         for form in (oz.Form.FP8, oz.Form.INT8, oz.Form.FP64):

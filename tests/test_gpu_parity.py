@@ -238,6 +238,33 @@ def test_nondefault_stream_and_repeat():
         assert torch.equal(x, y)
 
 
+@pytest.mark.parametrize("form", ["fp8", "int8"])
+def test_kernel_timing_ring(form):
+    # the plan's event ring times the product kernel alone: one duration per
+    # multiply, the ring keeps the last nslots, and it never exceeds the stage
+    A, B = gen_problem("dd", 520, 300, 260, seed=12)
+    Ad, Bd = to_dev(A), to_dev(B)
+    p = oz.Plan("dd", 520, 300, 260, form, 0)
+    C = [torch.empty((300, 520), dtype=torch.float64, device="cuda").T for _ in range(2)]
+    p.split(Ad, Bd)
+    assert p.read_timing(4) == []
+    p.set_timing(3)
+    stage = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        p.multiply(C)
+        e1.record()
+        torch.cuda.synchronize()
+        stage.append(e0.elapsed_time(e1))
+    t = p.read_timing(8)
+    assert len(t) == 3 and all(0 < x <= y + 1e-3 for x, y in zip(t, stage[2:]))
+    p.set_timing(0)
+    assert p.read_timing(8) == []
+    with pytest.raises(oz.OzmpError):
+        p.set_timing(-1)
+
+
 def _adversarial(q, rows, cols, seed, dtype=np.float64):
     """Components at exact powers of two with tiny tails of either sign,
     spans far beyond 128 bits, cancelling leading pairs and zeros: every
