@@ -15,7 +15,7 @@ static cudaError_t exponents_impl(const SplitArgs& g, cudaStream_t st) {
     if (mx == 0) mx = 1;
     k_init_exponents<<<(unsigned)((mx + 255) / 256), 256, 0, st>>>(g.E, g.mp, g.F, g.np, g.status);
     if (g.m > 0 && g.k > 0) {
-        int kchunk = 256;
+        int kchunk = 64;
         dim3 gr((unsigned)((g.m + 255) / 256), (unsigned)((g.k + kchunk - 1) / kchunk));
         k_exp_rows<T><<<gr, 256, 0, st>>>(a, g.m, g.k, kchunk, g.E, g.status);
     }

@@ -34,6 +34,25 @@ __device__ __forceinline__ bool load_elem(const Operand<T>& op, int64_t idx, T (
     return decode_all<T>(v, op.q, c, Ptop);
 }
 
+// the components of element idx (zeros when !inside), loaded without any
+// arithmetic so that a thread's loads of several elements are all in flight
+// before the first one is decoded
+template <typename T>
+__device__ __forceinline__ void load_raw(const Operand<T>& op, bool inside, int64_t idx, T (&v)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = (inside && i < op.q) ? op.c[i][idx] : (T)0;
+}
+
+// exponent of one loaded element; false for a non-finite component
+template <typename T>
+__device__ __forceinline__ bool exponent_loaded(const T (&v)[4], int q, int& e) {
+    Comp c[4];
+    int Ptop;
+    const bool ok = decode_all<T>(v, q, c, Ptop);
+    e = exponent_of<T>(c, v, q, Ptop);
+    return ok;
+}
+
 // ---------------------------------------------------------------------------
 // K1: exponents
 // ---------------------------------------------------------------------------
@@ -48,13 +67,17 @@ __device__ __forceinline__ void exp_rows_body(Operand<T> a, int64_t m, int64_t k
     int64_t p1 = p0 + kchunk < k ? p0 + kchunk : k;
     int emax = OZMP_EXP_ZERO;
     bool ok = true;
-    for (int64_t p = p0; p < p1; ++p) {
-        Comp c[4];
-        T v[4];
-        int Ptop;
-        ok &= load_elem<T>(a, i + p * a.ld, v, c, Ptop);
-        int e = exponent_of<T>(c, v, a.q, Ptop);
-        emax = e > emax ? e : emax;
+    constexpr int U = 4;   // elements whose loads are issued together
+    for (int64_t p = p0; p < p1; p += U) {
+        T v[U][4];
+#pragma unroll
+        for (int u = 0; u < U; ++u) load_raw<T>(a, p + u < p1, i + (p + u) * a.ld, v[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            int e;
+            ok &= exponent_loaded<T>(v[u], a.q, e);
+            emax = e > emax ? e : emax;
+        }
     }
     if (emax != OZMP_EXP_ZERO) atomicMax(&E[i], emax);
     if (!ok) atomicOr(status, ST_NONFINITE);
@@ -76,13 +99,17 @@ __device__ __forceinline__ void exp_cols_body(Operand<T> b, int64_t k, int64_t n
     if (j >= n) return;
     int emax = OZMP_EXP_ZERO;
     bool ok = true;
-    for (int64_t p = lane; p < k; p += 32) {
-        Comp c[4];
-        T v[4];
-        int Ptop;
-        ok &= load_elem<T>(b, p + j * b.ld, v, c, Ptop);
-        int e = exponent_of<T>(c, v, b.q, Ptop);
-        emax = e > emax ? e : emax;
+    constexpr int U = 4;   // elements whose loads are issued together
+    for (int64_t p = lane; p < k; p += 32 * U) {
+        T v[U][4];
+#pragma unroll
+        for (int u = 0; u < U; ++u) load_raw<T>(b, p + 32 * u < k, p + 32 * u + j * b.ld, v[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            int e;
+            ok &= exponent_loaded<T>(v[u], b.q, e);
+            emax = e > emax ? e : emax;
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -138,6 +165,20 @@ __device__ __forceinline__ int window_of(const Operand<T>& op, bool inside, int6
     return digit_window<NW, T>(c, v, op.q, Erow, w);
 }
 
+// the same on components already loaded (zeros outside the matrix)
+template <typename T, int NW>
+__device__ __forceinline__ int window_loaded(const T (&v)[4], int q, int Erow, uint64_t (&w)[NW]) {
+    Comp c[4];
+    int Ptop;
+    decode_all<T>(v, q, c, Ptop);
+    if (Ptop == -100000 || Erow == OZMP_EXP_ZERO) {
+#pragma unroll
+        for (int j = 0; j < NW; ++j) w[j] = 0;
+        return 0;
+    }
+    return digit_window<NW, T>(c, v, q, Erow, w);
+}
+
 // Rows of A (column-major) -> Adig[(t * mp + i) * kp + p], 1-byte digits.
 // Tile: 32 rows x 64 columns, 256 threads; thread (row ri, quad) handles
 // 4 consecutive columns of one row (two quads per thread); the 4 digits of
@@ -157,11 +198,14 @@ __device__ __forceinline__ void split_rows_b1_body(Operand<T> a, int64_t m, int6
         const int qd = (threadIdx.x >> 5) + 8 * h;
         uint64_t w[4][NW];
         int sign[4];
+        T v[4][4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int64_t p = p0 + 4 * qd + e;
-            sign[e] = window_of<T, NW>(a, i < m && p < k, i + p * a.ld, Erow, w[e]);
+            load_raw<T>(a, i < m && p < k, i + p * a.ld, v[e]);
         }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) sign[e] = window_loaded<T, NW>(v[e], a.q, Erow, w[e]);
 #pragma unroll
         for (int t = 1; t <= DigitTraits<FORM>::MAXS; ++t)
             if (t <= s) sw[((t - 1) * TI + ri) * QW + qd] = pack4<FORM, NW>(w, sign, t);
@@ -193,11 +237,11 @@ __device__ __forceinline__ void split_cols_b1_body(Operand<T> b, int64_t k, int6
     const int Ecol = (j < n) ? F[j] : OZMP_EXP_ZERO;
     uint64_t w[4][NW];
     int sign[4];
+    T v[4][4];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const int64_t p = p0 + e;
-        sign[e] = window_of<T, NW>(b, j < n && p < k, p + j * b.ld, Ecol, w[e]);
-    }
+    for (int e = 0; e < 4; ++e) load_raw<T>(b, j < n && p0 + e < k, p0 + e + j * b.ld, v[e]);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) sign[e] = window_loaded<T, NW>(v[e], b.q, Ecol, w[e]);
 #pragma unroll
     for (int t = 1; t <= DigitTraits<FORM>::MAXS; ++t)
         if (t <= s)
