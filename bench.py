@@ -383,6 +383,12 @@ def main():
     else:
         peak, peak_note = 1.05, "DMMA mma.sync f64 microbenchmark on this GB300 (no MEASURED_PEAKS entry)"
     sbytes = splitter_bytes(q, w, m, n, k, info.nslices, info.digit_bytes)
+    # DRAM bytes per launch of the product kernel, from the ncu capture in
+    # profiles/k_gemm_tc_dd4096_s12.md scaled to this launch (reads by pairs,
+    # limb writes by drains); only for the kernel and workload captured there
+    traffic = None
+    if oz.Form(info.form) == oz.Form.FP8 and args.prec == "dd" and m == n == k == 4096 and info.nslices == 32:
+        traffic = 7.256e9 * 528 / 78 + 1.523e9 * 46 / 12
 
     line = {
         "metric": metric, "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
@@ -395,7 +401,7 @@ def main():
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 gpu",
                    "l2": "inputs larger than L2 (A, B and the digit workspace each exceed 129 MB)"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": {oz.Form.FP8: "k_gemm_tc (tcgen05)", oz.Form.FP8_MMA: "k_gemm_b1<FP8> (mma.sync)",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": {oz.Form.FP8: "k_gemm_tc (tcgen05)", oz.Form.FP8_MMA: "k_gemm_b1<FP8> (mma.sync)",
                                 oz.Form.INT8: "k_gemm_b1<INT8> (mma.sync)"}.get(oz.Form(info.form), "k_gemm_f64 (DMMA)"),
                      "peak_source": peak_note,
                      # back-to-back steps hold the GPU under its power cap: the sustained
