@@ -4,7 +4,9 @@
  * C ABI of the library.  It computes C := A * B (paper, Sec. 1 problem
  * statement; Sec. 3, Algorithm 1) for multi-component operands: every
  * element is the exact sum of q components, DD/TD/QD = 2/3/4 binary64
- * words, TS = 3 binary32 words (Sec. 1).
+ * words, TS = 3 binary32 words (Sec. 1), and more generally any q from 2
+ * to OZMP_MAX_COMPONENTS binary64 words (about 53 q bits; Sec. 5 compares
+ * the scheme with arbitrary-precision arithmetic of 212 to 742 bits).
  *
  * Layout and ownership (every entry point):
  *   - Matrices are column-major (BLAS convention of the problem C := AB).
@@ -60,8 +62,15 @@ typedef enum {
     OZMP_ERR_TIMEOUT = 7       /* device status: a bounded wait in the batched scheduler gave up */
 } ozmp_status;
 
-/* precision of the operands (component count and word type) */
+/* precision of the operands (component count and word type).  A value q
+ * with 2 <= q <= OZMP_MAX_COMPONENTS is q binary64 components (OZMP_DD,
+ * OZMP_TD and OZMP_QD are q = 2, 3, 4; OZMP_PREC_Q(q) names the others);
+ * OZMP_TS is 3 binary32 components.  The automatic slice count targets a
+ * normwise error of 2^(-50 q) for q binary64 components and 2^-66 for TS.
+ * More than 4 components are provided by the FP8 (tcgen05) form only. */
 typedef enum { OZMP_DD = 2, OZMP_TD = 3, OZMP_QD = 4, OZMP_TS = 103 } ozmp_prec;
+#define OZMP_MAX_COMPONENTS 16
+#define OZMP_PREC_Q(q) ((ozmp_prec)(q))
 
 /* digit form of the slice products */
 typedef enum {
@@ -74,8 +83,11 @@ typedef enum {
 
 /* all-zero row/column exponent */
 #define OZMP_EXP_ZERO ((int32_t)(-2147483647 - 1))
-/* largest slice count */
-#define OZMP_MAX_SLICES 64
+/* largest slice count accepted as an argument; each form provides fewer:
+ * FP8 (tcgen05) up to 239 (beta s + 65 <= 1024 window bits), FP8_MMA 64,
+ * INT8 36, FP64 up to beta s <= 376; above the form's limit plan creation
+ * returns OZMP_ERR_UNSUPPORTED */
+#define OZMP_MAX_SLICES 256
 
 /* cudaStream_t, passed as an opaque pointer (NULL = the legacy default stream) */
 typedef void* ozmp_stream;
@@ -104,7 +116,8 @@ typedef struct {
  * Sec. 3, Algorithm 1 (the choice of D, here nslices) and Sec. 3's remark
  * that the needed slice count depends on the data.
  *   nslices = 0 chooses s from the precision's target (2^-100 DD, 2^-150 TD,
- *   2^-200 QD, 2^-66 TS) with a guard of log2 k + 16 bits; 1..64 forces s.
+ *   2^-200 QD, 2^(-50 q) for q binary64 components, 2^-66 TS) with a guard
+ *   of log2 k + 16 bits; 1..OZMP_MAX_SLICES forces s (see the form limits).
  *   stream: stream used by later executions through this plan.
  * The plan allocates its workspace lazily on first execution unless one is
  * supplied with ozmp_plan_set_workspace.  Returns INVALID_ARG for bad
@@ -155,6 +168,11 @@ ozmp_status ozmp_gemm_qd(int64_t m, int64_t n, int64_t k, const double* const A[
 ozmp_status ozmp_gemm_ts(int64_t m, int64_t n, int64_t k, const float* const A[3], int64_t lda,
                          const float* const B[3], int64_t ldb, float* const C[3], int64_t ldc,
                          int nslices);
+/* q binary64 components, 2 <= q <= OZMP_MAX_COMPONENTS (A, B, C: arrays of q
+ * device pointers); INVALID_ARG for q out of range.  Sec. 5's multiple
+ * precision beyond QD. */
+ozmp_status ozmp_gemm_md(int q, int64_t m, int64_t n, int64_t k, const double* const* A, int64_t lda,
+                         const double* const* B, int64_t ldb, double* const* C, int64_t ldc, int nslices);
 
 /*
  * ozmp_gemm_dd_noalloc -- the double-double product (as ozmp_gemm_dd, form

@@ -30,13 +30,15 @@ import numpy as np
 __all__ = ["PRECISIONS", "components_of", "gen_operand", "gen_problem",
            "batched_problem_shapes", "digit_matrix"]
 
-#: number of components and component dtype for each precision
+#: number of components and component dtype for each precision; "q<N>" is
+#: N binary64 components (q2/q3/q4 draw exactly as dd/td/qd)
 PRECISIONS = {
     "dd": (2, np.float64),
     "td": (3, np.float64),
     "qd": (4, np.float64),
     "ts": (3, np.float32),
 }
+PRECISIONS.update({f"q{q}": (q, np.float64) for q in range(2, 17)})
 
 
 def components_of(prec: str):

@@ -24,7 +24,7 @@ __all__ = [
     "Status", "Prec", "Form", "OzmpError", "PlanInfo", "Plan", "load", "colmajor",
     "ozmp_plan_create", "ozmp_plan_destroy", "ozmp_plan_get_info", "ozmp_plan_set_workspace",
     "ozmp_plan_set_stream", "ozmp_plan_execute", "ozmp_plan_get_status", "ozmp_plan_split",
-    "ozmp_plan_diagonal", "ozmp_plan_multiply", "ozmp_plan_set_timing", "ozmp_plan_read_timing", "ozmp_gemm_dd", "ozmp_gemm_td", "ozmp_gemm_qd", "ozmp_gemm_ts", "ozmp_gemm_dd_noalloc", "ozmp_gemm_batched", "Problem", "ozmp_gemm_naive",
+    "ozmp_plan_diagonal", "ozmp_plan_multiply", "ozmp_plan_set_timing", "ozmp_plan_read_timing", "ozmp_gemm_dd", "ozmp_gemm_td", "ozmp_gemm_qd", "ozmp_gemm_ts", "ozmp_gemm_md", "prec_code", "MAX_COMPONENTS", "ozmp_gemm_dd_noalloc", "ozmp_gemm_batched", "Problem", "ozmp_gemm_naive",
     "ozmp_set_stream", "ozmp_set_form", "ozmp_last_status", "ozmp_version", "gemm", "EXP_ZERO",
 ]
 
@@ -57,10 +57,24 @@ class Form(IntEnum):
     FP8_MMA = 4
 
 
+MAX_COMPONENTS = 16
+# "dd"/"td"/"qd"/"ts" and "q2" .. "q16" (q binary64 components)
 PREC_BY_NAME = {"dd": Prec.DD, "td": Prec.TD, "qd": Prec.QD, "ts": Prec.TS}
+PREC_BY_NAME.update({f"q{q}": q for q in range(2, MAX_COMPONENTS + 1)})
 FORM_BY_NAME = {"auto": Form.AUTO, "fp64": Form.FP64, "int8": Form.INT8, "fp8": Form.FP8,
                 "fp8mma": Form.FP8_MMA}
 NCOMP = {Prec.DD: 2, Prec.TD: 3, Prec.QD: 4, Prec.TS: 3}
+NCOMP.update({q: q for q in range(5, MAX_COMPONENTS + 1)})
+
+
+def prec_code(prec) -> int:
+    """The C ABI precision code of a name ("dd", "q8", ...) or code."""
+    if isinstance(prec, str):
+        return int(PREC_BY_NAME[prec])
+    p = int(prec)
+    if p not in NCOMP:
+        raise ValueError(f"unknown precision {prec!r}")
+    return p
 
 
 class OzmpError(RuntimeError):
@@ -118,6 +132,7 @@ SIGNATURES = {
     "ozmp_gemm_td": [_I64, _I64, _I64, _PP, _I64, _PP, _I64, _PP, _I64, ctypes.c_int],
     "ozmp_gemm_qd": [_I64, _I64, _I64, _PP, _I64, _PP, _I64, _PP, _I64, ctypes.c_int],
     "ozmp_gemm_ts": [_I64, _I64, _I64, _PP, _I64, _PP, _I64, _PP, _I64, ctypes.c_int],
+    "ozmp_gemm_md": [ctypes.c_int, _I64, _I64, _I64, _PP, _I64, _PP, _I64, _PP, _I64, ctypes.c_int],
     "ozmp_gemm_dd_noalloc": [_I64, _I64, _I64, _PP, _I64, _PP, _I64, _PP, _I64, ctypes.c_int, _VP],
     "ozmp_set_stream": [_VP],
     "ozmp_set_form": [ctypes.c_int],
@@ -285,6 +300,17 @@ def ozmp_gemm_ts(A, B, C, nslices=0):
     _plain("ozmp_gemm_ts", A, B, C, nslices)
 
 
+def ozmp_gemm_md(A, B, C, nslices=0):
+    """q binary64 components (q = len(A), 2 <= q <= 16)."""
+    m, k = A[0].shape
+    n = B[0].shape[1]
+    pa, ka = _ptrs(A)
+    pb, kb = _ptrs(B)
+    pc, kc = _ptrs(C)
+    st = load().ozmp_gemm_md(len(A), m, n, k, pa, _ld(A[0]), pb, _ld(B[0]), pc, _ld(C[0]), nslices)
+    _check(st, "ozmp_gemm_md")
+
+
 def ozmp_gemm_dd_noalloc(A, B, C, nslices=0, stream=None):
     """Double-double product that allocates nothing (a fixed 64 MiB scratch
     inside the library); for callers that cannot call cudaMalloc."""
@@ -324,7 +350,7 @@ def ozmp_gemm_batched(problems, form=Form.AUTO, stream=None, plan=None):
 
 def ozmp_gemm_naive(prec, A, B, C, stream=None):
     """The triple-loop multi-component product (the paper's baseline)."""
-    prec = PREC_BY_NAME[prec] if isinstance(prec, str) else Prec(prec)
+    prec = prec_code(prec)
     m, k = A[0].shape
     n = B[0].shape[1]
     pa, ka = _ptrs(A)
@@ -358,7 +384,7 @@ class Plan:
 
     def __init__(self, prec, m, n, k, form=Form.AUTO, nslices=0, stream=None, workspace=True):
         import torch
-        self.prec = PREC_BY_NAME[prec] if isinstance(prec, str) else Prec(prec)
+        self.prec = prec_code(prec)
         self.form_req = FORM_BY_NAME[form] if isinstance(form, str) else Form(form)
         self.h = ozmp_plan_create(self.prec, m, n, k, self.form_req, nslices, stream)
         self.info = ozmp_plan_get_info(self.h)

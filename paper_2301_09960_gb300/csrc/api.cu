@@ -114,7 +114,7 @@ ozmp_status ozmp_plan_execute(ozmp_plan p, const void* const* A, int64_t lda, co
     if (launch_split(a, p->stream) != cudaSuccess) return OZMP_ERR_CUDA;
     if (plan_upload_schedule(p) != OZMP_OK) return OZMP_ERR_CUDA;
     GemmArgs g = gemm_args(p);
-    for (int c = 0; c < 4; ++c) g.C[c] = (c < p->q) ? C[c] : nullptr;
+    for (int c = 0; c < OZMP_MAX_COMPONENTS; ++c) g.C[c] = (c < p->q) ? C[c] : nullptr;
     g.ldc = ldc;
     take_timing(p, g);
     return launch_gemm(g, p->stream) == cudaSuccess ? OZMP_OK : OZMP_ERR_CUDA;
@@ -129,7 +129,7 @@ ozmp_status ozmp_plan_multiply(ozmp_plan p, void* const* C, int64_t ldc) {
     if (p->k == 0) return zero_c(p, C, ldc);
     if (plan_upload_schedule(p) != OZMP_OK) return OZMP_ERR_CUDA;
     GemmArgs g = gemm_args(p);
-    for (int c = 0; c < 4; ++c) g.C[c] = (c < p->q) ? C[c] : nullptr;
+    for (int c = 0; c < OZMP_MAX_COMPONENTS; ++c) g.C[c] = (c < p->q) ? C[c] : nullptr;
     g.ldc = ldc;
     take_timing(p, g);
     return launch_gemm(g, p->stream) == cudaSuccess ? OZMP_OK : OZMP_ERR_CUDA;
@@ -247,6 +247,12 @@ ozmp_status ozmp_gemm_qd(int64_t m, int64_t n, int64_t k, const double* const A[
 ozmp_status ozmp_gemm_ts(int64_t m, int64_t n, int64_t k, const float* const A[3], int64_t lda,
                          const float* const B[3], int64_t ldb, float* const C[3], int64_t ldc, int nslices) {
     return plain_gemm(OZMP_TS, m, n, k, (const void* const*)A, lda, (const void* const*)B, ldb, (void* const*)C, ldc, nslices);
+}
+ozmp_status ozmp_gemm_md(int q, int64_t m, int64_t n, int64_t k, const double* const* A, int64_t lda,
+                         const double* const* B, int64_t ldb, double* const* C, int64_t ldc, int nslices) {
+    if (q < 2 || q > OZMP_MAX_COMPONENTS) return OZMP_ERR_INVALID_ARG;
+    return plain_gemm(OZMP_PREC_Q(q), m, n, k, (const void* const*)A, lda, (const void* const*)B, ldb,
+                      (void* const*)C, ldc, nslices);
 }
 
 }  // extern "C"

@@ -361,29 +361,6 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
     if (CG == 2) cluster_sync();
 }
 
-// Rounding pass of the single-problem path: one thread per element of C
-// normalises the element's carry-save limbs 0 .. nl-1 (from its tile's split
-// slot when the tile was split into chunks, else from acc) and rounds them
-// canonically into the q components.  Bound by the limb reads.
-template <int NW>
-__global__ void __launch_bounds__(256) k_tc_finish(const GemmArgs g, int nl, const int* tile_slot, int tile_rows,
-                                                   int slot_limbs) {
-    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    if (i >= g.m) return;
-    const size_t sstride = (size_t)BN * BM;
-    for (int64_t j = blockIdx.y; j < g.n; j += gridDim.y) {
-        const int slot =
-            tile_slot ? tile_slot[(i / tile_rows) + (j / BN) * (g.mp / tile_rows)] : -1;
-        if (slot < 0) {
-            finish_element<NW>(g, nl, g.acc, (size_t)g.mp * g.np, (size_t)j * g.mp + i, i, j, 0, 0, false);
-        } else {
-            const int cta = slot * (tile_rows / BM) + (int)((i % tile_rows) / BM);
-            finish_element<NW>(g, nl, g.sacc + (size_t)cta * slot_limbs * sstride, sstride,
-                               (size_t)(j % BN) * BM + (size_t)(i % BM), i, j, 0, 0, false);
-        }
-    }
-}
-
 }  // namespace tc
 
 cudaError_t tc_set_smem() {
@@ -550,7 +527,7 @@ cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t st) {
     tc::Prob p;
     memset(&p, 0, sizeof(p));
     p.E = g.E; p.F = g.F; p.acc = g.acc;
-    for (int c = 0; c < 4; ++c) p.C[c] = g.C[c];
+    for (int c = 0; c < OZMP_MAX_COMPONENTS; ++c) p.C[c] = g.C[c];
     p.T = g.T;
     p.m = g.m; p.n = g.n; p.mp = g.mp; p.np = g.np; p.kp = g.kp; p.ldc = g.ldc;
     p.q = g.q; p.is_f32 = g.is_f32; p.s = g.s; p.beta = g.beta; p.ppd = g.ppd; p.acc_words = g.acc_words;
@@ -580,17 +557,12 @@ cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t st) {
     // the rounding pass: limbs 0 .. (beta (s - 1)) / 16 hold data (the last drain's shift)
     const int nl = g.d_only ? 1 : (g.beta * (g.s - 1)) / 16 + 1;
     const int slot_limbs = 4 * g.acc_words + 1;
-    const dim3 fg((unsigned)((g.m + 255) / 256), (unsigned)(g.n < 65535 ? g.n : 65535));
     const int* ts = sc.items ? g.tile_slot : nullptr;
     const int rows = tc::BM * cg;
-    switch (g.acc_words) {
-        case 2: tc::k_tc_finish<2><<<fg, 256, 0, st>>>(g, nl, ts, rows, slot_limbs); break;
-        case 3: tc::k_tc_finish<3><<<fg, 256, 0, st>>>(g, nl, ts, rows, slot_limbs); break;
-        case 4: tc::k_tc_finish<4><<<fg, 256, 0, st>>>(g, nl, ts, rows, slot_limbs); break;
-        case 5: tc::k_tc_finish<5><<<fg, 256, 0, st>>>(g, nl, ts, rows, slot_limbs); break;
-        case 6: tc::k_tc_finish<6><<<fg, 256, 0, st>>>(g, nl, ts, rows, slot_limbs); break;
-        default: tc::k_tc_finish<7><<<fg, 256, 0, st>>>(g, nl, ts, rows, slot_limbs); break;
-    }
+    if (g.acc_words < 2 || g.acc_words > 16) return cudaErrorInvalidValue;
+    e = g.acc_words <= 8 ? launch_tc_finish_lo(g, nl, ts, rows, slot_limbs, st)
+                         : launch_tc_finish_hi(g, nl, ts, rows, slot_limbs, st);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -225,28 +225,25 @@ struct Walk {
     }
 };
 
-// Limb accumulator of one element: NL int64 limbs, limb l weighs 2^(16 l),
-// limb l of the element at base[l * lstride + idx].  `zero` skips the load
-// (first and last drain of a tile coincide).  Writes C(i, j) (or T in the
+// Limb accumulator of one element: limbs 0 .. nl-1 of int64, limb l weighs
+// 2^(16 l), limb l of the element at base[l * lstride + idx].  `x` is added
+// to limb `li` (the last drain's contribution when it is fused here);
+// `zero` skips the loads (first and last drain of a tile coincide).  The
+// limbs are streamed through one carry chain into a two's complement value
+// of 64 NW bits, rounded canonically into C(i, j) (or written to T in the
 // diagnostic mode).
 template <int NW>
 __device__ __forceinline__ void finish_element(const GemmArgs& g, int nl, const int64_t* base, size_t lstride,
                                                size_t idx, int64_t i, int64_t j, int64_t x, int li, bool zero) {
-    constexpr int NLMAX = 4 * NW + 1;
-    int64_t L[NLMAX];
-#pragma unroll
-    for (int l = 0; l < NLMAX; ++l) L[l] = (!zero && l < nl) ? __ldcg(base + l * lstride + idx) : 0;
-#pragma unroll
-    for (int l = 0; l < NLMAX; ++l)
-        if (l == li) L[l] += x;
-    // carry-save limbs -> two's complement words (the value fits 64 NW bits)
     uint64_t w[NW];
 #pragma unroll
     for (int x2 = 0; x2 < NW; ++x2) w[x2] = 0;
     int64_t carry = 0;
 #pragma unroll
     for (int l = 0; l < 4 * NW; ++l) {
-        int64_t t = L[l] + carry;                 // |L| < 2^48, |carry| < 2^48
+        int64_t t = (!zero && l < nl) ? __ldcg(base + l * lstride + idx) : 0;   // |limb| < 2^48
+        if (l == li) t += x;
+        t += carry;                                // |carry| < 2^48
         w[l >> 2] |= ((uint64_t)t & 0xffffull) << (16 * (l & 3));
         carry = t >> 16;                           // arithmetic shift: floor division
     }
@@ -255,18 +252,17 @@ __device__ __forceinline__ void finish_element(const GemmArgs& g, int nl, const 
         g.T[i + j * g.m] = (int64_t)w[0];
         return;
     }
-    int Ei = g.E[i], Fj = g.F[j];
+    const int Ei = g.E[i], Fj = g.F[j];
+    const bool nz = (Ei != OZMP_EXP_ZERO && Fj != OZMP_EXP_ZERO);
+    const int U = nz ? Ei + Fj - g.beta * (g.s + 1) : 0;
+    const size_t at = (size_t)(i + j * g.ldc);
     bool ok = true;
     if (g.is_f32) {
-        float out[4] = {0.f, 0.f, 0.f, 0.f};
-        if (Ei != OZMP_EXP_ZERO && Fj != OZMP_EXP_ZERO)
-            ok = canonical_round<NW, float>(w, Ei + Fj - g.beta * (g.s + 1), g.q, out);
-        for (int c = 0; c < g.q; ++c) ((float*)g.C[c])[i + j * g.ldc] = out[c];
+        if (nz) ok = canonical_round_put<NW, float>(w, U, g.q, [&](int c, float v) { ((float*)g.C[c])[at] = v; });
+        else for (int c = 0; c < g.q; ++c) ((float*)g.C[c])[at] = 0.f;
     } else {
-        double out[4] = {0.0, 0.0, 0.0, 0.0};
-        if (Ei != OZMP_EXP_ZERO && Fj != OZMP_EXP_ZERO)
-            ok = canonical_round<NW, double>(w, Ei + Fj - g.beta * (g.s + 1), g.q, out);
-        for (int c = 0; c < g.q; ++c) ((double*)g.C[c])[i + j * g.ldc] = out[c];
+        if (nz) ok = canonical_round_put<NW, double>(w, U, g.q, [&](int c, double v) { ((double*)g.C[c])[at] = v; });
+        else for (int c = 0; c < g.q; ++c) ((double*)g.C[c])[at] = 0.0;
     }
     if (!ok) atomicOr(g.status, ST_RANGE);
 }
@@ -290,7 +286,7 @@ struct Prob {
     const int32_t* E;
     const int32_t* F;
     int64_t* acc;          // [nlimbs][np][mp] carry-save limbs
-    void* C[4];
+    void* C[OZMP_MAX_COMPONENTS];
     int64_t* T;            // diagnostic output (d_only)
     int64_t* sacc;         // split tiles: [slot][nlimbs][bn][BM] limbs, zeroed before the launch
     int* cnt;              // split tiles: chunks finished per slot, zeroed before the launch
@@ -309,7 +305,7 @@ __device__ __forceinline__ GemmArgs as_gemm_args(const Prob& p, uint32_t* status
     g.E = p.E; g.F = p.F; g.Adig = nullptr; g.Bdig = nullptr;
     g.s = p.s; g.beta = p.beta; g.ppd = p.ppd; g.group_start = 0; g.acc_words = p.acc_words; g.ngroups = 0;
     g.acc = p.acc;
-    for (int c = 0; c < 4; ++c) g.C[c] = p.C[c];
+    for (int c = 0; c < OZMP_MAX_COMPONENTS; ++c) g.C[c] = p.C[c];
     g.ldc = p.ldc;
     g.status = status;
     g.d_only = p.d_only;
@@ -408,6 +404,9 @@ int tc_num_sms();
 cudaError_t tc_launch(const tc::Sched& sc, const tc::Prob& single, const CUtensorMap& ma, const CUtensorMap& mb,
                       uint32_t* status, int grid, cudaStream_t st);
 cudaError_t tc_set_smem();
+// the rounding pass over the limbs (tc_finish_lo.cu / tc_finish_hi.cu)
+cudaError_t launch_tc_finish_lo(const GemmArgs& g, int nl, const int* ts, int rows, int slot_limbs, cudaStream_t st);
+cudaError_t launch_tc_finish_hi(const GemmArgs& g, int nl, const int* ts, int rows, int slot_limbs, cudaStream_t st);
 // the CTA-pair form: `clusters` clusters of two CTAs over the schedule
 cudaError_t tc_launch_pair(const tc::Sched& sc, const tc::Prob& single, const CUtensorMap& ma,
                            const CUtensorMap& mb, uint32_t* status, int clusters, cudaStream_t st);

@@ -21,6 +21,7 @@ struct SplitArgs {
     void* Adig;
     void* Bdig;
     int s, beta;
+    int big;               // the many-component / wide-window splitter (split_big.cu)
 };
 
 struct GemmArgs {
@@ -38,7 +39,7 @@ struct GemmArgs {
     int acc_words;         // 64-bit words of the per-element exact accumulator
     int ngroups;
     int64_t* acc;          // [acc_words][mp][np], used when ngroups > 1
-    void* C[4];
+    void* C[OZMP_MAX_COMPONENTS];
     int64_t ldc;
     uint32_t* status;
     int d_only;            // diagnostic: only diagonal d_only, raw int64 T_d written to T

@@ -80,7 +80,7 @@ extern "C" ozmp_status ozmp_gemm_dd_noalloc(int64_t m, int64_t n, int64_t k, con
     SplitArgs sa = split_args(&p, (const void* const*)A, lda, (const void* const*)B, ldb);
     if (launch_split(sa, p.stream) != cudaSuccess) return OZMP_ERR_CUDA;
     GemmArgs g = gemm_args(&p);
-    for (int c = 0; c < 4; ++c) g.C[c] = (c < 2) ? (void*)C[c] : nullptr;
+    for (int c = 0; c < OZMP_MAX_COMPONENTS; ++c) g.C[c] = (c < 2) ? (void*)C[c] : nullptr;
     g.ldc = ldc;
     return launch_gemm(g, p.stream) == cudaSuccess ? OZMP_OK : OZMP_ERR_CUDA;
 }

@@ -517,10 +517,11 @@ __device__ __forceinline__ uint32_t e4m3_of_int(int d) {
 // ----------------------------------------------------------------------------
 // canonical rounding of an exact two's complement accumulator into q words
 // ----------------------------------------------------------------------------
-// value = acc * 2^U.  Writes c_0 = RN(value), c_t = RN(value - c_0 - ...).
+// value = acc * 2^U.  Emits c_0 = RN(value), c_t = RN(value - c_0 - ...)
+// through put(t, c_t) for t = 0 .. q-1.
 // Returns false if a non-zero component would leave the normal range.
-template <int NW, typename T>
-__device__ __forceinline__ bool canonical_round(uint64_t (&acc)[NW], int U, int q, T* out) {
+template <int NW, typename T, typename Put>
+__device__ __forceinline__ bool canonical_round_put(uint64_t (&acc)[NW], int U, int q, Put&& put) {
     constexpr int P = (sizeof(T) == 8) ? 53 : 24;
     constexpr int EBIAS = (sizeof(T) == 8) ? 1023 : 127;
     constexpr int EMAX = (sizeof(T) == 8) ? 2046 : 254;
@@ -531,7 +532,7 @@ __device__ __forceinline__ bool canonical_round(uint64_t (&acc)[NW], int U, int 
 #pragma unroll 4
     for (int c = 0; c < q; ++c) {
         int top = mw_top<NW>(acc);
-        if (top < 0) { out[c] = (T)0; continue; }
+        if (top < 0) { put(c, (T)0); continue; }
         int z = 64 * NW - 1 - top;
         mw_shl<NW>(acc, z);
         scale -= z;
@@ -561,19 +562,26 @@ __device__ __forceinline__ bool canonical_round(uint64_t (&acc)[NW], int U, int 
         int be = ex + (P - 1) + EBIAS;             // biased exponent of 1.f x 2^(ex + P - 1)
         if (be < 1 || be > EMAX) {
             ok = false;
-            out[c] = (T)0;
+            put(c, (T)0);
         } else if (sizeof(T) == 8) {
             uint64_t bits = ((uint64_t)(sgn < 0) << 63) | ((uint64_t)be << 52) | (mant & ((1ull << 52) - 1ull));
             double dv = __longlong_as_double((long long)bits);
-            out[c] = (T)dv;
+            put(c, (T)dv);
         } else {
             uint32_t bits = ((uint32_t)(sgn < 0) << 31) | ((uint32_t)be << 23) | ((uint32_t)mant & 0x7fffffu);
             float fv = __uint_as_float(bits);
-            out[c] = (T)fv;
+            put(c, (T)fv);
         }
         if (up) sgn = -sgn;
     }
     return ok;
+}
+
+
+// the same into out[0 .. q-1]
+template <int NW, typename T>
+__device__ __forceinline__ bool canonical_round(uint64_t (&acc)[NW], int U, int q, T* out) {
+    return canonical_round_put<NW, T>(acc, U, q, [&](int c, T v) { out[c] = v; });
 }
 
 }  // namespace ozmp

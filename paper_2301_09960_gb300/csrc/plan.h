@@ -28,6 +28,7 @@ struct ozmp_plan_s {
     int sched_items, sched_slots, sched_grid;   // sched_slots: split-limb slots of single CTAs
     int tc_cg;                                   // 2: the schedule is over CTA-pair tiles
     int tc_dyn;                                  // items taken from a counter (else per-CTA lists)
+    int big;                                     // the many-component splitter (q > 4 or wide windows)
     // kernel timing ring (ozmp_plan_set_timing): tev[2 x] / tev[2 x + 1] around call x mod tev_n
     cudaEvent_t* tev;
     int tev_n;
@@ -47,24 +48,18 @@ using namespace ozmp;
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 inline int64_t roundup(int64_t x, int64_t r) { return (x + r - 1) / r * r; }
 
+// components of a precision: q for q binary64 words (2 <= q <= 16), 3 for TS
 inline int prec_q(int prec) {
-    switch (prec) {
-        case OZMP_DD: return 2;
-        case OZMP_TD: return 3;
-        case OZMP_QD: return 4;
-        case OZMP_TS: return 3;
-        default: return 0;
-    }
+    if (prec == OZMP_TS) return 3;
+    if (prec >= 2 && prec <= OZMP_MAX_COMPONENTS) return prec;
+    return 0;
 }
 
-// target error bits of each precision (2^-100 DD, 2^-150 TD, 2^-200 QD, 2^-66 TS)
+// target error bits of each precision: 50 q for q binary64 words (2^-100 DD,
+// 2^-150 TD, 2^-200 QD, ...), 66 for TS
 inline int prec_target_bits(int prec) {
-    switch (prec) {
-        case OZMP_DD: return 100;
-        case OZMP_TD: return 150;
-        case OZMP_QD: return 200;
-        default: return 66;
-    }
+    if (prec == OZMP_TS) return 66;
+    return 50 * prec_q(prec);
 }
 
 inline int ceil_log2(int64_t x) {
@@ -112,7 +107,9 @@ inline ozmp_status fill_schedule(ozmp_plan_s* p) {
     p->ngroups = 0;
     int dfirst = -1;
     unsigned __int128 hb = 0;
-    for (int d = p->s + 1; d >= 2; --d) {
+    // (the groups serve the mma.sync forms, whose bit mask holds s <= 64 diagonals;
+    // the tcgen05 form keeps carry-save limbs and needs none)
+    for (int d = p->s + 1; d >= 2 && p->s <= 64; --d) {
         unsigned __int128 tb = (unsigned __int128)(d - 1) * tpair;
         bool open = (dfirst < 0);
         if (!open) {
@@ -140,7 +137,7 @@ inline ozmp_status fill_schedule(ozmp_plan_s* p) {
     int bits = maxbits + ceil_log2(p->s + 1) + 2;   // sum of s terms, sign bit
     p->acc_words = (bits + 63) / 64;
     if (p->acc_words < 2) p->acc_words = 2;
-    if (p->acc_words > 7) return OZMP_ERR_UNSUPPORTED;
+    if (p->acc_words > (p->form == OZMP_FORM_FP8 ? 16 : 7)) return OZMP_ERR_UNSUPPORTED;
     p->nlimbs = 4 * p->acc_words + 1;
     return OZMP_OK;
 }
@@ -200,6 +197,7 @@ inline SplitArgs split_args(ozmp_plan_s* p, const void* const* A, int64_t lda, c
     a.Bdig = w + p->off_Bdig;
     a.s = p->s;
     a.beta = p->beta;
+    a.big = p->big;
     return a;
 }
 
@@ -326,15 +324,22 @@ inline ozmp_status plan_init(ozmp_plan_s* p, int prec, int64_t m, int64_t n, int
     p->m = m; p->n = n; p->k = k;
     p->beta = (p->form == OZMP_FORM_FP64) ? beta_fp64(k) : (p->form == OZMP_FORM_INT8 ? 7 : 4);
     p->db = (p->form == OZMP_FORM_FP64) ? 8 : 1;
-    int maxs = (p->form == OZMP_FORM_INT8) ? 36 : 64;
+    // slice limits: the register-resident splitter holds beta s <= 376 (7-word
+    // windows) and 4 components; the tcgen05 form goes on with the
+    // many-component splitter up to beta s + 65 <= 1024 (16-word windows)
+    const bool tc = (p->form == OZMP_FORM_FP8);
+    if (q > 4 && !tc) return OZMP_ERR_UNSUPPORTED;
+    const int maxs = tc ? (1024 - 65) / 4 : (p->form == OZMP_FORM_INT8 ? 36 : 64);
+    const int maxbits = tc ? 1024 - 65 : 376;
     if (nslices == 0) {
         int bits = prec_target_bits(prec) + ceil_log2(k > 0 ? k : 1) + 16;
         nslices = (bits + p->beta - 1) / p->beta;
         if (nslices > maxs) nslices = maxs;
-        while (nslices > 1 && nslices * p->beta > 376) --nslices;
+        while (nslices > 1 && nslices * p->beta > maxbits) --nslices;
     }
-    if (nslices > maxs || nslices * p->beta > 376) return OZMP_ERR_UNSUPPORTED;
+    if (nslices > maxs || nslices * p->beta > maxbits) return OZMP_ERR_UNSUPPORTED;
     p->s = nslices;
+    p->big = (q > 4 || nslices * p->beta > 376) ? 1 : 0;
     p->mp = roundup(m, 128);
     p->np = roundup(n, p->form == OZMP_FORM_FP8 ? 256 : 128);
     p->kp = roundup(k, 128);

@@ -6,14 +6,20 @@ namespace ozmp {
 cudaError_t launch_digits_fp8(const SplitArgs& g, cudaStream_t st);
 cudaError_t launch_digits_int8(const SplitArgs& g, cudaStream_t st);
 cudaError_t launch_digits_fp64(const SplitArgs& g, cudaStream_t st);
+cudaError_t launch_exponents_big(const SplitArgs& g, cudaStream_t st);
+cudaError_t launch_digits_big(const SplitArgs& g, cudaStream_t st);
+
+static void init_exponents(const SplitArgs& g, cudaStream_t st) {
+    int64_t mx = g.mp > g.np ? g.mp : g.np;
+    if (mx == 0) mx = 1;
+    k_init_exponents<<<(unsigned)((mx + 255) / 256), 256, 0, st>>>(g.E, g.mp, g.F, g.np, g.status);
+}
 
 template <typename T>
 static cudaError_t exponents_impl(const SplitArgs& g, cudaStream_t st) {
     Operand<T> a = make_op<T>(g.A, g.q, g.lda);
     Operand<T> b = make_op<T>(g.B, g.q, g.ldb);
-    int64_t mx = g.mp > g.np ? g.mp : g.np;
-    if (mx == 0) mx = 1;
-    k_init_exponents<<<(unsigned)((mx + 255) / 256), 256, 0, st>>>(g.E, g.mp, g.F, g.np, g.status);
+    init_exponents(g, st);
     if (g.m > 0 && g.k > 0) {
         int kchunk = 64;
         dim3 gr((unsigned)((g.m + 255) / 256), (unsigned)((g.k + kchunk - 1) / kchunk));
@@ -26,6 +32,13 @@ static cudaError_t exponents_impl(const SplitArgs& g, cudaStream_t st) {
 }
 
 cudaError_t launch_split(const SplitArgs& g, cudaStream_t st) {
+    if (g.big) {
+        // more than 4 components or a window wider than 448 bits (split_big.cu)
+        init_exponents(g, st);
+        cudaError_t e = launch_exponents_big(g, st);
+        if (e != cudaSuccess) return e;
+        return launch_digits_big(g, st);
+    }
     cudaError_t e = g.is_f32 ? exponents_impl<float>(g, st) : exponents_impl<double>(g, st);
     if (e != cudaSuccess) return e;
     if (g.form == OZMP_FORM_FP64) return launch_digits_fp64(g, st);

@@ -61,16 +61,41 @@ def test_plan_digit_width_and_schedule(form, beta, k):
 
 
 def test_plan_rejects_bad_arguments():
-    for args in [(7, 10, 10, 10, 0, 0), (2, -1, 10, 10, 0, 0), (2, 10, 10, 10, 9, 0), (2, 10, 10, 10, 0, 65)]:
+    for args in [(1, 10, 10, 10, 0, 0), (17, 10, 10, 10, 0, 0), (102, 10, 10, 10, 0, 0), (2, -1, 10, 10, 0, 0),
+                 (2, 10, 10, 10, 9, 0), (2, 10, 10, 10, 0, 257)]:
         with pytest.raises(oz.OzmpError) as e:
             oz.ozmp_plan_create(*args, None)
         assert e.value.status == oz.Status.ERR_INVALID_ARG
+    # valid arguments beyond a form's limits
+    for args in [(2, 10, 10, 10, oz.Form.FP8, 240), (2, 10, 10, 10, oz.Form.FP8_MMA, 65),
+                 (2, 10, 10, 10, oz.Form.INT8, 37), (5, 10, 10, 10, oz.Form.INT8, 0), (5, 10, 10, 10, oz.Form.FP64, 0)]:
+        with pytest.raises(oz.OzmpError) as e:
+            oz.ozmp_plan_create(*args, None)
+        assert e.value.status == oz.Status.ERR_UNSUPPORTED
     # binary32 accumulation of e4m3 digits is exact only up to k = 2^24 / 225
     with pytest.raises(oz.OzmpError) as e:
         oz.ozmp_plan_create(oz.Prec.DD, 8, 8, 80000, oz.Form.FP8, 0, None)
     assert e.value.status == oz.Status.ERR_UNSUPPORTED
     h = oz.ozmp_plan_create(oz.Prec.DD, 8, 8, 74565, oz.Form.FP8, 0, None)
     oz.ozmp_plan_destroy(h)
+
+
+@pytest.mark.parametrize("q", [2, 3, 4, 5, 8, 12, 16])
+def test_component_count_plans(q):
+    # q binary64 components: target 2^(-50 q) -> s = ceil((50 q + log2 k + 16) / 4) e4m3 digits,
+    # the accumulator holds every diagonal's weight, and more than 4 components
+    # take the tcgen05 form only
+    k = 1000
+    h = oz.ozmp_plan_create(q, 300, 200, k, oz.Form.AUTO, 0, None)
+    try:
+        i = oz.ozmp_plan_get_info(h)
+        assert i.form == oz.Form.FP8 and i.beta == 4
+        assert i.nslices == -(-(50 * q + 10 + 16) // 4)
+        assert i.nslices * 4 + 65 <= 1024
+        top_bits = 4 * (i.nslices - 1) + 20 + 8 + 2      # weight of diagonal 2, the sum of s + 1 terms, sign
+        assert 64 * i.acc_words >= top_bits
+    finally:
+        oz.ozmp_plan_destroy(h)
 
 
 def test_timing_ring_argument_checks():
