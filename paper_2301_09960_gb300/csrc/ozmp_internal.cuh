@@ -382,9 +382,64 @@ __device__ __forceinline__ int aligned_magnitude(const Comp (&c)[4], const T (&v
 // them, x = V 2^L + T, |T| < q 2^L, and the top bit of |x| is that of |V|
 // unless |V| is within q of a power of two (or |V| < 2^64); those rare cases
 // take the exact full-range path.
+// Fast exponent from the encodings alone.  Let the top component have the
+// largest exponent field, |top| in [2^(e-1), 2^e).  If every other component
+// is below 2^(e - P - g) (P = 53 or 24 significand bits, 2^g >= q - 1), the
+// others sum to less than an ulp of top, so |x| stays in (2^(e-1), 2^e) and
+// E(x) = e -- unless top is a power of two, when x drops below 2^(e-1) iff
+// the others sum to the opposite sign (decided here only for q = 2).
+// Returns false when these conditions do not settle E(x) (then the exact
+// window decides); zero, subnormal and non-finite tops also return false.
+template <typename T>
+__device__ __forceinline__ bool exponent_fast(const T (&v)[4], int q, int& E) {
+    constexpr int P = (sizeof(T) == 8) ? 53 : 24;
+    constexpr int EB = (sizeof(T) == 8) ? 1022 : 126;     // frexp exponent = field - EB
+    constexpr int EMAXF = (sizeof(T) == 8) ? 0x7ff : 0xff;
+    uint64_t bits[4];
+    int ef[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (sizeof(T) == 8) {
+            bits[i] = (uint64_t)__double_as_longlong((double)v[i]);
+            ef[i] = (int)((bits[i] >> 52) & 0x7ff);
+        } else {
+            bits[i] = __float_as_uint((float)v[i]);
+            ef[i] = (int)((bits[i] >> 23) & 0xff);
+        }
+        if (i >= q) ef[i] = 0;
+    }
+    int top = 0;
+#pragma unroll
+    for (int i = 1; i < 4; ++i) top = ef[i] > ef[top] ? i : top;
+    const int et = ef[top];
+    if (et == 0 || et == EMAXF) return false;
+    int eo = 0;   // largest exponent field among the others (0: zero or subnormal)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (i == top) continue;
+        if (ef[i] == EMAXF) return false;
+        const bool nonzero = (sizeof(T) == 8) ? ((bits[i] << 1) != 0) : ((bits[i] << 33) != 0);
+        if (nonzero) eo = (ef[i] > eo) ? ef[i] : (eo ? eo : 1);   // a subnormal counts as field 1
+    }
+    const int g = q <= 2 ? 0 : (q <= 3 ? 1 : 2);
+    if (eo && eo > et - P - g) return false;
+    const uint64_t mant = (sizeof(T) == 8) ? (bits[top] & 0xFFFFFFFFFFFFFull) : (bits[top] & 0x7FFFFFull);
+    E = et - EB;
+    if (mant == 0 && eo) {
+        if (q != 2) return false;
+        const bool opposite = (sizeof(T) == 8) ? (((bits[0] ^ bits[1]) >> 63) != 0) : (((bits[0] ^ bits[1]) >> 31) != 0);
+        if (opposite) E -= 1;
+    }
+    return true;
+}
+
 template <typename T>
 __device__ __forceinline__ int exponent_of(const Comp (&c)[4], const T (&v)[4], int q, int Ptop) {
     if (Ptop == -100000) return OZMP_EXP_ZERO;
+    {
+        int Ef;
+        if (exponent_fast<T>(v, q, Ef)) return Ef;
+    }
     const int L = Ptop - 125;
     unsigned __int128 V = 0;
     bool tail = false;
@@ -478,6 +533,38 @@ __device__ __forceinline__ uint32_t e4m3x4(uint32_t m4, uint32_t negmask) {
     const uint32_t big = ((m4 >> 3) & 0x01010101u) * 0xFFu;
     const uint32_t code = (a & ~big) | (b & big);
     return code | (negmask & __vcmpne4(code, 0u));
+}
+
+// prmt in its default mode: each selector nibble picks one of the 8 bytes of
+// {b, a} with its low 3 bits and, when its bit 3 is set, replicates that
+// byte's sign bit instead of copying it
+__device__ __forceinline__ uint32_t prmt_sign(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(sel));
+    return r;
+}
+
+// e4m3 codes of the four digit magnitudes held in the low 16 bits of x (one
+// nibble each, nibble i -> byte i), with the sign bit set on the non-zero
+// codes when negm = 0x80808080.  Two table lookups: codes of 0..7 where the
+// nibble is below 8 (the bytes selected for 8..15 replicate a clear sign bit
+// and give 0) and codes of 8..15 on the nibbles with bit 3 flipped.
+__device__ __forceinline__ uint32_t e4m3_nibbles4(uint32_t x, uint32_t negm) {
+    const uint32_t a = prmt_sign(0x44403800u, 0x4E4C4A48u, x);
+    const uint32_t b = prmt_sign(0x53525150u, 0x57565554u, x ^ 0x8888u);
+    const uint32_t code = a | b;
+    // 0x80 in every non-zero byte: (code & 0x78) is 0 or at least 0x38
+    return code | (((code & 0x78787878u) + 0x78787878u) & negm);
+}
+
+// 4 x 4 byte transpose: out[b] byte e = in[e] byte b
+__device__ __forceinline__ void transpose4(const uint32_t (&in)[4], uint32_t (&out)[4]) {
+    const uint32_t a = __byte_perm(in[0], in[1], 0x5140), b = __byte_perm(in[0], in[1], 0x7362);
+    const uint32_t c = __byte_perm(in[2], in[3], 0x5140), d = __byte_perm(in[2], in[3], 0x7362);
+    out[0] = __byte_perm(a, c, 0x5410);
+    out[1] = __byte_perm(a, c, 0x7632);
+    out[2] = __byte_perm(b, d, 0x5410);
+    out[3] = __byte_perm(b, d, 0x7632);
 }
 
 // four int8 digits (two's complement) of four magnitudes 0..127, sign bytes

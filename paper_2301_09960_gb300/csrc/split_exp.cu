@@ -15,18 +15,21 @@ static void init_exponents(const SplitArgs& g, cudaStream_t st) {
     k_init_exponents<<<(unsigned)((mx + 255) / 256), 256, 0, st>>>(g.E, g.mp, g.F, g.np, g.status);
 }
 
-template <typename T>
+template <typename T, int Q>
 static cudaError_t exponents_impl(const SplitArgs& g, cudaStream_t st) {
     Operand<T> a = make_op<T>(g.A, g.q, g.lda);
     Operand<T> b = make_op<T>(g.B, g.q, g.ldb);
     init_exponents(g, st);
+    // short per-thread chains (16 elements a row chunk, k / split a column
+    // part), so that many independent loads are in flight per SM
     if (g.m > 0 && g.k > 0) {
-        int kchunk = 64;
+        int kchunk = 16;
         dim3 gr((unsigned)((g.m + 255) / 256), (unsigned)((g.k + kchunk - 1) / kchunk));
-        k_exp_rows<T><<<gr, 256, 0, st>>>(a, g.m, g.k, kchunk, g.E, g.status);
+        k_exp_rows<T, Q><<<gr, 256, 0, st>>>(a, g.m, g.k, kchunk, g.E, g.status);
     }
     if (g.n > 0 && g.k > 0) {
-        k_exp_cols<T><<<(unsigned)((g.n + 7) / 8), 256, 0, st>>>(b, g.k, g.n, g.F, g.status);
+        const int split = (int)((g.k + 1023) / 1024 < 8 ? (g.k + 1023) / 1024 : 8);
+        k_exp_cols<T, Q><<<(unsigned)((g.n * split + 7) / 8), 256, 0, st>>>(b, g.k, g.n, g.F, g.status, split);
     }
     return cudaGetLastError();
 }
@@ -39,7 +42,10 @@ cudaError_t launch_split(const SplitArgs& g, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         return launch_digits_big(g, st);
     }
-    cudaError_t e = g.is_f32 ? exponents_impl<float>(g, st) : exponents_impl<double>(g, st);
+    cudaError_t e = g.is_f32     ? exponents_impl<float, 3>(g, st)
+                    : g.q == 2   ? exponents_impl<double, 2>(g, st)
+                    : g.q == 3   ? exponents_impl<double, 3>(g, st)
+                                 : exponents_impl<double, 4>(g, st);
     if (e != cudaSuccess) return e;
     if (g.form == OZMP_FORM_FP64) return launch_digits_fp64(g, st);
     if (g.form == OZMP_FORM_INT8) return launch_digits_int8(g, st);

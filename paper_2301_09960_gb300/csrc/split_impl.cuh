@@ -38,14 +38,17 @@ __device__ __forceinline__ bool load_elem(const Operand<T>& op, int64_t idx, T (
 // arithmetic so that a thread's loads of several elements are all in flight
 // before the first one is decoded
 template <typename T>
-__device__ __forceinline__ void load_raw(const Operand<T>& op, bool inside, int64_t idx, T (&v)[4]) {
+__device__ __forceinline__ void load_raw(const Operand<T>& op, int q, bool inside, int64_t idx, T (&v)[4]) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) v[i] = (inside && i < op.q) ? op.c[i][idx] : (T)0;
+    for (int i = 0; i < 4; ++i) v[i] = (inside && i < q) ? op.c[i][idx] : (T)0;
 }
 
-// exponent of one loaded element; false for a non-finite component
+// exponent of one loaded element; false for a non-finite component.  The
+// encodings alone settle almost every element (exponent_fast); the others
+// are decoded and summed exactly.
 template <typename T>
 __device__ __forceinline__ bool exponent_loaded(const T (&v)[4], int q, int& e) {
+    if (exponent_fast<T>(v, q, e)) return true;
     Comp c[4];
     int Ptop;
     const bool ok = decode_all<T>(v, q, c, Ptop);
@@ -58,9 +61,12 @@ __device__ __forceinline__ bool exponent_loaded(const T (&v)[4], int q, int& e) 
 // ---------------------------------------------------------------------------
 // rows of a column-major m x k matrix: one thread per row, a chunk of
 // columns per block row; consecutive threads read consecutive addresses.
-template <typename T>
+// Q > 0: the component count known at compile time (the loops over the
+// components and their registers shrink to it); Q = 0: a.q at run time.
+template <typename T, int Q = 0>
 __device__ __forceinline__ void exp_rows_body(Operand<T> a, int64_t m, int64_t k, int kchunk, int32_t* E,
                                                   uint32_t* status, int64_t bx, int64_t by) {
+    const int q = Q ? Q : a.q;
     int64_t i = bx * blockDim.x + threadIdx.x;
     if (i >= m) return;
     int64_t p0 = by * kchunk;
@@ -71,11 +77,11 @@ __device__ __forceinline__ void exp_rows_body(Operand<T> a, int64_t m, int64_t k
     for (int64_t p = p0; p < p1; p += U) {
         T v[U][4];
 #pragma unroll
-        for (int u = 0; u < U; ++u) load_raw<T>(a, p + u < p1, i + (p + u) * a.ld, v[u]);
+        for (int u = 0; u < U; ++u) load_raw<T>(a, q, p + u < p1, i + (p + u) * a.ld, v[u]);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             int e;
-            ok &= exponent_loaded<T>(v[u], a.q, e);
+            ok &= exponent_loaded<T>(v[u], q, e);
             emax = e > emax ? e : emax;
         }
     }
@@ -83,31 +89,38 @@ __device__ __forceinline__ void exp_rows_body(Operand<T> a, int64_t m, int64_t k
     if (!ok) atomicOr(status, ST_NONFINITE);
 }
 
-template <typename T>
+template <typename T, int Q>
 __global__ void __launch_bounds__(256) k_exp_rows(Operand<T> a, int64_t m, int64_t k, int kchunk, int32_t* E,
                                                   uint32_t* status) {
-    exp_rows_body(a, m, k, kchunk, E, status, (int64_t)blockIdx.x, (int64_t)blockIdx.y);
+    exp_rows_body<T, Q>(a, m, k, kchunk, E, status, (int64_t)blockIdx.x, (int64_t)blockIdx.y);
 }
 
-// columns of a column-major k x n matrix (contiguous): one warp per column,
-// warp-shuffle max reduction.
-template <typename T>
-__device__ __forceinline__ void exp_cols_body(Operand<T> b, int64_t k, int64_t n, int32_t* F, uint32_t* status, int64_t bx, int64_t by) {
+// columns of a column-major k x n matrix (contiguous): `split` warps per
+// column (consecutive warps, each a contiguous part of k), warp-shuffle max
+// reduction, atomicMax across the parts (F starts at OZMP_EXP_ZERO).
+template <typename T, int Q = 0>
+__device__ __forceinline__ void exp_cols_body(Operand<T> b, int64_t k, int64_t n, int32_t* F, uint32_t* status,
+                                              int64_t bx, int64_t by, int split = 1) {
+    const int q = Q ? Q : b.q;
     int warps = blockDim.x >> 5;
-    int64_t j = bx * warps + (threadIdx.x >> 5);
+    int64_t gw = bx * warps + (threadIdx.x >> 5);
+    int64_t j = gw / split;
+    int part = (int)(gw % split);
     int lane = threadIdx.x & 31;
     if (j >= n) return;
+    const int64_t plen = ((k + split - 1) / split + 31) / 32 * 32;
+    const int64_t pa = part * plen, pb = pa + plen < k ? pa + plen : k;
     int emax = OZMP_EXP_ZERO;
     bool ok = true;
     constexpr int U = 4;   // elements whose loads are issued together
-    for (int64_t p = lane; p < k; p += 32 * U) {
+    for (int64_t p = pa + lane; p < pb; p += 32 * U) {
         T v[U][4];
 #pragma unroll
-        for (int u = 0; u < U; ++u) load_raw<T>(b, p + 32 * u < k, p + 32 * u + j * b.ld, v[u]);
+        for (int u = 0; u < U; ++u) load_raw<T>(b, q, p + 32 * u < pb, p + 32 * u + j * b.ld, v[u]);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             int e;
-            ok &= exponent_loaded<T>(v[u], b.q, e);
+            ok &= exponent_loaded<T>(v[u], q, e);
             emax = e > emax ? e : emax;
         }
     }
@@ -118,14 +131,16 @@ __device__ __forceinline__ void exp_cols_body(Operand<T> b, int64_t k, int64_t n
     }
     unsigned bad = __ballot_sync(0xffffffffu, !ok);
     if (lane == 0) {
-        F[j] = emax;
+        if (split == 1) F[j] = emax;
+        else if (emax != OZMP_EXP_ZERO) atomicMax(&F[j], emax);
         if (bad) atomicOr(status, ST_NONFINITE);
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_exp_cols(Operand<T> b, int64_t k, int64_t n, int32_t* F, uint32_t* status) {
-    exp_cols_body(b, k, n, F, status, (int64_t)blockIdx.x, (int64_t)blockIdx.y);
+template <typename T, int Q>
+__global__ void __launch_bounds__(256) k_exp_cols(Operand<T> b, int64_t k, int64_t n, int32_t* F, uint32_t* status,
+                                                  int split) {
+    exp_cols_body<T, Q>(b, k, n, F, status, (int64_t)blockIdx.x, (int64_t)blockIdx.y, split);
 }
 
 // ---------------------------------------------------------------------------
@@ -149,6 +164,43 @@ __device__ __forceinline__ uint32_t pack4(const uint64_t (&w)[4][NW], const int 
         if (sign[e] < 0) neg |= (FORM == OZMP_FORM_INT8 ? 0xFFu : 0x80u) << (8 * e);
     }
     return (FORM == OZMP_FORM_INT8) ? int8x4(m4, neg) : e4m3x4(m4, neg);
+}
+
+// The e4m3 digits of four elements (consecutive k), all slices: calls
+// put(t, word) for t = 1 .. s with byte e of `word` = e4m3 code of digit t of
+// element e.  The windows are shifted left one bit so that digit t becomes
+// the nibble at bits [64 NW - 4 t, 64 NW - 4 t + 4): each 32-bit half-word
+// then holds 8 whole digits, encoded 4 at a time by table lookup and
+// transposed across the elements in registers.
+template <int NW, typename Put>
+__device__ __forceinline__ void pack_fp8_quad(uint64_t (&w)[4][NW], const int (&sign)[4], int s, Put&& put) {
+    constexpr int MAXS = DigitTraits<OZMP_FORM_FP8>::MAXS;
+    uint32_t negm[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        mw_shl<NW>(w[e], 1);
+        negm[e] = sign[e] < 0 ? 0x80808080u : 0u;
+    }
+#pragma unroll
+    for (int h = 0; h < 2 * NW && 8 * h < MAXS; ++h) {
+        if (8 * h >= s) break;
+        const int wi = NW - 1 - (h >> 1);
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const uint32_t X = (h & 1) ? (uint32_t)w[e][wi] : (uint32_t)(w[e][wi] >> 32);
+            lo[e] = e4m3_nibbles4(X, negm[e]);         // digits 8h+8, 8h+7, 8h+6, 8h+5 in bytes 0..3
+            hi[e] = e4m3_nibbles4(X >> 16, negm[e]);   // digits 8h+4 .. 8h+1
+        }
+        uint32_t th[4], tl[4];
+        transpose4(hi, th);
+        transpose4(lo, tl);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            if (8 * h + 4 - b <= s) put(8 * h + 4 - b, th[b]);
+            if (8 * h + 8 - b <= s) put(8 * h + 8 - b, tl[b]);
+        }
+    }
 }
 
 template <typename T, int NW>
@@ -184,9 +236,10 @@ __device__ __forceinline__ int window_loaded(const T (&v)[4], int q, int Erow, u
 // 4 consecutive columns of one row (two quads per thread); the 4 digits of
 // a slice go to shared memory as one word [t][ri][quad], then the tile is
 // written K-contiguous.
-template <typename T, int FORM, int NW>
+template <typename T, int FORM, int NW, int Q = 0>
 __device__ __forceinline__ void split_rows_b1_body(Operand<T> a, int64_t m, int64_t k, const int32_t* E,
                                                        uint8_t* dig, int64_t mp, int64_t kp, int s, int64_t bx, int64_t by) {
+    const int q = Q ? Q : a.q;
     constexpr int TI = 32, TP = 64, QW = TP / 4;    // 16 words per tile row
     extern __shared__ __align__(16) uint32_t sw[];  // [s][TI][QW]
     const int64_t i0 = bx * TI, p0 = by * TP;
@@ -202,13 +255,17 @@ __device__ __forceinline__ void split_rows_b1_body(Operand<T> a, int64_t m, int6
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int64_t p = p0 + 4 * qd + e;
-            load_raw<T>(a, i < m && p < k, i + p * a.ld, v[e]);
+            load_raw<T>(a, q, i < m && p < k, i + p * a.ld, v[e]);
         }
 #pragma unroll
-        for (int e = 0; e < 4; ++e) sign[e] = window_loaded<T, NW>(v[e], a.q, Erow, w[e]);
+        for (int e = 0; e < 4; ++e) sign[e] = window_loaded<T, NW>(v[e], q, Erow, w[e]);
+        if constexpr (FORM == OZMP_FORM_FP8) {
+            pack_fp8_quad<NW>(w, sign, s, [&](int t, uint32_t word) { sw[((t - 1) * TI + ri) * QW + qd] = word; });
+        } else {
 #pragma unroll
-        for (int t = 1; t <= DigitTraits<FORM>::MAXS; ++t)
-            if (t <= s) sw[((t - 1) * TI + ri) * QW + qd] = pack4<FORM, NW>(w, sign, t);
+            for (int t = 1; t <= DigitTraits<FORM>::MAXS; ++t)
+                if (t <= s) sw[((t - 1) * TI + ri) * QW + qd] = pack4<FORM, NW>(w, sign, t);
+        }
     }
     __syncthreads();
     const int total = s * TI * QW;
@@ -218,17 +275,18 @@ __device__ __forceinline__ void split_rows_b1_body(Operand<T> a, int64_t m, int6
     }
 }
 
-template <typename T, int FORM, int NW>
+template <typename T, int FORM, int NW, int Q>
 __global__ void __launch_bounds__(256) k_split_rows_b1(Operand<T> a, int64_t m, int64_t k, const int32_t* E,
                                                        uint8_t* dig, int64_t mp, int64_t kp, int s) {
-    split_rows_b1_body<T, FORM, NW>(a, m, k, E, dig, mp, kp, s, (int64_t)blockIdx.x, (int64_t)blockIdx.y);
+    split_rows_b1_body<T, FORM, NW, Q>(a, m, k, E, dig, mp, kp, s, (int64_t)blockIdx.x, (int64_t)blockIdx.y);
 }
 
 // Columns of B (contiguous along k) -> Bdig[(t * np + j) * kp + p], 1-byte
 // digits: 4 consecutive k per thread, one 32-bit store per slice.
-template <typename T, int FORM, int NW>
+template <typename T, int FORM, int NW, int Q = 0>
 __device__ __forceinline__ void split_cols_b1_body(Operand<T> b, int64_t k, int64_t n, const int32_t* F,
                                                        uint8_t* dig, int64_t np, int64_t kp, int s, int64_t bx, int64_t by) {
+    const int q = Q ? Q : b.q;
     const int64_t quads = kp / 4;
     int64_t g = bx * blockDim.x + threadIdx.x;
     if (g >= quads * np) return;
@@ -239,19 +297,25 @@ __device__ __forceinline__ void split_cols_b1_body(Operand<T> b, int64_t k, int6
     int sign[4];
     T v[4][4];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) load_raw<T>(b, j < n && p0 + e < k, p0 + e + j * b.ld, v[e]);
+    for (int e = 0; e < 4; ++e) load_raw<T>(b, q, j < n && p0 + e < k, p0 + e + j * b.ld, v[e]);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) sign[e] = window_loaded<T, NW>(v[e], b.q, Ecol, w[e]);
+    for (int e = 0; e < 4; ++e) sign[e] = window_loaded<T, NW>(v[e], q, Ecol, w[e]);
+    if constexpr (FORM == OZMP_FORM_FP8) {
+        pack_fp8_quad<NW>(w, sign, s, [&](int t, uint32_t word) {
+            *reinterpret_cast<uint32_t*>(dig + ((size_t)(t - 1) * np + j) * kp + p0) = word;
+        });
+    } else {
 #pragma unroll
-    for (int t = 1; t <= DigitTraits<FORM>::MAXS; ++t)
-        if (t <= s)
-            *reinterpret_cast<uint32_t*>(dig + ((size_t)(t - 1) * np + j) * kp + p0) = pack4<FORM, NW>(w, sign, t);
+        for (int t = 1; t <= DigitTraits<FORM>::MAXS; ++t)
+            if (t <= s)
+                *reinterpret_cast<uint32_t*>(dig + ((size_t)(t - 1) * np + j) * kp + p0) = pack4<FORM, NW>(w, sign, t);
+    }
 }
 
-template <typename T, int FORM, int NW>
+template <typename T, int FORM, int NW, int Q>
 __global__ void __launch_bounds__(256) k_split_cols_b1(Operand<T> b, int64_t k, int64_t n, const int32_t* F,
                                                        uint8_t* dig, int64_t np, int64_t kp, int s) {
-    split_cols_b1_body<T, FORM, NW>(b, k, n, F, dig, np, kp, s, (int64_t)blockIdx.x, (int64_t)blockIdx.y);
+    split_cols_b1_body<T, FORM, NW, Q>(b, k, n, F, dig, np, kp, s, (int64_t)blockIdx.x, (int64_t)blockIdx.y);
 }
 
 // binary64 digits, rows of A: 16 x 16 tile staged in shared memory
@@ -309,20 +373,35 @@ static inline Operand<T> make_op(const void* const* comps, int q, int64_t ld) {
 // words of the digit window: word 0 below every digit, sign bit on top
 static inline int digit_words(int beta, int s) { return (beta * s + 65 + 63) / 64; }
 
-template <typename T, int FORM, int NW>
-static cudaError_t digits_b1(const SplitArgs& g, cudaStream_t st) {
+template <typename T, int FORM, int NW, int Q>
+static cudaError_t digits_b1_q(const SplitArgs& g, cudaStream_t st) {
     Operand<T> a = make_op<T>(g.A, g.q, g.lda);
     Operand<T> b = make_op<T>(g.B, g.q, g.ldb);
     dim3 gr((unsigned)(g.mp / 32), (unsigned)(g.kp / 64));
     size_t sm = (size_t)g.s * 32 * 16 * 4;
-    auto kr = k_split_rows_b1<T, FORM, NW>;
+    auto kr = k_split_rows_b1<T, FORM, NW, Q>;
     cudaError_t e = cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     kr<<<gr, 256, sm, st>>>(a, g.m, g.k, g.E, (uint8_t*)g.Adig, g.mp, g.kp, g.s);
     int64_t tot = (g.kp / 4) * g.np;
-    k_split_cols_b1<T, FORM, NW><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(b, g.k, g.n, g.F, (uint8_t*)g.Bdig,
-                                                                              g.np, g.kp, g.s);
+    k_split_cols_b1<T, FORM, NW, Q><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(b, g.k, g.n, g.F,
+                                                                                 (uint8_t*)g.Bdig, g.np, g.kp, g.s);
     return cudaGetLastError();
+}
+
+// the e4m3 form (the product path) is specialised on the component count;
+// the int8 form keeps it a run-time value
+template <typename T, int FORM, int NW>
+static cudaError_t digits_b1(const SplitArgs& g, cudaStream_t st) {
+    if constexpr (FORM == OZMP_FORM_FP8 && sizeof(T) == 8) {
+        if (g.q == 2) return digits_b1_q<T, FORM, NW, 2>(g, st);
+        if (g.q == 3) return digits_b1_q<T, FORM, NW, 3>(g, st);
+        return digits_b1_q<T, FORM, NW, 4>(g, st);
+    } else if constexpr (FORM == OZMP_FORM_FP8) {
+        return digits_b1_q<T, FORM, NW, 3>(g, st);
+    } else {
+        return digits_b1_q<T, FORM, NW, 0>(g, st);
+    }
 }
 
 template <typename T, int NW>
