@@ -19,7 +19,9 @@ Printed: one JSON line (rank 0).  Besides the contract keys it carries
                    host cores, on a bounded block of the same product, with
                    the GPU result's error against it;
   variants      -- single timed passes of the other forms/precisions
-                   (DD and QD, e4m3 / int8 / binary64 digits) at 4096^3.
+                   (DD and QD, e4m3 / int8 / binary64 digits) at 4096^3;
+  multiprecision_2048 -- 8 and 16 binary64 components (424 / 848 bits)
+                   at 2048^3, e4m3 digits on tcgen05.
 
 --impl reference times the oracle itself (the CPU reference of this repo)
 on a bounded block per step.
@@ -452,6 +454,17 @@ def main():
             except Exception as ex:  # report, do not hide
                 var.append({"prec": vp, "form": vf, "error": repr(ex)[:200]})
         line["variants"] = var
+        # more components (Sec. 5's multiple precisions beyond QD): q binary64
+        # words, about 53 q bits, target 2^(-50 q); one timed pass at 2048^3
+        md = []
+        for q in (8, 16):
+            try:
+                r = run_variant(oz, torch, f"q{q}", "fp8", 2048, args.phi, 1, 1)
+                r["bits"] = 53 * q
+                md.append(r)
+            except Exception as ex:
+                md.append({"prec": f"q{q}", "form": "fp8", "error": repr(ex)[:200]})
+        line["multiprecision_2048"] = md
         line["config2_td_qd_1024"] = config2(oz, torch)
         line["config4_batched512"] = config4(oz, torch)
 
