@@ -265,6 +265,27 @@ ozmp_status ozmp_plan_split(ozmp_plan plan, const void* const* A, int64_t lda,
 ozmp_status ozmp_plan_multiply(ozmp_plan plan, void* const* C, int64_t ldc);
 ozmp_status ozmp_plan_diagonal(ozmp_plan plan, int d, int64_t* T);
 
+/*
+ * LU factorisation without pivoting (Sec. 5, "LU decomposition using
+ * matrix multiplication"): A = L U in place, L unit lower (its diagonal not
+ * stored), U upper, for q binary64 components, 2 <= q <= 4 (DD, TD, QD).
+ * A: q device pointers, n x n column-major, leading dimension lda >= n.
+ * The factorisation recurses on halves down to 32 x 32 blocks; the trailing
+ * updates A22 - L21 U12 and the off-diagonal updates of the triangular
+ * solves are Ozaki-scheme products (tcgen05 e4m3 form, slice count for the
+ * precision's target); every other operation is evaluated exactly and
+ * rounded once into q components (pivot reciprocals by a fixed Newton
+ * sequence of such operations).  Synchronous: returns after the stream has
+ * finished, with the device status (RANGE for a zero pivot or an exponent
+ * outside the accumulator, NONFINITE, ...).  Errors: INVALID_ARG, NOMEM,
+ * CUDA.  Workspace and product plans are kept per calling thread.
+ */
+ozmp_status ozmp_lu(int q, int64_t n, double* const* A, int64_t lda, ozmp_stream stream);
+/* Solve A X = B with the factors of ozmp_lu (L Y = B, then U X = Y), in
+ * place in B (n x nrhs, ldb >= n, q components); synchronous as ozmp_lu. */
+ozmp_status ozmp_lu_solve(int q, int64_t n, int64_t nrhs, const double* const* LU, int64_t lda,
+                          double* const* B, int64_t ldb, ozmp_stream stream);
+
 /* Kernel timing (instrumentation; the paper has no counterpart).
  * ozmp_plan_set_timing: with nslots > 0 the plan owns a ring of nslots CUDA
  *   event pairs and, at every ozmp_plan_execute / ozmp_plan_multiply, records

@@ -24,7 +24,7 @@ __all__ = [
     "Status", "Prec", "Form", "OzmpError", "PlanInfo", "Plan", "load", "colmajor",
     "ozmp_plan_create", "ozmp_plan_destroy", "ozmp_plan_get_info", "ozmp_plan_set_workspace",
     "ozmp_plan_set_stream", "ozmp_plan_execute", "ozmp_plan_get_status", "ozmp_plan_split",
-    "ozmp_plan_diagonal", "ozmp_plan_multiply", "ozmp_plan_set_timing", "ozmp_plan_read_timing", "ozmp_gemm_dd", "ozmp_gemm_td", "ozmp_gemm_qd", "ozmp_gemm_ts", "ozmp_gemm_md", "prec_code", "MAX_COMPONENTS", "ozmp_gemm_dd_noalloc", "ozmp_gemm_batched", "Problem", "ozmp_gemm_naive",
+    "ozmp_plan_diagonal", "ozmp_plan_multiply", "ozmp_plan_set_timing", "ozmp_plan_read_timing", "ozmp_gemm_dd", "ozmp_gemm_td", "ozmp_gemm_qd", "ozmp_gemm_ts", "ozmp_gemm_md", "ozmp_lu", "ozmp_lu_solve", "prec_code", "MAX_COMPONENTS", "ozmp_gemm_dd_noalloc", "ozmp_gemm_batched", "Problem", "ozmp_gemm_naive",
     "ozmp_set_stream", "ozmp_set_form", "ozmp_last_status", "ozmp_version", "gemm", "EXP_ZERO",
 ]
 
@@ -133,6 +133,8 @@ SIGNATURES = {
     "ozmp_gemm_qd": [_I64, _I64, _I64, _PP, _I64, _PP, _I64, _PP, _I64, ctypes.c_int],
     "ozmp_gemm_ts": [_I64, _I64, _I64, _PP, _I64, _PP, _I64, _PP, _I64, ctypes.c_int],
     "ozmp_gemm_md": [ctypes.c_int, _I64, _I64, _I64, _PP, _I64, _PP, _I64, _PP, _I64, ctypes.c_int],
+    "ozmp_lu": [ctypes.c_int, _I64, _PP, _I64, _VP],
+    "ozmp_lu_solve": [ctypes.c_int, _I64, _I64, _PP, _I64, _PP, _I64, _VP],
     "ozmp_gemm_dd_noalloc": [_I64, _I64, _I64, _PP, _I64, _PP, _I64, _PP, _I64, ctypes.c_int, _VP],
     "ozmp_set_stream": [_VP],
     "ozmp_set_form": [ctypes.c_int],
@@ -298,6 +300,29 @@ def ozmp_gemm_qd(A, B, C, nslices=0):
 
 def ozmp_gemm_ts(A, B, C, nslices=0):
     _plain("ozmp_gemm_ts", A, B, C, nslices)
+
+
+def ozmp_lu(A, stream=None):
+    """In-place LU without pivoting of the n x n q-component matrix A (list of
+    q column-major torch tensors); returns the device status."""
+    n = A[0].shape[0]
+    pa, ka = _ptrs(A)
+    st = load().ozmp_lu(len(A), n, pa, _ld(A[0]), _stream_handle(stream))
+    if st in (Status.ERR_INVALID_ARG, Status.ERR_NOMEM, Status.ERR_CUDA, Status.ERR_UNSUPPORTED):
+        _check(st, "ozmp_lu")
+    return Status(st)
+
+
+def ozmp_lu_solve(LU, B, stream=None):
+    """Solve with the factors of ozmp_lu, in place in B (n x nrhs)."""
+    n = LU[0].shape[0]
+    nrhs = B[0].shape[1]
+    pa, ka = _ptrs(LU)
+    pb, kb = _ptrs(B)
+    st = load().ozmp_lu_solve(len(LU), n, nrhs, pa, _ld(LU[0]), pb, _ld(B[0]), _stream_handle(stream))
+    if st in (Status.ERR_INVALID_ARG, Status.ERR_NOMEM, Status.ERR_CUDA, Status.ERR_UNSUPPORTED):
+        _check(st, "ozmp_lu_solve")
+    return Status(st)
 
 
 def ozmp_gemm_md(A, B, C, nslices=0):
