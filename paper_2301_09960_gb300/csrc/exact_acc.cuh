@@ -174,5 +174,165 @@ __device__ __noinline__ void round_q(Acc& a, int q, double* out) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// The same operation with a register-resident window (the fast path).  A
+// term generator gen(v) calls v.value(x) and v.product(x, y, negate) for
+// every term; it is walked twice: once for the largest leading-bit position
+// and the term count, which fix a window of NW words whose top leaves room
+// for the carries, and once to add the terms exactly.  If a term has bits
+// below the window the register sum is not exact and the local-memory
+// accumulator above evaluates the terms instead.  Either way the result is
+// the exact value rounded canonically into q components.
+// ---------------------------------------------------------------------------
+struct TopVisitor {
+    int top = -100000;   // largest leading-bit position (weight 2^top)
+    int count = 0;
+    __device__ __forceinline__ void value(double x) {
+        Comp c;
+        decode(x, c);
+        if (!c.M) return;
+        const int t = c.e + 63 - __clzll((long long)c.M);
+        top = t > top ? t : top;
+        ++count;
+    }
+    __device__ __forceinline__ void product(double x, double y, bool) {
+        Comp cx, cy;
+        decode(x, cx);
+        decode(y, cy);
+        if (!cx.M || !cy.M) return;
+        const int t = cx.e + cy.e + (63 - __clzll((long long)cx.M)) + (63 - __clzll((long long)cy.M)) + 1;
+        top = t > top ? t : top;
+        ++count;
+    }
+};
+
+template <int NW>
+struct RegVisitor {
+    uint64_t w[NW];
+    int L;               // weight of window bit 0
+    bool tail;           // some term had bits below the window
+
+    __device__ __forceinline__ void init(int top, int count) {
+#pragma unroll
+        for (int j = 0; j < NW; ++j) w[j] = 0;
+        int g = 1;
+        while ((1 << g) <= count) ++g;          // |sum| < 2^(top + 1 + g)
+        L = top + 1 + g - (64 * NW - 1);        // bit 64 NW - 1 is the sign
+        tail = false;
+    }
+    __device__ __forceinline__ void add128(uint64_t hi, uint64_t lo, int e, bool neg) {
+        int sh = e - L;
+        if (sh < 0) {
+            const int r = -sh;
+            bool lost;
+            if (r >= 128) lost = (hi | lo) != 0;
+            else if (r >= 64) lost = (lo != 0) || (r > 64 && (hi << (128 - r)) != 0);
+            else lost = (lo << (64 - r)) != 0;
+            if (lost) { tail = true; return; }
+            if (r >= 128) return;
+            if (r >= 64) { lo = hi >> (r - 64); hi = 0; }
+            else { lo = (lo >> r) | (hi << (64 - r)); hi >>= r; }
+            sh = 0;
+        }
+        const int wi = sh >> 6, b = sh & 63;
+        const uint64_t p0 = lo << b;
+        const uint64_t p1 = b ? ((hi << b) | (lo >> (64 - b))) : hi;
+        const uint64_t p2 = b ? (hi >> (64 - b)) : 0ull;
+        uint64_t p[NW];
+#pragma unroll
+        for (int j = 0; j < NW; ++j) p[j] = (j == wi) ? p0 : (j == wi + 1) ? p1 : (j == wi + 2) ? p2 : 0ull;
+        if (neg) mw_sub<NW>(w, p); else mw_add<NW>(w, p);
+    }
+    __device__ __forceinline__ void value(double x) {
+        Comp c;
+        decode(x, c);
+        if (c.M) add128(0, c.M, c.e, c.neg != 0);
+    }
+    __device__ __forceinline__ void product(double x, double y, bool negate) {
+        Comp cx, cy;
+        decode(x, cx);
+        decode(y, cy);
+        if (!cx.M || !cy.M) return;
+        add128(__umul64hi(cx.M, cy.M), cx.M * cy.M, cx.e + cy.e, ((cx.neg ^ cy.neg) != 0) != negate);
+    }
+};
+
+struct KulVisitor {
+    Acc a;
+    __device__ __forceinline__ void value(double x) { add_value(a, x); }
+    __device__ __forceinline__ void product(double x, double y, bool negate) { add_product(a, x, y, negate); }
+};
+
+// out[0 .. q-1] = canonical rounding of the exact sum of gen's terms; `bad`
+// is set when a term or a component leaves the representable range
+template <int NW, typename Gen>
+__device__ __forceinline__ void exact_round(int q, Gen&& gen, double* out, bool& bad) {
+    TopVisitor tv;
+    gen(tv);
+    if (tv.count == 0) {
+        for (int c = 0; c < q; ++c) out[c] = 0.0;
+        return;
+    }
+    RegVisitor<NW> rv;
+    rv.init(tv.top, tv.count);
+    gen(rv);
+    if (!rv.tail) {
+        if (!canonical_round<NW, double>(rv.w, rv.L, q, out)) bad = true;
+        return;
+    }
+    KulVisitor kv;
+    clear(kv.a);
+    gen(kv);
+    bad |= kv.a.range_bad;
+    round_q(kv.a, q, out);
+    bad |= kv.a.range_bad;
+}
+
+// Warp-cooperative form: gen(v, part) yields the terms of part `part`
+// (0 .. 31); lane l adds part l into its own register window (all lanes
+// share the anchor from the warp-wide largest leading bit and term count),
+// the 32 windows are summed exactly with xor shuffles, and every lane
+// rounds the total.  If some lane's terms have bits below the window, one
+// lane evaluates all parts in the local-memory accumulator and broadcasts
+// the result.  All 32 lanes of the warp must call this together.
+template <int NW, typename Gen>
+__device__ __forceinline__ void warp_exact_round(int q, Gen&& gen, double* out, bool& bad) {
+    const int lane = threadIdx.x & 31;
+    TopVisitor tv;
+    gen(tv, lane);
+    const int top = __reduce_max_sync(0xffffffffu, tv.top);
+    const int count = (int)__reduce_add_sync(0xffffffffu, (unsigned)tv.count);
+    if (count == 0) {
+        for (int c = 0; c < q; ++c) out[c] = 0.0;
+        return;
+    }
+    RegVisitor<NW> rv;
+    rv.init(top, count);
+    gen(rv, lane);
+    if (!__any_sync(0xffffffffu, rv.tail)) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            uint64_t other[NW];
+#pragma unroll
+            for (int j = 0; j < NW; ++j) other[j] = __shfl_xor_sync(0xffffffffu, rv.w[j], o);
+            mw_add<NW>(rv.w, other);
+        }
+        if (!canonical_round<NW, double>(rv.w, rv.L, q, out)) bad = true;
+        return;
+    }
+    double res[8];
+    bool b = false;
+    if (lane == 0) {
+        KulVisitor kv;
+        clear(kv.a);
+        for (int part = 0; part < 32; ++part) gen(kv, part);
+        b = kv.a.range_bad;
+        round_q(kv.a, q, res);
+        b |= kv.a.range_bad;
+    }
+    for (int c = 0; c < q; ++c) out[c] = __shfl_sync(0xffffffffu, res[c], 0);
+    bad |= __shfl_sync(0xffffffffu, (int)b, 0) != 0;
+}
+
 }  // namespace xacc
 }  // namespace ozmp

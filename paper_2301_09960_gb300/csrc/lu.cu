@@ -27,7 +27,6 @@
 namespace ozmp {
 namespace lu {
 
-using xacc::Acc;
 constexpr int NB = 32;      // base block
 constexpr int QL = 4;       // largest component count of the LU path
 
@@ -39,238 +38,277 @@ struct Mat {
 // number of Newton steps for q components: 53 correct bits doubled each step
 __host__ __device__ constexpr int newton_steps(int q) { return q <= 1 ? 0 : (q <= 2 ? 2 : 3); }
 
-// r = 1 / d to q components: x_0 = RN(1 / d_0); x := x + x (1 - d x), each
+// register window of the exact operations: 2 q + 2 words hold every term of
+// the products of q-component values of similar size
+template <int Q>
+struct W { static constexpr int NW = 2 * Q + 2; };
+
+// r = 1 / d to Q components: x_0 = RN(1 / d_0); x := x + x (1 - d x), each
 // operation evaluated exactly and rounded canonically
-__device__ void recip_q(const double* d, int q, double* r, bool& bad) {
-    double x[QL] = {0, 0, 0, 0}, e[QL] = {0, 0, 0, 0};
+template <int Q>
+__device__ void recip_q(const double* d, double* r, bool& bad) {
+    double x[Q], e[Q];
+#pragma unroll
+    for (int c = 0; c < Q; ++c) x[c] = 0.0;
     x[0] = 1.0 / d[0];
-    Acc a;
-    for (int it = 0; it < newton_steps(q); ++it) {
-        xacc::clear(a);
-        xacc::add_value(a, 1.0);
-        for (int i = 0; i < q; ++i)
-            for (int j = 0; j < q; ++j) xacc::add_product(a, d[i], x[j], true);
-        bad |= a.range_bad;
-        xacc::round_q(a, q, e);
-        bad |= a.range_bad;
-        xacc::clear(a);
-        for (int i = 0; i < q; ++i) xacc::add_value(a, x[i]);
-        for (int i = 0; i < q; ++i)
-            for (int j = 0; j < q; ++j) xacc::add_product(a, x[i], e[j], false);
-        bad |= a.range_bad;
-        xacc::round_q(a, q, x);
-        bad |= a.range_bad;
+    for (int it = 0; it < newton_steps(Q); ++it) {
+        xacc::exact_round<W<Q>::NW>(Q, [&](auto& v) {
+            v.value(1.0);
+            for (int i = 0; i < Q; ++i)
+                for (int j = 0; j < Q; ++j) v.product(d[i], x[j], true);
+        }, e, bad);
+        double y[Q];
+        xacc::exact_round<W<Q>::NW>(Q, [&](auto& v) {
+            for (int i = 0; i < Q; ++i) v.value(x[i]);
+            for (int i = 0; i < Q; ++i)
+                for (int j = 0; j < Q; ++j) v.product(x[i], e[j], false);
+        }, y, bad);
+#pragma unroll
+        for (int c = 0; c < Q; ++c) x[c] = y[c];
     }
-    for (int i = 0; i < q; ++i) r[i] = x[i];
+#pragma unroll
+    for (int c = 0; c < Q; ++c) r[c] = x[c];
 }
 
-// a += sum_{t} sign * X[t] Y[t] for q-component values (component-major)
-__device__ __forceinline__ void dot_into(Acc& a, const double* xs, int xstride, const double* ys, int ystride,
-                                         int cstride_x, int cstride_y, int len, int q) {
-    for (int t = 0; t < len; ++t)
-        for (int i = 0; i < q; ++i)
-            for (int j = 0; j < q; ++j)
-                xacc::add_product(a, xs[t * xstride + i * cstride_x], ys[t * ystride + j * cstride_y], true);
+// RN_Q(n * r) for Q-component n and r
+template <int Q>
+__device__ __forceinline__ void mul_round(const double* n, const double* r, double* out, bool& bad) {
+    xacc::exact_round<W<Q>::NW>(Q, [&](auto& v) {
+        for (int i = 0; i < Q; ++i)
+            for (int j = 0; j < Q; ++j) v.product(n[i], r[j], false);
+    }, out, bad);
 }
 
 // shared-memory copy of an n x n block: S[(c * NB + j) * NB + i] = component c of (i, j)
-__device__ __forceinline__ void stage(const Mat& A, int n, int q, double* S) {
-    for (int x = threadIdx.x; x < q * NB * NB; x += blockDim.x) {
+template <int Q>
+__device__ __forceinline__ void stage(const Mat& A, int n, double* S) {
+    for (int x = threadIdx.x; x < Q * NB * NB; x += blockDim.x) {
         const int c = x / (NB * NB), j = (x / NB) % NB, i = x % NB;
         S[x] = (i < n && j < n) ? A.c[c][i + (int64_t)j * A.ld] : 0.0;
     }
 }
+#define SIDX(c, i, j) (((c) * NB + (j)) * NB + (i))
 
 // 32 x 32 (or smaller) LU in one CTA, Crout order: for k = 0 .. n-1, row k
-// of U then column k of L, each entry one exact dot product rounded once;
+// of U then column k of L, each entry one exact dot product rounded once
+// (a warp per entry, its lanes sharing the terms);
 // l_ik = RN_q(RN_q(a_ik - sum) * RN_q(1 / u_kk)).
-__global__ void __launch_bounds__(64) k_base_lu(Mat A, int n, int q, uint32_t* status) {
-    __shared__ double S[QL * NB * NB];
-    __shared__ double R[QL];
+constexpr int LU_WARPS = 16;
+
+template <int Q>
+__global__ void __launch_bounds__(32 * LU_WARPS) k_base_lu(Mat A, int n, uint32_t* status) {
+    __shared__ double S[Q * NB * NB];
+    __shared__ double R[Q];
     __shared__ int bad_any;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) bad_any = 0;
-    stage(A, n, q, S);
+    stage<Q>(A, n, S);
     __syncthreads();
     bool bad = false;
-    Acc a;
-    double out[QL];
+    double out[Q];
     for (int k = 0; k < n; ++k) {
         // row k of U: u_kj = a_kj - sum_{t<k} l_kt u_tj, j = k .. n-1
-        for (int j = k + (int)threadIdx.x; j < n; j += blockDim.x) {
-            xacc::clear(a);
-            for (int c = 0; c < q; ++c) xacc::add_value(a, S[(c * NB + j) * NB + k]);
-            dot_into(a, &S[k], NB, &S[j * NB], 1, NB * NB, NB * NB, k, q);
-            bad |= a.range_bad;
-            xacc::round_q(a, q, out);
-            bad |= a.range_bad;
-            for (int c = 0; c < q; ++c) S[(c * NB + j) * NB + k] = out[c];
+        for (int j = k + warp; j < n; j += LU_WARPS) {
+            xacc::warp_exact_round<W<Q>::NW>(Q, [&](auto& v, int part) {
+                if (part == 0)
+                    for (int c = 0; c < Q; ++c) v.value(S[SIDX(c, k, j)]);
+                for (int t = part; t < k; t += 32)
+                    for (int c1 = 0; c1 < Q; ++c1)
+                        for (int c2 = 0; c2 < Q; ++c2) v.product(S[SIDX(c1, k, t)], S[SIDX(c2, t, j)], true);
+            }, out, bad);
+            if (lane == 0)
+#pragma unroll
+                for (int c = 0; c < Q; ++c) S[SIDX(c, k, j)] = out[c];
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            double d[QL];
-            for (int c = 0; c < q; ++c) d[c] = S[(c * NB + k) * NB + k];
+            double d[Q];
+#pragma unroll
+            for (int c = 0; c < Q; ++c) d[c] = S[SIDX(c, k, k)];
             if (d[0] == 0.0) bad = true;
-            else recip_q(d, q, R, bad);
+            else recip_q<Q>(d, R, bad);
         }
         __syncthreads();
         // column k of L: l_ik = (a_ik - sum_{t<k} l_it u_tk) / u_kk, i = k+1 .. n-1
-        for (int i = k + 1 + (int)threadIdx.x; i < n; i += blockDim.x) {
-            xacc::clear(a);
-            for (int c = 0; c < q; ++c) xacc::add_value(a, S[(c * NB + k) * NB + i]);
-            dot_into(a, &S[i], NB, &S[k * NB], 1, NB * NB, NB * NB, k, q);
-            bad |= a.range_bad;
-            double num[QL];
-            xacc::round_q(a, q, num);
-            xacc::clear(a);
-            for (int c1 = 0; c1 < q; ++c1)
-                for (int c2 = 0; c2 < q; ++c2) xacc::add_product(a, num[c1], R[c2], false);
-            bad |= a.range_bad;
-            xacc::round_q(a, q, out);
-            bad |= a.range_bad;
-            for (int c = 0; c < q; ++c) S[(c * NB + k) * NB + i] = out[c];
+        for (int i = k + 1 + warp; i < n; i += LU_WARPS) {
+            double num[Q];
+            xacc::warp_exact_round<W<Q>::NW>(Q, [&](auto& v, int part) {
+                if (part == 0)
+                    for (int c = 0; c < Q; ++c) v.value(S[SIDX(c, i, k)]);
+                for (int t = part; t < k; t += 32)
+                    for (int c1 = 0; c1 < Q; ++c1)
+                        for (int c2 = 0; c2 < Q; ++c2) v.product(S[SIDX(c1, i, t)], S[SIDX(c2, t, k)], true);
+            }, num, bad);
+            if (lane == 0) {
+                mul_round<Q>(num, R, out, bad);
+#pragma unroll
+                for (int c = 0; c < Q; ++c) S[SIDX(c, i, k)] = out[c];
+            }
         }
         __syncthreads();
     }
     if (bad) atomicOr(&bad_any, 1);
     __syncthreads();
-    for (int x = threadIdx.x; x < q * NB * NB; x += blockDim.x) {
+    for (int x = threadIdx.x; x < Q * NB * NB; x += blockDim.x) {
         const int c = x / (NB * NB), j = (x / NB) % NB, i = x % NB;
         if (i < n && j < n) A.c[c][i + (int64_t)j * A.ld] = S[x];
     }
     if (threadIdx.x == 0 && bad_any) atomicOr(status, ST_RANGE);
 }
 
-// L X = B, L n x n unit lower (n <= 32), B n x w: one thread per column,
+constexpr int TS_WARPS = 4;   // warps (right-hand sides) per CTA of the triangular-solve bases
+
+// L X = B, L n x n unit lower (n <= 32), B n x w: one warp per column,
 // x_ij = RN_q(b_ij - sum_{t<i} l_it x_tj), in place in B
-__global__ void __launch_bounds__(128) k_base_trsm_ll(Mat L, Mat B, int n, int64_t w, int q, uint32_t* status) {
-    __shared__ double S[QL * NB * NB];
-    stage(L, n, q, S);
+template <int Q>
+__global__ void __launch_bounds__(32 * TS_WARPS) k_base_trsm_ll(Mat L, Mat B, int n, int64_t w, uint32_t* status) {
+    __shared__ double S[Q * NB * NB];
+    __shared__ double Xs[TS_WARPS][Q * NB];
+    stage<Q>(L, n, S);
     __syncthreads();
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= w) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * TS_WARPS + warp;
+    if (j >= w) return;   // the whole warp
+    double* X = Xs[warp];
     bool bad = false;
-    Acc a;
-    double out[QL];
-    double X[QL * NB];   // column j of the solution, [c][i]
     for (int i = 0; i < n; ++i) {
-        xacc::clear(a);
-        for (int c = 0; c < q; ++c) xacc::add_value(a, B.c[c][i + j * B.ld]);
-        for (int t = 0; t < i; ++t)
-            for (int c1 = 0; c1 < q; ++c1)
-                for (int c2 = 0; c2 < q; ++c2)
-                    xacc::add_product(a, S[(c1 * NB + t) * NB + i], X[c2 * NB + t], true);
-        bad |= a.range_bad;
-        xacc::round_q(a, q, out);
-        bad |= a.range_bad;
-        for (int c = 0; c < q; ++c) X[c * NB + i] = out[c];
+        double out[Q];
+        xacc::warp_exact_round<W<Q>::NW>(Q, [&](auto& v, int part) {
+            if (part == 0)
+                for (int c = 0; c < Q; ++c) v.value(B.c[c][i + j * B.ld]);
+            for (int t = part; t < i; t += 32)
+                for (int c1 = 0; c1 < Q; ++c1)
+                    for (int c2 = 0; c2 < Q; ++c2) v.product(S[SIDX(c1, i, t)], X[c2 * NB + t], true);
+        }, out, bad);
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < Q; ++c) X[c * NB + i] = out[c];
+        __syncwarp();
     }
-    for (int i = 0; i < n; ++i)
-        for (int c = 0; c < q; ++c) B.c[c][i + j * B.ld] = X[c * NB + i];
-    if (bad) atomicOr(status, ST_RANGE);
+    if (lane < n)
+#pragma unroll
+        for (int c = 0; c < Q; ++c) B.c[c][lane + j * B.ld] = X[c * NB + lane];
+    if (bad && lane == 0) atomicOr(status, ST_RANGE);
 }
 
-// reciprocals of the diagonal of an n x n upper block into S_r[c * NB + j]
-__device__ __forceinline__ void diag_recips(const double* S, int n, int q, double* Sr, bool& bad) {
+// reciprocals of the diagonal of an n x n upper block into Sr[c * NB + j]
+template <int Q>
+__device__ __forceinline__ void diag_recips(const double* S, int n, double* Sr, bool& bad) {
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        double d[QL], r[QL];
-        for (int c = 0; c < q; ++c) d[c] = S[(c * NB + j) * NB + j];
-        if (d[0] == 0.0) { bad = true; for (int c = 0; c < q; ++c) r[c] = 0.0; }
-        else recip_q(d, q, r, bad);
-        for (int c = 0; c < q; ++c) Sr[c * NB + j] = r[c];
+        double d[Q], r[Q];
+#pragma unroll
+        for (int c = 0; c < Q; ++c) d[c] = S[SIDX(c, j, j)];
+        if (d[0] == 0.0) {
+            bad = true;
+#pragma unroll
+            for (int c = 0; c < Q; ++c) r[c] = 0.0;
+        } else {
+            recip_q<Q>(d, r, bad);
+        }
+#pragma unroll
+        for (int c = 0; c < Q; ++c) Sr[c * NB + j] = r[c];
     }
 }
 
-// X U = B, U n x n upper (n <= 32), B h x n: one thread per row,
+// X U = B, U n x n upper (n <= 32), B h x n: one warp per row,
 // x_ij = RN_q(RN_q(b_ij - sum_{t<j} x_it u_tj) * RN_q(1 / u_jj)), in place
-__global__ void __launch_bounds__(128) k_base_trsm_ru(Mat U, Mat B, int n, int64_t h, int q, uint32_t* status) {
-    __shared__ double S[QL * NB * NB];
-    __shared__ double Sr[QL * NB];
-    stage(U, n, q, S);
+template <int Q>
+__global__ void __launch_bounds__(32 * TS_WARPS) k_base_trsm_ru(Mat U, Mat B, int n, int64_t h, uint32_t* status) {
+    __shared__ double S[Q * NB * NB];
+    __shared__ double Sr[Q * NB];
+    __shared__ double Xs[TS_WARPS][Q * NB];
+    stage<Q>(U, n, S);
     __syncthreads();
     bool bad = false;
-    diag_recips(S, n, q, Sr, bad);
+    diag_recips<Q>(S, n, Sr, bad);
     __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < h) {
-        Acc a;
-        double out[QL], num[QL];
-        double X[QL * NB];   // row i of the solution, [c][j]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * TS_WARPS + warp;
+    if (i < h) {   // the whole warp
+        double* X = Xs[warp];
         for (int j = 0; j < n; ++j) {
-            xacc::clear(a);
-            for (int c = 0; c < q; ++c) xacc::add_value(a, B.c[c][i + (int64_t)j * B.ld]);
-            for (int t = 0; t < j; ++t)
-                for (int c1 = 0; c1 < q; ++c1)
-                    for (int c2 = 0; c2 < q; ++c2)
-                        xacc::add_product(a, X[c1 * NB + t], S[(c2 * NB + j) * NB + t], true);
-            bad |= a.range_bad;
-            xacc::round_q(a, q, num);
-            xacc::clear(a);
-            for (int c1 = 0; c1 < q; ++c1)
-                for (int c2 = 0; c2 < q; ++c2) xacc::add_product(a, num[c1], Sr[c2 * NB + j], false);
-            bad |= a.range_bad;
-            xacc::round_q(a, q, out);
-            bad |= a.range_bad;
-            for (int c = 0; c < q; ++c) X[c * NB + j] = out[c];
+            double num[Q], out[Q], rr[Q];
+            xacc::warp_exact_round<W<Q>::NW>(Q, [&](auto& v, int part) {
+                if (part == 0)
+                    for (int c = 0; c < Q; ++c) v.value(B.c[c][i + (int64_t)j * B.ld]);
+                for (int t = part; t < j; t += 32)
+                    for (int c1 = 0; c1 < Q; ++c1)
+                        for (int c2 = 0; c2 < Q; ++c2) v.product(X[c1 * NB + t], S[SIDX(c2, t, j)], true);
+            }, num, bad);
+            if (lane == 0) {
+#pragma unroll
+                for (int c = 0; c < Q; ++c) rr[c] = Sr[c * NB + j];
+                mul_round<Q>(num, rr, out, bad);
+#pragma unroll
+                for (int c = 0; c < Q; ++c) X[c * NB + j] = out[c];
+            }
+            __syncwarp();
         }
-        for (int j = 0; j < n; ++j)
-            for (int c = 0; c < q; ++c) B.c[c][i + (int64_t)j * B.ld] = X[c * NB + j];
+        if (lane < n)
+#pragma unroll
+            for (int c = 0; c < Q; ++c) B.c[c][i + (int64_t)lane * B.ld] = X[c * NB + lane];
     }
     if (bad) atomicOr(status, ST_RANGE);
 }
 
-// U X = B, U n x n upper (n <= 32), B n x w: one thread per column, back
+// U X = B, U n x n upper (n <= 32), B n x w: one warp per column, back
 // substitution x_ij = RN_q(RN_q(b_ij - sum_{t>i} u_it x_tj) * RN_q(1 / u_ii))
-__global__ void __launch_bounds__(128) k_base_trsm_lu(Mat U, Mat B, int n, int64_t w, int q, uint32_t* status) {
-    __shared__ double S[QL * NB * NB];
-    __shared__ double Sr[QL * NB];
-    stage(U, n, q, S);
+template <int Q>
+__global__ void __launch_bounds__(32 * TS_WARPS) k_base_trsm_lu(Mat U, Mat B, int n, int64_t w, uint32_t* status) {
+    __shared__ double S[Q * NB * NB];
+    __shared__ double Sr[Q * NB];
+    __shared__ double Xs[TS_WARPS][Q * NB];
+    stage<Q>(U, n, S);
     __syncthreads();
     bool bad = false;
-    diag_recips(S, n, q, Sr, bad);
+    diag_recips<Q>(S, n, Sr, bad);
     __syncthreads();
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < w) {
-        Acc a;
-        double out[QL], num[QL];
-        double X[QL * NB];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * TS_WARPS + warp;
+    if (j < w) {   // the whole warp
+        double* X = Xs[warp];
         for (int i = n - 1; i >= 0; --i) {
-            xacc::clear(a);
-            for (int c = 0; c < q; ++c) xacc::add_value(a, B.c[c][i + j * B.ld]);
-            for (int t = i + 1; t < n; ++t)
-                for (int c1 = 0; c1 < q; ++c1)
-                    for (int c2 = 0; c2 < q; ++c2)
-                        xacc::add_product(a, S[(c1 * NB + t) * NB + i], X[c2 * NB + t], true);
-            bad |= a.range_bad;
-            xacc::round_q(a, q, num);
-            xacc::clear(a);
-            for (int c1 = 0; c1 < q; ++c1)
-                for (int c2 = 0; c2 < q; ++c2) xacc::add_product(a, num[c1], Sr[c2 * NB + i], false);
-            bad |= a.range_bad;
-            xacc::round_q(a, q, out);
-            bad |= a.range_bad;
-            for (int c = 0; c < q; ++c) X[c * NB + i] = out[c];
+            double num[Q], out[Q], rr[Q];
+            xacc::warp_exact_round<W<Q>::NW>(Q, [&](auto& v, int part) {
+                if (part == 0)
+                    for (int c = 0; c < Q; ++c) v.value(B.c[c][i + j * B.ld]);
+                for (int t = i + 1 + part; t < n; t += 32)
+                    for (int c1 = 0; c1 < Q; ++c1)
+                        for (int c2 = 0; c2 < Q; ++c2) v.product(S[SIDX(c1, i, t)], X[c2 * NB + t], true);
+            }, num, bad);
+            if (lane == 0) {
+#pragma unroll
+                for (int c = 0; c < Q; ++c) rr[c] = Sr[c * NB + i];
+                mul_round<Q>(num, rr, out, bad);
+#pragma unroll
+                for (int c = 0; c < Q; ++c) X[c * NB + i] = out[c];
+            }
+            __syncwarp();
         }
-        for (int i = 0; i < n; ++i)
-            for (int c = 0; c < q; ++c) B.c[c][i + j * B.ld] = X[c * NB + i];
+        if (lane < n)
+#pragma unroll
+            for (int c = 0; c < Q; ++c) B.c[c][lane + j * B.ld] = X[c * NB + lane];
     }
     if (bad) atomicOr(status, ST_RANGE);
 }
 
 // C := RN_q(C - P) elementwise, C m x n (ld C.ld), P m x n (ld P.ld)
-__global__ void __launch_bounds__(256) k_sub(Mat C, Mat P, int64_t m, int64_t n, int q, uint32_t* status) {
+template <int Q>
+__global__ void __launch_bounds__(256) k_sub(Mat C, Mat P, int64_t m, int64_t n, uint32_t* status) {
     const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= m * n) return;
     const int64_t i = x % m, j = x / m;
-    Acc a;
-    xacc::clear(a);
-    for (int c = 0; c < q; ++c) {
-        xacc::add_value(a, C.c[c][i + j * C.ld]);
-        xacc::add_value(a, -P.c[c][i + j * P.ld]);
-    }
-    double out[QL];
-    xacc::round_q(a, q, out);
-    for (int c = 0; c < q; ++c) C.c[c][i + j * C.ld] = out[c];
-    if (a.range_bad) atomicOr(status, ST_RANGE);
+    bool bad = false;
+    double out[Q];
+    xacc::exact_round<W<Q>::NW>(Q, [&](auto& v) {
+        for (int c = 0; c < Q; ++c) {
+            v.value(C.c[c][i + j * C.ld]);
+            v.value(-P.c[c][i + j * P.ld]);
+        }
+    }, out, bad);
+#pragma unroll
+    for (int c = 0; c < Q; ++c) C.c[c][i + j * C.ld] = out[c];
+    if (bad) atomicOr(status, ST_RANGE);
 }
 
 // ---------------------------------------------------------------------------
@@ -323,14 +361,24 @@ static void gemm_sub(Ctx& x, const Mat& C, const Mat& A, const Mat& B, int64_t m
         x.failed = true;
         return;
     }
-    k_sub<<<blocks(m * n, 256), 256, 0, x.st>>>(C, Pm, m, n, x.q, x.status);
+    switch (x.q) {
+        case 2: k_sub<2><<<blocks(m * n, 256), 256, 0, x.st>>>(C, Pm, m, n, x.status); break;
+        case 3: k_sub<3><<<blocks(m * n, 256), 256, 0, x.st>>>(C, Pm, m, n, x.status); break;
+        default: k_sub<4><<<blocks(m * n, 256), 256, 0, x.st>>>(C, Pm, m, n, x.status); break;
+    }
 }
 
 // L X = B (L m x m unit lower, B m x w), in place
 static void trsm_ll(Ctx& x, const Mat& L, const Mat& B, int64_t m, int64_t w) {
     if (x.failed || m == 0 || w == 0) return;
     if (m <= NB) {
-        if (!x.dry) k_base_trsm_ll<<<blocks(w, 128), 128, 0, x.st>>>(L, B, (int)m, w, x.q, x.status);
+        if (!x.dry) {
+            switch (x.q) {
+                case 2: k_base_trsm_ll<2><<<blocks(w, TS_WARPS), 32 * TS_WARPS, 0, x.st>>>(L, B, (int)m, w, x.status); break;
+                case 3: k_base_trsm_ll<3><<<blocks(w, TS_WARPS), 32 * TS_WARPS, 0, x.st>>>(L, B, (int)m, w, x.status); break;
+                default: k_base_trsm_ll<4><<<blocks(w, TS_WARPS), 32 * TS_WARPS, 0, x.st>>>(L, B, (int)m, w, x.status); break;
+            }
+        }
         return;
     }
     const int64_t m1 = half(m);
@@ -343,7 +391,13 @@ static void trsm_ll(Ctx& x, const Mat& L, const Mat& B, int64_t m, int64_t w) {
 static void trsm_ru(Ctx& x, const Mat& U, const Mat& B, int64_t m, int64_t h) {
     if (x.failed || m == 0 || h == 0) return;
     if (m <= NB) {
-        if (!x.dry) k_base_trsm_ru<<<blocks(h, 128), 128, 0, x.st>>>(U, B, (int)m, h, x.q, x.status);
+        if (!x.dry) {
+            switch (x.q) {
+                case 2: k_base_trsm_ru<2><<<blocks(h, TS_WARPS), 32 * TS_WARPS, 0, x.st>>>(U, B, (int)m, h, x.status); break;
+                case 3: k_base_trsm_ru<3><<<blocks(h, TS_WARPS), 32 * TS_WARPS, 0, x.st>>>(U, B, (int)m, h, x.status); break;
+                default: k_base_trsm_ru<4><<<blocks(h, TS_WARPS), 32 * TS_WARPS, 0, x.st>>>(U, B, (int)m, h, x.status); break;
+            }
+        }
         return;
     }
     const int64_t m1 = half(m);
@@ -356,7 +410,13 @@ static void trsm_ru(Ctx& x, const Mat& U, const Mat& B, int64_t m, int64_t h) {
 static void trsm_lu(Ctx& x, const Mat& U, const Mat& B, int64_t m, int64_t w) {
     if (x.failed || m == 0 || w == 0) return;
     if (m <= NB) {
-        if (!x.dry) k_base_trsm_lu<<<blocks(w, 128), 128, 0, x.st>>>(U, B, (int)m, w, x.q, x.status);
+        if (!x.dry) {
+            switch (x.q) {
+                case 2: k_base_trsm_lu<2><<<blocks(w, TS_WARPS), 32 * TS_WARPS, 0, x.st>>>(U, B, (int)m, w, x.status); break;
+                case 3: k_base_trsm_lu<3><<<blocks(w, TS_WARPS), 32 * TS_WARPS, 0, x.st>>>(U, B, (int)m, w, x.status); break;
+                default: k_base_trsm_lu<4><<<blocks(w, TS_WARPS), 32 * TS_WARPS, 0, x.st>>>(U, B, (int)m, w, x.status); break;
+            }
+        }
         return;
     }
     const int64_t m1 = half(m);
@@ -368,7 +428,13 @@ static void trsm_lu(Ctx& x, const Mat& U, const Mat& B, int64_t m, int64_t w) {
 static void lu_rec(Ctx& x, const Mat& A, int64_t n) {
     if (x.failed || n == 0) return;
     if (n <= NB) {
-        if (!x.dry) k_base_lu<<<1, 64, 0, x.st>>>(A, (int)n, x.q, x.status);
+        if (!x.dry) {
+            switch (x.q) {
+                case 2: k_base_lu<2><<<1, 32 * LU_WARPS, 0, x.st>>>(A, (int)n, x.status); break;
+                case 3: k_base_lu<3><<<1, 32 * LU_WARPS, 0, x.st>>>(A, (int)n, x.status); break;
+                default: k_base_lu<4><<<1, 32 * LU_WARPS, 0, x.st>>>(A, (int)n, x.status); break;
+            }
+        }
         return;
     }
     const int64_t n1 = half(n), n2 = n - n1;
