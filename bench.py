@@ -21,7 +21,9 @@ Printed: one JSON line (rank 0).  Besides the contract keys it carries
   variants      -- single timed passes of the other forms/precisions
                    (DD and QD, e4m3 / int8 / binary64 digits) at 4096^3;
   multiprecision_2048 -- 8 and 16 binary64 components (424 / 848 bits)
-                   at 2048^3, e4m3 digits on tcgen05.
+                   at 2048^3, e4m3 digits on tcgen05;
+  lu_4096       -- the LU application: DD n = 4096 and TD n = 2048 LU
+                   without pivoting on Ozaki products, and the solve.
 
 --impl reference times the oracle itself (the CPU reference of this repo)
 on a bounded block per step.
@@ -153,6 +155,40 @@ def run_variant(oz, torch, prec, form, n, phi, steps, warmup, nslices=0):
            "slice_tflops": i.npairs * flops / (sum(gemm_ms) / steps * 1e-3) / 1e12, "status": st.name}
     del p, Ad, Bd, C
     torch.cuda.empty_cache()
+    return out
+
+
+def lu_variant(oz, torch):
+    """The LU application (Sec. 5): in-place LU without pivoting of a random
+    n x n matrix (a_ij = U[0,1), the paper's test matrix) in DD and TD, and
+    the solve of A x = b with b_i = 1 / i; time of the second call (the first
+    creates the product plans), (2/3) n^3 / time."""
+    import numpy as np
+    out = []
+    for q, n in ((2, 4096), (3, 2048)):
+        try:
+            rng = np.random.default_rng(0)
+            A = rng.random((n, n))
+            comps = [np.asfortranarray(A)] + [np.zeros((n, n), order="F") for _ in range(q - 1)]
+            Ad = [oz.colmajor(c) for c in comps]
+            W = [a.clone() for a in Ad]
+            oz.ozmp_lu(W)
+            W = [a.clone() for a in Ad]
+            torch.cuda.synchronize()
+            t0 = time.time()
+            st = oz.ozmp_lu(W)
+            t_lu = time.time() - t0
+            b = [oz.colmajor(np.asfortranarray(1.0 / np.arange(1, n + 1, dtype=np.float64)[:, None]))] + \
+                [torch.zeros((1, n), dtype=torch.float64, device="cuda").T for _ in range(q - 1)]
+            t0 = time.time()
+            st2 = oz.ozmp_lu_solve(W, b)
+            t_s = time.time() - t0
+            out.append({"prec": {2: "dd", 3: "td"}[q], "n": n, "lu_s": t_lu, "gflops": 2 * n ** 3 / 3 / t_lu / 1e9,
+                        "solve_s": t_s, "status": st.name, "solve_status": st2.name})
+            del Ad, W, b
+            torch.cuda.empty_cache()
+        except Exception as ex:
+            out.append({"q": q, "n": n, "error": repr(ex)[:200]})
     return out
 
 
@@ -465,6 +501,7 @@ def main():
             except Exception as ex:
                 md.append({"prec": f"q{q}", "form": "fp8", "error": repr(ex)[:200]})
         line["multiprecision_2048"] = md
+        line["lu_4096"] = lu_variant(oz, torch)
         line["config2_td_qd_1024"] = config2(oz, torch)
         line["config4_batched512"] = config4(oz, torch)
 
