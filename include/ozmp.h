@@ -286,6 +286,26 @@ ozmp_status ozmp_lu(int q, int64_t n, double* const* A, int64_t lda, ozmp_stream
 ozmp_status ozmp_lu_solve(int q, int64_t n, int64_t nrhs, const double* const* LU, int64_t lda,
                           double* const* B, int64_t ldb, ozmp_stream stream);
 
+/*
+ * Algorithm 1 as printed (Sec. 3), kept beside the truncating-digit form for
+ * comparisons of accuracy and slice count: for alpha = 1 .. D-1 the slice
+ * A_alpha = (V_s + tau) - tau in binary64 round-to-nearest, V_s = RN64 of the
+ * exact remainder, tau = 2^(ceil(log2 mu) + ceil((53 + log2 k) / 2)) per row
+ * (per column for B) with mu the largest |V_s| of the row; the last slice is
+ * RN64 of the remainder.  The D (D + 1) / 2 products A_alpha B_beta with
+ * alpha + beta <= D + 1 are binary64 GEMMs (cuBLAS DGEMM, as the paper's GPU
+ * path); they are summed exactly and rounded canonically into C.
+ * q binary64 components (2 <= q <= OZMP_MAX_COMPONENTS), 1 <= D <= 32.
+ * Optional device outputs (NULL: internal): slices_A (D x m x k, slice
+ * alpha at (alpha-1) m k, column-major, ld m), slices_B (D x k x n, ld k),
+ * products (D (D+1)/2 x m x n, ld m, pairs alpha-major).  Synchronous;
+ * returns the device status (NONFINITE, RANGE).  Errors: INVALID_ARG,
+ * NOMEM, CUDA.
+ */
+ozmp_status ozmp_gemm_literal(int q, int D, int64_t m, int64_t n, int64_t k, const double* const* A, int64_t lda,
+                              const double* const* B, int64_t ldb, double* const* C, int64_t ldc,
+                              double* slices_A, double* slices_B, double* products, ozmp_stream stream);
+
 /* Kernel timing (instrumentation; the paper has no counterpart).
  * ozmp_plan_set_timing: with nslots > 0 the plan owns a ring of nslots CUDA
  *   event pairs and, at every ozmp_plan_execute / ozmp_plan_multiply, records

@@ -24,7 +24,7 @@ __all__ = [
     "Status", "Prec", "Form", "OzmpError", "PlanInfo", "Plan", "load", "colmajor",
     "ozmp_plan_create", "ozmp_plan_destroy", "ozmp_plan_get_info", "ozmp_plan_set_workspace",
     "ozmp_plan_set_stream", "ozmp_plan_execute", "ozmp_plan_get_status", "ozmp_plan_split",
-    "ozmp_plan_diagonal", "ozmp_plan_multiply", "ozmp_plan_set_timing", "ozmp_plan_read_timing", "ozmp_gemm_dd", "ozmp_gemm_td", "ozmp_gemm_qd", "ozmp_gemm_ts", "ozmp_gemm_md", "ozmp_lu", "ozmp_lu_solve", "prec_code", "MAX_COMPONENTS", "ozmp_gemm_dd_noalloc", "ozmp_gemm_batched", "Problem", "ozmp_gemm_naive",
+    "ozmp_plan_diagonal", "ozmp_plan_multiply", "ozmp_plan_set_timing", "ozmp_plan_read_timing", "ozmp_gemm_dd", "ozmp_gemm_td", "ozmp_gemm_qd", "ozmp_gemm_ts", "ozmp_gemm_md", "ozmp_lu", "ozmp_lu_solve", "ozmp_gemm_literal", "prec_code", "MAX_COMPONENTS", "ozmp_gemm_dd_noalloc", "ozmp_gemm_batched", "Problem", "ozmp_gemm_naive",
     "ozmp_set_stream", "ozmp_set_form", "ozmp_last_status", "ozmp_version", "gemm", "EXP_ZERO",
 ]
 
@@ -134,6 +134,8 @@ SIGNATURES = {
     "ozmp_gemm_ts": [_I64, _I64, _I64, _PP, _I64, _PP, _I64, _PP, _I64, ctypes.c_int],
     "ozmp_gemm_md": [ctypes.c_int, _I64, _I64, _I64, _PP, _I64, _PP, _I64, _PP, _I64, ctypes.c_int],
     "ozmp_lu": [ctypes.c_int, _I64, _PP, _I64, _VP],
+    "ozmp_gemm_literal": [ctypes.c_int, ctypes.c_int, _I64, _I64, _I64, _PP, _I64, _PP, _I64, _PP, _I64,
+                          _VP, _VP, _VP, _VP],
     "ozmp_lu_solve": [ctypes.c_int, _I64, _I64, _PP, _I64, _PP, _I64, _VP],
     "ozmp_gemm_dd_noalloc": [_I64, _I64, _I64, _PP, _I64, _PP, _I64, _PP, _I64, ctypes.c_int, _VP],
     "ozmp_set_stream": [_VP],
@@ -300,6 +302,24 @@ def ozmp_gemm_qd(A, B, C, nslices=0):
 
 def ozmp_gemm_ts(A, B, C, nslices=0):
     _plain("ozmp_gemm_ts", A, B, C, nslices)
+
+
+def ozmp_gemm_literal(A, B, C, D, slices_A=None, slices_B=None, products=None, stream=None):
+    """Algorithm 1 as printed: binary64 round-to-nearest slices (D of each
+    operand), DGEMM slice products, exact sum rounded into C.  Optional
+    torch outputs: slices_A (D, k, m) / slices_B (D, n, k) / products
+    (D(D+1)/2, n, m) contiguous tensors (each slice column-major)."""
+    m, k = A[0].shape
+    n = B[0].shape[1]
+    pa, ka = _ptrs(A)
+    pb, kb = _ptrs(B)
+    pc, kc = _ptrs(C)
+    vp = lambda t: ctypes.c_void_p(t.data_ptr() if t is not None else 0)
+    st = load().ozmp_gemm_literal(len(A), D, m, n, k, pa, _ld(A[0]), pb, _ld(B[0]), pc, _ld(C[0]),
+                                  vp(slices_A), vp(slices_B), vp(products), _stream_handle(stream))
+    if st in (Status.ERR_INVALID_ARG, Status.ERR_NOMEM, Status.ERR_CUDA, Status.ERR_UNSUPPORTED):
+        _check(st, "ozmp_gemm_literal")
+    return Status(st)
 
 
 def ozmp_lu(A, stream=None):

@@ -30,7 +30,7 @@ __device__ __forceinline__ void clear(Acc& a) {
 }
 
 // add (neg ? -1 : 1) * (hi:lo) * 2^e, hi:lo a 128-bit magnitude
-__device__ __noinline__ void add128(Acc& a, uint64_t hi, uint64_t lo, int e, bool neg) {
+static __device__ __noinline__ void add128(Acc& a, uint64_t hi, uint64_t lo, int e, bool neg) {
     if (hi == 0 && lo == 0) return;
     int sh = e - KL;
     if (sh < 0) {
@@ -89,7 +89,7 @@ __device__ __forceinline__ void add_product(Acc& a, double x, double y, bool neg
 }
 
 // canonical rounding into q binary64 components (the accumulator is used up)
-__device__ __noinline__ void round_q(Acc& a, int q, double* out) {
+static __device__ __noinline__ void round_q(Acc& a, int q, double* out) {
     int sgn = 1;
     if (a.w[KW - 1] >> 63) {
         // negate in place
