@@ -23,7 +23,9 @@ Printed: one JSON line (rank 0).  Besides the contract keys it carries
   multiprecision_2048 -- 8 and 16 binary64 components (424 / 848 bits)
                    at 2048^3, e4m3 digits on tcgen05;
   lu_4096       -- the LU application: DD n = 4096 and TD n = 2048 LU
-                   without pivoting on Ozaki products, and the solve.
+                   without pivoting on Ozaki products, and the solve;
+  literal_vs_truncating_1024 -- Algorithm 1 as printed against the
+                   truncating binary64-digit form, error and time per D.
 
 --impl reference times the oracle itself (the CPU reference of this repo)
 on a bounded block per step.
@@ -155,6 +157,54 @@ def run_variant(oz, torch, prec, form, n, phi, steps, warmup, nslices=0):
            "slice_tflops": i.npairs * flops / (sum(gemm_ms) / steps * 1e-3) / 1e12, "status": st.name}
     del p, Ad, Bd, C
     torch.cuda.empty_cache()
+    return out
+
+
+def literal_variant(oz, torch, n=1024):
+    """Accuracy and time against the division count D: Algorithm 1 as printed
+    (binary64 round-to-nearest slices, DGEMM products) and the truncating
+    binary64-digit form with s = D, both against the e4m3 form at its
+    automatic slice count (error near 2^-106) as the reference; DD, n^3,
+    phi = 1.  err = ||C_D - C_ref||_F / ||C_ref||_F over the whole C."""
+    import numpy as np
+    A, B = _host_operands("dd", n, n, n, 1.0, 0)
+    Ad = [oz.colmajor(a) for a in A]
+    Bd = [oz.colmajor(b) for b in B]
+    ref, _ = oz.gemm(Ad, Bd, "dd", "fp8", 0)
+    R = [t.cpu().numpy() for t in ref]
+    rn = float(np.sqrt(np.sum(R[0] ** 2)))
+
+    def err(C):
+        Cn = [t.cpu().numpy() for t in C]
+        d = (Cn[0] - R[0]) + (Cn[1] - R[1])
+        return float(np.sqrt(np.sum(d ** 2))) / rn
+
+    out = []
+    for D in (3, 4, 5, 6, 7, 8):
+        row = {"D": D}
+        try:
+            C = [torch.empty((n, n), dtype=torch.float64, device="cuda").T for _ in range(2)]
+            oz.ozmp_gemm_literal(Ad, Bd, C, D)
+            t0 = time.time()
+            st = oz.ozmp_gemm_literal(Ad, Bd, C, D)
+            row["literal_ms"] = (time.time() - t0) * 1e3
+            row["literal_err"] = err(C)
+            row["literal_status"] = st.name
+            p = oz.Plan("dd", n, n, n, "fp64", D)
+            C2 = [torch.empty((n, n), dtype=torch.float64, device="cuda").T for _ in range(2)]
+            p.execute(Ad, Bd, C2)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            p.execute(Ad, Bd, C2)
+            e1.record()
+            torch.cuda.synchronize()
+            row["truncating_fp64_ms"] = e0.elapsed_time(e1)
+            row["truncating_fp64_err"] = err(C2)
+            del p
+        except Exception as ex:
+            row["error"] = repr(ex)[:200]
+        out.append(row)
     return out
 
 
@@ -502,6 +552,7 @@ def main():
                 md.append({"prec": f"q{q}", "form": "fp8", "error": repr(ex)[:200]})
         line["multiprecision_2048"] = md
         line["lu_4096"] = lu_variant(oz, torch)
+        line["literal_vs_truncating_1024"] = literal_variant(oz, torch)
         line["config2_td_qd_1024"] = config2(oz, torch)
         line["config4_batched512"] = config4(oz, torch)
 
