@@ -549,6 +549,8 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
                     sc.ntiles = 0;
                     sc.counter = nullptr;
                     sc.nitems = 0;
+                    sc.wait_limit = 0;
+                    sc.inject_stall = 0;
                     tc::Prob dummy;
                     memset(&dummy, 0, sizeof(dummy));
                     CUtensorMap m0;

@@ -39,6 +39,8 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = CG == 2 ? cluster_rank() : 0u;
+    const long long WL = sc.wait_limit > 0 ? sc.wait_limit : WAIT_LIMIT;   // polls before a wait gives up
+    const long long DL = WL < DRAIN_LIMIT ? WL : DRAIN_LIMIT;               // ... for work already in flight
     const int cid = CG == 2 ? (int)cluster_id_x() : (int)blockIdx.x;
     const int ncl = CG == 2 ? (int)cluster_count_x() : (int)gridDim.x;
     // the leader's full and acc-empty barriers, and the peer's abort flag
@@ -67,7 +69,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
         const int r = k % RING;
         const unsigned ph = (unsigned)((k / RING) & 1);
         if (publisher) {
-            if (!mbar_wait<CG == 2>(&ring_empty[r], ph ^ 1u, abort_flag)) return -2;
+            if (!mbar_wait<CG == 2>(&ring_empty[r], ph ^ 1u, abort_flag, WL)) return -2;
             const int idx = atomicAdd(sc.counter, 1);
             ring[r] = idx;
             if (CG == 2) {
@@ -81,7 +83,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
         // cannot part on a timeout
         int idx = -2;
         if (!warp_wide || lane == 0) {
-            if (mbar_wait<CG == 2>(&ring_full[r], ph, abort_flag)) {
+            if (mbar_wait<CG == 2>(&ring_full[r], ph, abort_flag, WL)) {
                 idx = ring[r];
                 if (CG == 2) mbar_arrive_cluster(ring_empty_cl + 8u * r);
                 else mbar_arrive(&ring_empty[r]);
@@ -142,7 +144,10 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                     for (int kc = 0; kc < it.KT; ++kc, ++n) {
                         const int st = (int)(n % NS);
                         const unsigned ph = (unsigned)((n / NS) & 1);
-                        if (!mbar_wait<CG == 2>(&empty[st], ph ^ 1u, abort_flag)) { ok = false; break; }
+                        if (!mbar_wait<CG == 2>(&empty[st], ph ^ 1u, abort_flag, WL)) { ok = false; break; }
+                        // test hook: the first stage of this CTA's first item is never loaded
+                        // (its full barrier is never completed), so the waits on it run out
+                        if (sc.inject_stall && k == 0 && pi == it.pa && kc == 0) continue;
                         if (rank == 0) mbar_expect_tx(&full[st], tx);
                         if (CG == 2) {
                             tma_load_2d_pair(sA + (size_t)st * STAGE_A, it.ma, full_cl + 8u * st, kc * BK, ya);
@@ -162,7 +167,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                 if (rank == 0) {
                     volatile int never = 0;
                     for (long long q = n - 1; q >= 0 && q >= n - NS; --q)
-                        mbar_wait<CG == 2>(&full[(int)(q % NS)], (unsigned)((q / NS) & 1), &never, DRAIN_LIMIT);
+                        mbar_wait<CG == 2>(&full[(int)(q % NS)], (unsigned)((q / NS) & 1), &never, DL);
                 }
             }
         }
@@ -171,7 +176,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
         if (lane == 0 && rank == 0) {
             long long n = 0;
             int buf = 0, uses[2] = {0, 0};
-            bool ok = mbar_wait<CG == 2>(&acce[0], 1u, abort_flag);     // first use of buffer 0
+            bool ok = mbar_wait<CG == 2>(&acce[0], 1u, abort_flag, WL);     // first use of buffer 0
             for (int k = 0; ok; ++k) {
                 const int idx = take(k, false, false);
                 if (idx == -2) { ok = false; break; }
@@ -188,7 +193,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                     for (int kc = 0; kc < it.KT; ++kc, ++n) {
                         const int st = (int)(n % NS);
                         const unsigned ph = (unsigned)((n / NS) & 1);
-                        if (!mbar_wait<CG == 2>(&full[st], ph, abort_flag)) { ok = false; break; }
+                        if (!mbar_wait<CG == 2>(&full[st], ph, abort_flag, WL)) { ok = false; break; }
                         tc_fence_after();
                         const uint64_t ad = desc_sw128(saddr(sA + (size_t)st * STAGE_A));
                         const uint64_t bd = desc_sw128(saddr(sB + (size_t)st * SB));
@@ -215,7 +220,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                         since = 0;
                         fresh = true;
                         // the k-th use of a buffer waits for the epilogues' (k-1)-th release
-                        if (!mbar_wait<CG == 2>(&acce[buf], (unsigned)((uses[buf] & 1) ^ 1), abort_flag)) {
+                        if (!mbar_wait<CG == 2>(&acce[buf], (unsigned)((uses[buf] & 1) ^ 1), abort_flag, WL)) {
                             ok = false;
                             break;
                         }
@@ -229,7 +234,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
             if (CG == 2) mma_commit_local_pair(done);
             else mma_commit(done);
             volatile int never = 0;
-            mbar_wait<CG == 2>(done, 0u, &never, DRAIN_LIMIT);
+            mbar_wait<CG == 2>(done, 0u, &never, DL);
         }
     } else {
         // ------------------------------------------------------------ epilogue
@@ -268,7 +273,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                     const unsigned par = (unsigned)((ev >> 1) & 1);
                     ++ev;
                     int got = 0;
-                    if (lane == 0) got = mbar_wait<CG == 2>(&accf[buf], par, abort_flag) ? 1 : 0;
+                    if (lane == 0) got = mbar_wait<CG == 2>(&accf[buf], par, abort_flag, WL) ? 1 : 0;
                     if (!__shfl_sync(0xffffffffu, got, 0)) { ok = false; break; }
                     __syncwarp();
                     tc_fence_after();
@@ -544,6 +549,8 @@ cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t st) {
     sc.ntiles = (int)((g.mp / (tc::BM * cg)) * (g.np / tc::BN));
     sc.counter = sc.items ? g.counter : nullptr;
     sc.nitems = g.sched_nitems;
+    sc.wait_limit = g.wait_limit;
+    sc.inject_stall = g.inject_stall;
     if (sc.items && g.split_bytes) {
         // split limbs, chunk counters and the feed counter are one region
         e = cudaMemsetAsync(g.sacc ? (void*)g.sacc : (void*)g.cnt_region, 0, g.split_bytes, st);

@@ -330,6 +330,8 @@ struct Sched {
     int ntiles;                // no item list: tiles of the one problem
     int* counter;              // non-null: items are taken in list order from this counter
     int nitems;                //   (zeroed before the launch) instead of the per-CTA lists
+    long long wait_limit;      // polls before a wait gives up (0: WAIT_LIMIT)
+    int inject_stall;          // test hook: never load the first stage of each CTA's first item
 };
 
 // Dynamic item feed: the leader's producer takes the next item index from the

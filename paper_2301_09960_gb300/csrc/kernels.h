@@ -54,6 +54,8 @@ struct GemmArgs {
     int* cnt_region;           // start of the counters (cnt, then the feed counter)
     const int* tile_slot;      // per tile of the schedule: its split-limb slot, or -1 (whole tile)
     cudaEvent_t tev_start, tev_stop;   // recorded around the product kernel when non-null
+    long long wait_limit;      // tcgen05 form: polls before a wait gives up (0: the default)
+    int inject_stall;          // tcgen05 form, test hook: a stage that is never loaded
     int sched_nitems;
     size_t split_bytes;        // bytes of sacc + cnt + counter
     int tc_cg;                 // 2: CTA-pair tiles (256 x 256, cta_group::2); else one CTA per tile

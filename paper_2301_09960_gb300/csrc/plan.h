@@ -29,6 +29,9 @@ struct ozmp_plan_s {
     int tc_cg;                                   // 2: the schedule is over CTA-pair tiles
     int tc_dyn;                                  // items taken from a counter (else per-CTA lists)
     int big;                                     // the many-component splitter (q > 4 or wide windows)
+    // tcgen05 form, for tests of the bounded waits (OZMP_TC_WAIT_LIMIT, OZMP_TC_INJECT_STALL)
+    long long tc_wait_limit;
+    int tc_inject_stall;
     // kernel timing ring (ozmp_plan_set_timing): tev[2 x] / tev[2 x + 1] around call x mod tev_n
     cudaEvent_t* tev;
     int tev_n;
@@ -229,6 +232,8 @@ inline GemmArgs gemm_args(ozmp_plan_s* p) {
         g.split_bytes = p->split_bytes;
         g.tc_cg = p->tc_cg;
     }
+    g.wait_limit = p->tc_wait_limit;
+    g.inject_stall = p->tc_inject_stall;
     return g;
 }
 
@@ -260,6 +265,12 @@ inline ozmp_status plan_schedule(ozmp_plan_s* p) {
     if (!p->sched_host) return OZMP_ERR_NOMEM;
     int* items = p->sched_host;
     int* off = p->sched_host + (size_t)6 * ntiles * 8;
+    // test hooks of the bounded waits: a smaller poll limit, and a stage whose
+    // copies are never issued so that the waits on it run out
+    const char* wl = getenv("OZMP_TC_WAIT_LIMIT");
+    p->tc_wait_limit = wl ? atoll(wl) : 0;
+    const char* inj = getenv("OZMP_TC_INJECT_STALL");
+    p->tc_inject_stall = (inj && inj[0] == '1') ? 1 : 0;
     const char* dyn = getenv("OZMP_TC_DYNAMIC");
     p->tc_dyn = !(dyn && dyn[0] == '0');
     p->sched_grid = tc_schedule(ntiles, pairs, sms, items, off, &p->sched_items, &p->sched_slots, !p->tc_dyn);
