@@ -111,11 +111,28 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# ranks: one replica per GPU, each with its own problem (no data-path
+# collective); the time of the job is the slowest rank's
+# ---------------------------------------------------------------------------
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def _rank_seed(rank: int) -> int:
+    """Seed of a rank's operands (rank 0: the single-GPU workload)."""
+    return 1000 * rank
+
+
+def _max_over_ranks(x: float, device) -> float:
+    """Largest x over the ranks of the default process group."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def _host_operands(prec, m, n, k, phi, seed):
@@ -376,7 +393,7 @@ def main():
 
     m = n = k = args.n
     prec, form = args.prec, args.form
-    A, B = _host_operands(prec, m, n, k, args.phi, 1000 * rank)
+    A, B = _host_operands(prec, m, n, k, args.phi, _rank_seed(rank))
     q = len(A)
     dt = torch.float32 if prec == "ts" else torch.float64
     w = 4 if prec == "ts" else 8
@@ -419,9 +436,7 @@ def main():
     gemm_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / args.steps
     status = plan.status()
     if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = _max_over_ranks(total_ms, "cuda")
     ms_per_step = total_ms / args.steps
     flops = 2.0 * m * n * k
     value = ws * flops / (ms_per_step * 1e-3) / 1e9
