@@ -141,7 +141,9 @@ def test_zero_rows_unnormalised_and_slow_path():
     hi[2] = [2.0 ** -1000, 1.0, 0.0, 0.0]
     hi[3] = [1.0, 1.0, 1.0, 1.0]
     lo[3] = [-1.0, 0.0, 0.0, 2.0 ** -53]                           # complete cancellation
-    # row 1 and 4, 5 are zero
+    hi[4] = [2.0 ** 60, -(2.0 ** 200), 3.0, 0.0]
+    lo[4] = [-(2.0 ** 60 - 1.0), 2.0 ** 200 - 2.0 ** 148, -(2.0 ** 55), 0.0]   # components far above the value
+    # rows 1 and 5 are zero
     A = [np.asfortranarray(hi), np.asfortranarray(lo)]
     rng = np.random.default_rng(0)
     B = [np.asfortranarray(rng.standard_normal((k, n))), np.zeros((k, n), order="F")]
