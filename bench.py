@@ -523,8 +523,11 @@ def main():
     line = {
         "metric": metric, "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "e4m3 digits / f32 acc" if info.form in (oz.Form.FP8, oz.Form.FP8_MMA) else
-        ("s8 digits / s32 acc" if info.form == oz.Form.INT8 else "f64 digits / f64 acc"),
+        "vs_baseline": None, "dtype": "e4m3" if info.form in (oz.Form.FP8, oz.Form.FP8_MMA) else
+        ("s8" if info.form == oz.Form.INT8 else "f64"),
+        "acc_dtype": "f32 (integers below 2^24, exact) -> int64 carry-save limbs" if info.form == oz.Form.FP8 else
+        ("f32 (exact integers) -> int64" if info.form == oz.Form.FP8_MMA else
+         ("s32 -> int64" if info.form == oz.Form.INT8 else "f64 (exact integers) -> int64")),
         "data": "synthetic (Eq. 1, seeded)",
         "config": {"workload": workload, "prec": prec, "form": oz.Form(info.form).name.lower(), "m": m, "n": n,
                    "k": k, "phi": args.phi, "beta": info.beta, "nslices": info.nslices, "pairs": info.npairs,
