@@ -215,7 +215,9 @@ ozmp_status ozmp_gemm_dd_noalloc(int64_t m, int64_t n, int64_t k, const double* 
  *   between calls.  Destroy with ozmp_plan_destroy; status with
  *   ozmp_plan_get_status (one word for the whole batch).
  * The problem array and the component-pointer arrays it points to are read
- * during the call only.
+ * during the call only.  Batched problems hold at most 4 components and
+ * beta * nslices <= 376 bits (else OZMP_ERR_UNSUPPORTED); larger ones go
+ * through single-problem plans.
  */
 typedef struct {
     ozmp_prec prec;

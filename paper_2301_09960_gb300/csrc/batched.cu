@@ -254,6 +254,7 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
         int q = prec_q(r.prec);
         if (!q || r.m < 0 || r.n < 0 || r.k < 0 || r.nslices < 0 || r.nslices > OZMP_MAX_SLICES)
             return OZMP_ERR_INVALID_ARG;
+        if (q > 4) return OZMP_ERR_UNSUPPORTED;   // the batched kernels hold at most 4 components
         if (r.lda < (r.m > 1 ? r.m : 1) || r.ldb < (r.k > 1 ? r.k : 1) || r.ldc < (r.m > 1 ? r.m : 1))
             return OZMP_ERR_INVALID_ARG;
         if (r.m > 0 && r.n > 0) {
@@ -288,6 +289,7 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
             const ozmp_problem& r = probs[i];
             ozmp_plan_s& s = b->subs[i];
             ozmp_status e = plan_init(&s, r.prec, r.m, r.n, r.k, fm, r.nslices, stream);
+            if (e == OZMP_OK && s.big) e = OZMP_ERR_UNSUPPORTED;   // windows wider than the batched splitter's
             if (e != OZMP_OK) { destroy_batch(b); return e; }
             b->q[i] = s.q;
             if (fm == OZMP_FORM_FP8) {

@@ -76,3 +76,15 @@ def test_batched_plan_rejects_a_different_batch():
         oz.ozmp_gemm_batched(other, plan=plan)
     assert e.value.status == oz.Status.ERR_INVALID_ARG
     oz.ozmp_plan_destroy(plan)
+
+
+def test_batched_rejects_more_than_four_components_and_wide_windows():
+    probs = _make([(40, 30, 20, "q5")], 3)
+    with pytest.raises(oz.OzmpError) as e:
+        oz.ozmp_gemm_batched(probs)
+    assert e.value.status == oz.Status.ERR_UNSUPPORTED
+    probs = _make([(40, 30, 20, "dd")], 3)
+    probs = [(p[0], p[1], p[2], p[3], 120) for p in probs]     # beta s = 480 bits
+    with pytest.raises(oz.OzmpError) as e:
+        oz.ozmp_gemm_batched(probs)
+    assert e.value.status == oz.Status.ERR_UNSUPPORTED
