@@ -109,6 +109,21 @@ __global__ void __launch_bounds__(256) k_b_split_cols(const BSplit* P, const int
 
 }  // namespace ozmp
 
+// Rounding pass of the batched products: block b belongs to problem
+// ids[x], x the last with pre[x] <= b; one thread per element of its C
+// normalises the element's limbs and rounds them into the q components.
+__global__ void __launch_bounds__(256) k_b_finish(const tc::Prob* probs, const int* ids, const int* pre, int count,
+                                                  uint32_t* status) {
+    const int x = find_prob(pre, count, blockIdx.x);
+    const tc::Prob& P = probs[ids[x]];
+    const int64_t e = (int64_t)(blockIdx.x - pre[x]) * blockDim.x + threadIdx.x;
+    if (e >= P.m * P.n) return;
+    const int64_t i = e % P.m, j = e / P.m;
+    const GemmArgs g = tc::as_gemm_args(P, status);
+    const int nl = (P.beta * (P.s - 1)) / 16 + 1;   // limbs 0 .. the last drain's
+    tc::finish_dispatch(g, nl, P.acc, (size_t)P.mp * P.np, (size_t)j * P.mp + i, i, j, 0, 0, false);
+}
+
 // ----------------------------------------------------------------------------
 // host: batched plan
 // ----------------------------------------------------------------------------
@@ -137,6 +152,8 @@ struct Batch {
     void* pinned = nullptr;        // host mirror of the pointer-carrying descriptors
     size_t pinned_bytes = 0;
     size_t off_probs = 0, off_maps = 0, off_items = 0, off_cta = 0, off_status = 0;
+    size_t off_fids = 0, off_fpre = 0;   // rounding pass: problem ids and their block prefixes
+    int fin_count = 0, fin_blocks = 0;   // (0 blocks: the product kernel rounds in place)
     int grid = 0;
     std::vector<int> q;
     cudaGraphExec_t gexec = nullptr;
@@ -369,6 +386,24 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
         b->off_maps = mo; mo = a256(mo + sizeof(CUtensorMap) * 2 * count);
         b->off_items = mo; mo = a256(mo + sizeof(tc::WorkItem) * (items.size() + 1));
         b->off_cta = mo; mo = a256(mo + sizeof(int) * (cta_off.size() + 1));
+        // the rounding pass over the limbs runs after the product launch (unless
+        // OZMP_BATCH_DEFER=0 keeps the rounding inside the product kernel)
+        std::vector<int> fids, fpre(1, 0);
+        {
+            const char* env = getenv("OZMP_BATCH_DEFER");
+            const bool defer = !(env && env[0] == '0');
+            if (fm == OZMP_FORM_FP8 && defer)
+                for (int i = 0; i < count; ++i) {
+                    const ozmp_plan_s& sx = b->subs[i];
+                    if (sx.m == 0 || sx.n == 0 || sx.k == 0) continue;
+                    fids.push_back(i);
+                    fpre.push_back(fpre.back() + (int)((sx.m * sx.n + 255) / 256));
+                }
+        }
+        b->fin_count = (int)fids.size();
+        b->fin_blocks = fpre.back();
+        b->off_fids = mo; mo = a256(mo + sizeof(int) * (fids.size() + 1));
+        b->off_fpre = mo; mo = a256(mo + sizeof(int) * fpre.size());
         b->off_status = mo; mo = a256(mo + 16);
         b->meta_bytes = mo;
         if (cudaMalloc(&b->meta, b->meta_bytes) != cudaSuccess) {
@@ -417,6 +452,8 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
         }
         memcpy(host.data() + (b->off_items - b->off_maps), items.data(), sizeof(tc::WorkItem) * items.size());
         memcpy(host.data() + (b->off_cta - b->off_maps), cta_off.data(), sizeof(int) * cta_off.size());
+        if (!fids.empty()) memcpy(host.data() + (b->off_fids - b->off_maps), fids.data(), sizeof(int) * fids.size());
+        memcpy(host.data() + (b->off_fpre - b->off_maps), fpre.data(), sizeof(int) * fpre.size());
         if (cudaMemcpy((char*)b->meta + b->off_maps, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
             destroy_batch(b);
             return OZMP_ERR_CUDA;
@@ -465,6 +502,7 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
         p.m = s.m; p.n = s.n; p.mp = s.mp; p.np = s.np; p.kp = s.kp; p.ldc = r.ldc;
         p.q = s.q; p.is_f32 = s.is_f32; p.s = s.s; p.beta = s.beta; p.ppd = s.ppd; p.acc_words = s.acc_words;
         p.bn = b->bn[i];
+        p.defer = b->fin_blocks > 0 ? 1 : 0;
     }
 
     // ---------------------------------------------------------------- graph
@@ -559,6 +597,10 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
                     memset(&m0, 0, sizeof(m0));
                     tc_launch(sc, dummy, m0, m0, status, b->grid, cs);
                 }
+                if (b->fin_blocks > 0)
+                    k_b_finish<<<b->fin_blocks, 256, 0, cs>>>(
+                        (const tc::Prob*)((char*)b->meta + b->off_probs), (const int*)((char*)b->meta + b->off_fids),
+                        (const int*)((char*)b->meta + b->off_fpre), b->fin_count, status);
             } else {
                 // other forms: the problems one after another inside the graph
                 for (int i = 0; i < count; ++i) {

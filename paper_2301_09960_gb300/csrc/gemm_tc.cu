@@ -428,8 +428,21 @@ bool tc_make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t kp, u
     return r == CUDA_SUCCESS;
 }
 
-int tc_schedule(int ntiles, int pairs, int sms, int* items, int* off, int* nitems, int* nslots, bool regroup) {
+int tc_schedule(int ntiles, int pairs, int sms, int* items, int* off, int* nitems, int* nslots, bool regroup,
+                int tm, int group) {
     if (sms < 1) sms = 1;
+    // tile order: bands of `group` row tiles, column by column within a band
+    // (group <= 0: plain column-major order of the tiles)
+    std::vector<int> order(ntiles);
+    if (group > 0 && tm > 0 && ntiles % tm == 0) {
+        const int tn = ntiles / tm;
+        int x = 0;
+        for (int i0 = 0; i0 < tm; i0 += group)
+            for (int j = 0; j < tn; ++j)
+                for (int i = i0; i < i0 + group && i < tm; ++i) order[x++] = i + tm * j;
+    } else {
+        for (int t = 0; t < ntiles; ++t) order[t] = t;
+    }
     const int waves = ntiles / sms, r = ntiles % sms;
     // chunks per tail tile: minimise waves + ceil(r c / sms) / c (+ a small per-chunk cost)
     int best_c = 1;
@@ -448,14 +461,14 @@ int tc_schedule(int ntiles, int pairs, int sms, int* items, int* off, int* nitem
         w[0] = 0; w[1] = tile; w[2] = pa; w[3] = pb; w[4] = slot; w[5] = nch;
         per[cta].push_back(n++);
     };
-    for (int t = 0; t < waves * sms; ++t) put(t % sms, t, 0, pairs, -1, 1);
+    for (int t = 0; t < waves * sms; ++t) put(t % sms, order[t], 0, pairs, -1, 1);
     int next = 0;
     for (int t = waves * sms; t < ntiles; ++t) {
-        if (c == 1) { put(next, t, 0, pairs, -1, 1); next = (next + 1) % grid; continue; }
+        if (c == 1) { put(next, order[t], 0, pairs, -1, 1); next = (next + 1) % grid; continue; }
         const int slot = slots++;
         for (int x = 0; x < c; ++x) {
             const int pa = (int)((int64_t)pairs * x / c), pb = (int)((int64_t)pairs * (x + 1) / c);
-            put(next, t, pa, pb, slot, c);
+            put(next, order[t], pa, pb, slot, c);
             next = (next + 1) % grid;
         }
     }

@@ -66,7 +66,9 @@ struct GemmArgs {
 // tiles than CTAs) split into pair-range chunks.  Writes items (6 ints each:
 // prob, tile, pa, pb, slot, nchunks), regrouped per CTA with CTA offsets when
 // `regroup` (else in creation order for the dynamic feed); returns the grid.
-int tc_schedule(int ntiles, int pairs, int sms, int* items, int* off, int* nitems, int* nslots, bool regroup);
+// Tiles are taken in bands of `group` of the tm row tiles (0: column-major).
+int tc_schedule(int ntiles, int pairs, int sms, int* items, int* off, int* nitems, int* nslots, bool regroup,
+                int tm, int group);
 int tc_num_sms();
 int tc_num_pair_slots();   // co-resident clusters of two CTAs of the tcgen05 pair form
 

@@ -273,7 +273,10 @@ inline ozmp_status plan_schedule(ozmp_plan_s* p) {
     p->tc_inject_stall = (inj && inj[0] == '1') ? 1 : 0;
     const char* dyn = getenv("OZMP_TC_DYNAMIC");
     p->tc_dyn = !(dyn && dyn[0] == '0');
-    p->sched_grid = tc_schedule(ntiles, pairs, sms, items, off, &p->sched_items, &p->sched_slots, !p->tc_dyn);
+    const char* grp = getenv("OZMP_TC_GROUP");
+    const int tm = (int)(p->mp / (128 * p->tc_cg));
+    p->sched_grid = tc_schedule(ntiles, pairs, sms, items, off, &p->sched_items, &p->sched_slots, !p->tc_dyn, tm,
+                                grp ? atoi(grp) : 0);
     p->sched_slots *= p->tc_cg;
     // CTA offsets right after the items in the host copy
     int* off2 = items + 6 * p->sched_items;
