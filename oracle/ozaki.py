@@ -15,6 +15,9 @@ Two splits are provided.
   x.  Hence x = sum_t d_t 2^(E_i - beta*t) + r exactly, |d_t| <= 2^beta - 1,
   |r| < 2^(E_i - beta*s).  The digits are found here from one exact big
   integer per element (a different algorithm from the library's).
+* ``split_balanced`` -- the same truncated value written in balanced
+  radix-32 digits (|d| <= 16, all exact in e4m3), found from the least
+  significant end by residues in [-16, 15].
 * ``paper_literal`` -- Algorithm 1 as printed: round-to-nearest extraction
   (A + S_A) - S_A in binary64, an exact (L-bit) residual update, and the
   last slice taken as the rounded remainder.
@@ -58,6 +61,7 @@ def beta_fp32(k: int) -> int:
 
 BETA_INT8 = 7   # |d| <= 127: an int8 digit
 BETA_FP8 = 4    # |d| <= 15: exactly representable in e4m3
+BETA_BAL = 5    # balanced radix-32 digits, |d| <= 16: exactly representable in e4m3
 
 
 def pairs(D: int):
@@ -100,8 +104,54 @@ def split(comps, beta: int, s: int):
     return E, dig
 
 
-def split_remainder(comps, E, dig, beta: int):
-    """Exact remainders r = x - sum_t d_t 2^(E - beta t), as dyadics."""
+def split_balanced(comps, s: int):
+    """Balanced radix-32 digits of the truncated value (the e4m3 form with
+    beta = 5).
+
+    Row exponents E_i as in ``split``.  The magnitude is truncated at
+    2^(E_i + 1 - 5 s): N = floor(|x| 2^(5 s - 1 - E_i)), an integer below
+    2^(5 s - 1).  Its digits are peeled off from the least significant end:
+    d_s is the residue of N modulo 32 taken in [-16, 15], N := (N - d_s) / 32,
+    and so on down to d_2; what is left is the top digit d_1, in [0, 16].
+    Every digit then takes the sign of x, so
+    x = sum_t d_t 2^(E_i + 1 - 5 t) + r with |d_t| <= 16,
+    |r| < 2^(E_i + 1 - 5 s) and r of the sign of x (truncation toward zero):
+    the same truncated value as ``split`` with beta = 1 and 5 s - 1 slices,
+    written with a third fewer slices than beta = 4 needs for it.
+    Returns (E, digits) shaped as ``split``'s.
+    """
+    r, k = comps[0].shape
+    vals = X.matrix_values(comps)
+    E = []
+    for i in range(r):
+        E.append(max(X.exponent(v) for v in vals[i]) if k else EXP_ZERO)
+    dig = np.zeros((s, r, k), dtype=np.int64)
+    for i in range(r):
+        Ei = E[i]
+        if Ei == EXP_ZERO:
+            continue
+        for p in range(k):
+            n, e = vals[i][p]
+            if n == 0:
+                continue
+            sh = e + 5 * s - 1 - Ei
+            a = abs(n)
+            N = a << sh if sh >= 0 else a >> (-sh)
+            sg = 1 if n > 0 else -1
+            for t in range(s, 1, -1):
+                d = N % 32
+                if d >= 16:
+                    d -= 32
+                dig[t - 1, i, p] = sg * d
+                N = (N - d) // 32
+            assert 0 <= N <= 16
+            dig[0, i, p] = sg * N
+    return E, dig
+
+
+def split_remainder(comps, E, dig, beta: int, eoff: int = 0):
+    """Exact remainders r = x - sum_t d_t 2^(E + eoff - beta t), as dyadics
+    (eoff = 1 for the balanced digits of ``split_balanced``)."""
     r, k = comps[0].shape
     s = dig.shape[0]
     vals = X.matrix_values(comps)
@@ -114,7 +164,7 @@ def split_remainder(comps, E, dig, beta: int):
                 for t in range(1, s + 1):
                     d = int(dig[t - 1, i, p])
                     if d:
-                        acc = X.add(acc, (-d, E[i] - beta * t))
+                        acc = X.add(acc, (-d, E[i] + eoff - beta * t))
             row.append(acc)
         out.append(row)
     return out
@@ -142,9 +192,10 @@ def slice_products(Ad, Bd):
     return T
 
 
-def ozaki_sum(E, F, T, beta: int, s: int):
-    """Exact S_ij = sum_{d=2}^{s+1} 2^(E_i + F_j - beta d) T_d(i, j)
-    (Algorithm 1's final loop, summed without rounding)."""
+def ozaki_sum(E, F, T, beta: int, s: int, eoff: int = 0):
+    """Exact S_ij = sum_{d=2}^{s+1} 2^(E_i + F_j + eoff - beta d) T_d(i, j)
+    (Algorithm 1's final loop, summed without rounding; eoff = 2 for two
+    operands in balanced digits)."""
     m, n = T[2].shape
     out = []
     for i in range(m):
@@ -156,22 +207,28 @@ def ozaki_sum(E, F, T, beta: int, s: int):
             N = 0
             for d in range(2, s + 2):
                 N += int(T[d][i, j]) << (beta * (s + 1 - d))
-            row.append((N, E[i] + F[j] - beta * (s + 1)) if N else (0, 0))
+            row.append((N, E[i] + F[j] + eoff - beta * (s + 1)) if N else (0, 0))
         out.append(row)
     return out
 
 
-def ozaki_product(A, B, beta: int, s: int):
-    """The whole CPU Ozaki product with exact truncating digits.
+def ozaki_product(A, B, beta: int, s: int, balanced: bool = False):
+    """The whole CPU Ozaki product with exact truncating digits (balanced
+    radix-32 digits of the truncated values when ``balanced``; beta is then 5).
 
     A: list of m x k component arrays; B: list of k x n component arrays.
     Returns a dict with E, F, digits, T and the exact Ozaki sum S.
     """
-    E, Ad = split(A, beta, s)
     Bt = [np.asfortranarray(b.T) for b in B]
-    F, Bd = split(Bt, beta, s)
+    if balanced:
+        assert beta == BETA_BAL
+        E, Ad = split_balanced(A, s)
+        F, Bd = split_balanced(Bt, s)
+    else:
+        E, Ad = split(A, beta, s)
+        F, Bd = split(Bt, beta, s)
     T = slice_products(Ad, Bd)
-    S = ozaki_sum(E, F, T, beta, s)
+    S = ozaki_sum(E, F, T, beta, s, 2 if balanced else 0)
     return {"E": E, "F": F, "Ad": Ad, "Bd": Bd, "T": T, "S": S}
 
 

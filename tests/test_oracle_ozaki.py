@@ -228,3 +228,83 @@ def test_paper_literal_plateau_matches_paper_division_counts(prec, q):
     assert e_after >= e_at / 2
     if prec != "td":
         assert err(Dp - 1) > 2 * e_at
+
+
+# ---------------------------------------------------------------------------
+# balanced radix-32 digits (e4m3, beta = 5)
+# ---------------------------------------------------------------------------
+def test_balanced_split_hand_examples():
+    # worked by hand: 0.99 has E = 0; N = floor(0.99 * 2^9) = 506 = 16 * 32 - 6
+    # (residue 26 -> -6, carry 16 into the top digit); 1 - 2^-20 gives
+    # N = 511 = 16 * 32 - 1; 0.5 gives N = 256 = 8 * 32; 0.75 with s = 3
+    # gives N = 0.75 * 2^14 = 12 * 1024
+    A = [np.array([[0.99, -0.99, 0.5, 1 - 2.0 ** -20]])]
+    E, dig = O.split_balanced(A, 2)
+    assert E == [0]
+    assert [[int(d) for d in dig[:, 0, p]] for p in range(4)] == [[16, -6], [-16, 6], [8, 0], [16, -1]]
+    E, dig = O.split_balanced([np.array([[0.75]])], 3)
+    assert [int(d) for d in dig[:, 0, 0]] == [12, 0, 0]
+
+
+@pytest.mark.parametrize("prec,s", [("dd", 26), ("td", 9), ("qd", 44), ("ts", 14), ("dd", 1)])
+def test_balanced_split_invariants(prec, s):
+    rng = np.random.default_rng(11)
+    A = gen_operand(rng, prec, 6, 9, phi=2.0)
+    E, dig = O.split_balanced(A, s)
+    rem = O.split_remainder(A, E, dig, 5, eoff=1)
+    E1, bits = O.split(A, 1, 5 * s - 1)           # the same truncation, one bit per slice
+    assert E1 == E
+    vals = X.matrix_values(A)
+    for i in range(6):
+        for p in range(9):
+            x = X.to_fraction(vals[i][p])
+            ds = [int(dig[t, i, p]) for t in range(s)]
+            sg = 1 if x >= 0 else -1
+            assert 0 <= sg * ds[0] <= 16
+            assert all(-16 <= sg * d <= 15 for d in ds[1:])
+            back = sum(Fraction(d) * Fraction(2) ** (E[i] + 1 - 5 * (t + 1)) for t, d in enumerate(ds))
+            r = X.to_fraction(rem[i][p])
+            assert back + r == x
+            assert abs(r) < Fraction(2) ** (E[i] + 1 - 5 * s)
+            assert x == 0 or r == 0 or (r > 0) == (x > 0)      # truncation toward zero
+            trunc = sum(Fraction(int(bits[t, i, p])) * Fraction(2) ** (E[i] - (t + 1)) for t in range(5 * s - 1))
+            assert back == trunc
+
+
+def test_balanced_ozaki_sum_error_bound():
+    # remainders below 2^(E + 1 - 5 s), digits |d| <= 16, dropped pairs
+    # t + u > s + 1: |S_ij - C*_ij| <= 2 k s 2^(E_i + F_j + 2 - 5 s)
+    for prec, s in [("dd", 9), ("td", 12), ("qd", 5)]:
+        A, B = gen_problem(prec, 4, 5, 16, phi=1.0, seed=5)
+        r = O.ozaki_product(A, B, O.BETA_BAL, s, balanced=True)
+        ex = _clib.exact_block(A, B, range(4), range(5))
+        for i in range(4):
+            for j in range(5):
+                d = abs(X.to_fraction(r["S"][i][j]) - X.to_fraction(ex[i][j]))
+                assert d <= 2 * 16 * s * Fraction(2) ** (r["E"][i] + r["F"][j] + 2 - 5 * s)
+
+
+def test_balanced_ozaki_exact_special_cases():
+    # k = 1: a's 53 bits sit in the top 11 digits of a 23-digit window (the
+    # low 61 bits of N are zero, so are its 12 lowest digits), the same for
+    # b; every non-zero pair has t + u <= 22 <= s + 1 and S = a b exactly,
+    # whose canonical DD is TwoProd(a, b)
+    rng = random.Random(10)
+    for _ in range(50):
+        a = math.ldexp(rng.uniform(0.5, 1) * rng.choice([-1, 1]), rng.randint(-30, 30))
+        b = math.ldexp(rng.uniform(0.5, 1) * rng.choice([-1, 1]), rng.randint(-30, 30))
+        r = O.ozaki_product([np.array([[a]]), np.array([[0.0]])], [np.array([[b]]), np.array([[0.0]])],
+                            O.BETA_BAL, 23, balanced=True)
+        assert X.to_fraction(r["S"][0][0]) == Fraction(a) * Fraction(b)
+        assert X.to_components(r["S"][0][0], 2) == list(eft.two_prod(a, b))
+    # small integers (|a| <= 1000, E <= 10): with s = 8 the window's low 29
+    # bits are zero, only digits 1..3 can be non-zero, no non-zero pair is dropped
+    g = np.random.default_rng(12)
+    Ai = g.integers(-1000, 1001, (5, 8)).astype(np.float64)
+    Bi = g.integers(-1000, 1001, (8, 4)).astype(np.float64)
+    r = O.ozaki_product([np.asfortranarray(Ai), np.zeros((5, 8), order="F")],
+                        [np.asfortranarray(Bi), np.zeros((8, 4), order="F")], O.BETA_BAL, 8, balanced=True)
+    C = Ai @ Bi
+    for i in range(5):
+        for j in range(4):
+            assert X.to_fraction(r["S"][i][j]) == Fraction(int(C[i, j]))
