@@ -4,7 +4,8 @@
 Workload (the headline one): double-double C = A B with m = n = k = 4096,
 operands of Eq. 1 with exponent spread phi = 1 (synthetic, seeded), the
 slice count chosen automatically for the 2^-100 target; the digit form is
-selectable (default: the e4m3-digit form).  A step is the whole hot path:
+selectable (default: the automatic form, balanced radix-32 e4m3 digits on
+tcgen05).  A step is the whole hot path:
 exponent reduce + digit split (K1, K2) and the fused slice products with
 exact accumulation (K3).  Metric: effective GFLOP/s = 2 m n k / time.
 
@@ -19,7 +20,8 @@ Printed: one JSON line (rank 0).  Besides the contract keys it carries
                    host cores, on a bounded block of the same product, with
                    the GPU result's error against it;
   variants      -- single timed passes of the other forms/precisions
-                   (DD and QD, e4m3 / int8 / binary64 digits) at 4096^3;
+                   (DD and QD; balanced and 4-bit e4m3 / int8 / binary64
+                   digits) at 4096^3;
   multiprecision_2048 -- 8 and 16 binary64 components (424 / 848 bits)
                    at 2048^3, e4m3 digits on tcgen05;
   lu_4096       -- the LU application: DD n = 4096 and TD n = 2048 LU
@@ -265,7 +267,7 @@ def config2(oz, torch):
     out = []
     n = 1024
     for prec in ("td", "qd"):
-        for form in ("fp64", "fp8"):
+        for form in ("fp64", "fp8bal", "fp8"):
             try:
                 out.append(run_variant(oz, torch, prec, form, n, 1.0, 1, 1))
             except Exception as ex:
@@ -338,7 +340,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="dd")
-    ap.add_argument("--form", default="fp8")
+    ap.add_argument("--form", default="auto")
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--phi", type=float, default=1.0)
     ap.add_argument("--nslices", type=int, default=0)
@@ -505,7 +507,7 @@ def main():
     alg_flops = info.npairs * flops
     achieved = alg_flops / (kernel_ms * 1e-3) / 1e12
     peak_sus = None
-    if info.form in (oz.Form.FP8, oz.Form.FP8_MMA):
+    if info.form in (oz.Form.FP8, oz.Form.FP8_BAL, oz.Form.FP8_MMA):
         peak, peak_note = peak_fp8, f"e4m3 dense = bf16 {src} burst x 2 (nominal ratio)"
         peak_sus = bf16_sus * 2.0
     elif info.form == oz.Form.INT8:
@@ -514,18 +516,20 @@ def main():
         peak, peak_note = 1.05, "DMMA mma.sync f64 microbenchmark on this GB300 (no MEASURED_PEAKS entry)"
     sbytes = splitter_bytes(q, w, m, n, k, info.nslices, info.digit_bytes)
     # DRAM bytes per launch of the product kernel, from the ncu capture in
-    # profiles/k_gemm_tc_dd4096_s12.md scaled to this launch (reads by pairs,
-    # limb writes by drains); only for the kernel and workload captured there
+    # profiles/k_gemm_tc_bal_dd4096_s12.md (the same kernel and operands with
+    # 12 slices: 78 pairs, 12 drains per tile) scaled to this launch: operand
+    # reads by pairs, limb writes by drains; only for the workload captured there
     traffic = None
-    if oz.Form(info.form) == oz.Form.FP8 and args.prec == "dd" and m == n == k == 4096 and info.nslices == 32:
-        traffic = 7.256e9 * 528 / 78 + 1.523e9 * 46 / 12
+    if oz.Form(info.form) == oz.Form.FP8_BAL and prec == "dd" and m == n == k == 4096 and info.nslices == 26:
+        traffic = 9.353e9 * info.npairs / 78 + 1.609e9 * 36 / 12
 
     line = {
         "metric": metric, "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "e4m3" if info.form in (oz.Form.FP8, oz.Form.FP8_MMA) else
+        "vs_baseline": None, "dtype": "e4m3" if info.form in (oz.Form.FP8, oz.Form.FP8_BAL, oz.Form.FP8_MMA) else
         ("s8" if info.form == oz.Form.INT8 else "f64"),
-        "acc_dtype": "f32 (integers below 2^24, exact) -> int64 carry-save limbs" if info.form == oz.Form.FP8 else
+        "acc_dtype": "f32 (integers below 2^24, exact) -> int64 carry-save limbs"
+        if info.form in (oz.Form.FP8, oz.Form.FP8_BAL) else
         ("f32 (exact integers) -> int64" if info.form == oz.Form.FP8_MMA else
          ("s32 -> int64" if info.form == oz.Form.INT8 else "f64 (exact integers) -> int64")),
         "data": "synthetic (Eq. 1, seeded)",
@@ -534,7 +538,8 @@ def main():
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 gpu",
                    "l2": "inputs larger than L2 (A, B and the digit workspace each exceed 129 MB)"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": {oz.Form.FP8: "k_gemm_tc (tcgen05)", oz.Form.FP8_MMA: "k_gemm_b1<FP8> (mma.sync)",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": {oz.Form.FP8: "k_gemm_tc (tcgen05)",
+                                oz.Form.FP8_BAL: "k_gemm_tc (tcgen05)", oz.Form.FP8_MMA: "k_gemm_b1<FP8> (mma.sync)",
                                 oz.Form.INT8: "k_gemm_b1<INT8> (mma.sync)"}.get(oz.Form(info.form), "k_gemm_f64 (DMMA)"),
                      "peak_source": peak_note,
                      # back-to-back steps hold the GPU under its power cap: the sustained
@@ -550,7 +555,7 @@ def main():
                              "stream during step i's product (double-buffered device operands)"},
         # per step: 5 split kernels (exponent init, row and column exponents, row and
         # column digits) + the slice-product kernel + (tcgen05 form) its rounding pass
-        "gpu_launches": (7 if oz.Form(info.form) == oz.Form.FP8 else 6) * args.steps,
+        "gpu_launches": (7 if oz.Form(info.form) in (oz.Form.FP8, oz.Form.FP8_BAL) else 6) * args.steps,
         "clocks": clk,
         "device_status": status.name,
     }
@@ -580,8 +585,8 @@ def main():
         del Ad, Bd, C, Ad2, Bd2, Cd2
         torch.cuda.empty_cache()
         var = []
-        for vp, vf in [("dd", "fp8mma"), ("dd", "int8"), ("dd", "fp64"), ("qd", "fp8"), ("qd", "fp8mma"),
-                       ("qd", "int8"), ("qd", "fp64")]:
+        for vp, vf in [("dd", "fp8"), ("dd", "fp8mma"), ("dd", "int8"), ("dd", "fp64"), ("qd", "fp8bal"),
+                       ("qd", "fp8"), ("qd", "fp8mma"), ("qd", "int8"), ("qd", "fp64")]:
             try:
                 var.append(run_variant(oz, torch, vp, vf, args.n, args.phi, 1, 1))
             except Exception as ex:  # report, do not hide

@@ -55,6 +55,7 @@ class Form(IntEnum):
     INT8 = 2
     FP8 = 3
     FP8_MMA = 4
+    FP8_BAL = 5
 
 
 MAX_COMPONENTS = 16
@@ -62,7 +63,7 @@ MAX_COMPONENTS = 16
 PREC_BY_NAME = {"dd": Prec.DD, "td": Prec.TD, "qd": Prec.QD, "ts": Prec.TS}
 PREC_BY_NAME.update({f"q{q}": q for q in range(2, MAX_COMPONENTS + 1)})
 FORM_BY_NAME = {"auto": Form.AUTO, "fp64": Form.FP64, "int8": Form.INT8, "fp8": Form.FP8,
-                "fp8mma": Form.FP8_MMA}
+                "fp8mma": Form.FP8_MMA, "fp8bal": Form.FP8_BAL}
 NCOMP = {Prec.DD: 2, Prec.TD: 3, Prec.QD: 4, Prec.TS: 3}
 NCOMP.update({q: q for q in range(5, MAX_COMPONENTS + 1)})
 

@@ -21,7 +21,7 @@ ozmp_status ozmp_plan_create(ozmp_plan* plan, ozmp_prec prec, int64_t m, int64_t
                              ozmp_form form, int nslices, ozmp_stream stream) {
     if (!plan) return OZMP_ERR_INVALID_ARG;
     *plan = nullptr;
-    ozmp_plan_s* p = new (std::nothrow) ozmp_plan_s;
+    ozmp_plan_s* p = new (std::nothrow) ozmp_plan_s();   // zeroed: a rejected plan frees nothing it has not set
     if (!p) return OZMP_ERR_NOMEM;
     ozmp_status st = plan_init(p, prec, m, n, k, form, nslices, stream);
     if (st == OZMP_OK) st = plan_schedule(p);
@@ -59,7 +59,7 @@ ozmp_status ozmp_plan_destroy(ozmp_plan p) {
 ozmp_status ozmp_plan_get_info(ozmp_plan p, ozmp_plan_info* info) {
     if (!p || !info) return OZMP_ERR_INVALID_ARG;
     info->prec = p->prec;
-    info->form = p->form;
+    info->form = p->bal ? OZMP_FORM_FP8_BAL : p->form;
     info->beta = p->beta;
     info->nslices = p->s;
     info->npairs = (int64_t)p->s * (p->s + 1) / 2;
@@ -206,7 +206,7 @@ ozmp_status ozmp_set_stream(ozmp_stream stream) {
 }
 
 ozmp_status ozmp_set_form(ozmp_form form) {
-    if (form < OZMP_FORM_AUTO || form > OZMP_FORM_FP8_MMA) return OZMP_ERR_INVALID_ARG;
+    if (form < OZMP_FORM_AUTO || form > OZMP_FORM_FP8_BAL) return OZMP_ERR_INVALID_ARG;
     tl_form = form;
     return OZMP_OK;
 }

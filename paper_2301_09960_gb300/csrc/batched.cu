@@ -89,22 +89,42 @@ __global__ void __launch_bounds__(256) k_b_exp_cols(const BSplit* P, const int* 
     exp_cols_body(opB<T>(s), s.k, s.n, s.F, status, (int64_t)(blockIdx.x - pre[p]), (int64_t)0);
 }
 
-template <typename T, int NW>
+// FORM: OZMP_FORM_FP8 (4-bit digits) or OZMP_FORM_FP8_BAL (balanced radix-32 digits)
+template <typename T, int NW, int FORM>
 __global__ void __launch_bounds__(256) k_b_split_rows(const BSplit* P, const int* pre, int count) {
     const int p = find_prob(pre, count, blockIdx.x);
     const BSplit& s = P[p];
     const int lb = blockIdx.x - pre[p];
     const int nbx = (int)(s.mp / 32);
-    split_rows_b1_body<T, OZMP_FORM_FP8, NW>(opA<T>(s), s.m, s.k, s.E, s.Adig, s.mp, s.kp, s.s,
-                                             (int64_t)(lb % nbx), (int64_t)(lb / nbx));
+    split_rows_b1_body<T, FORM, NW>(opA<T>(s), s.m, s.k, s.E, s.Adig, s.mp, s.kp, s.s,
+                                    (int64_t)(lb % nbx), (int64_t)(lb / nbx));
 }
 
-template <typename T, int NW>
+template <typename T, int NW, int FORM>
 __global__ void __launch_bounds__(256) k_b_split_cols(const BSplit* P, const int* pre, int count) {
     const int p = find_prob(pre, count, blockIdx.x);
     const BSplit& s = P[p];
-    split_cols_b1_body<T, OZMP_FORM_FP8, NW>(opB<T>(s), s.k, s.n, s.F, s.Bdig, s.np, s.kp, s.s,
-                                             (int64_t)(blockIdx.x - pre[p]), (int64_t)0);
+    split_cols_b1_body<T, FORM, NW>(opB<T>(s), s.k, s.n, s.F, s.Bdig, s.np, s.kp, s.s,
+                                    (int64_t)(blockIdx.x - pre[p]), (int64_t)0);
+}
+
+template <typename T, int FORM>
+static void set_split_smem(size_t sm) {
+    cudaFuncSetAttribute(k_b_split_rows<T, 4, FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_b_split_rows<T, 6, FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+}
+
+// the digit launches of one group (rows of A into shared-memory tiles, columns of B direct)
+template <typename T, int FORM>
+static void split_group(int nw, const int (&blocks)[5], const BSplit* sp, const int* const (&pre)[5], int cnt,
+                        size_t sm, cudaStream_t cs) {
+    if (nw == 4) {
+        k_b_split_rows<T, 4, FORM><<<blocks[3], 256, sm, cs>>>(sp, pre[3], cnt);
+        k_b_split_cols<T, 4, FORM><<<blocks[4], 256, 0, cs>>>(sp, pre[4], cnt);
+    } else {
+        k_b_split_rows<T, 6, FORM><<<blocks[3], 256, sm, cs>>>(sp, pre[3], cnt);
+        k_b_split_cols<T, 6, FORM><<<blocks[4], 256, 0, cs>>>(sp, pre[4], cnt);
+    }
 }
 
 }  // namespace ozmp
@@ -141,6 +161,7 @@ struct Group {              // problems sharing a component type (batched split 
 
 struct Batch {
     int count = 0, form = 0;
+    bool bal = false;              // balanced radix-32 e4m3 digits (FORM_FP8_BAL)
     std::vector<ozmp_plan_s> subs;
     std::vector<size_t> ws_off;
     std::vector<int> bn;
@@ -263,8 +284,16 @@ void destroy(void* b) { destroy_batch((Batch*)b); }
 extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, ozmp_form form, ozmp_stream stream,
                                          ozmp_plan* plan) {
     if (!probs || count <= 0 || !plan) return OZMP_ERR_INVALID_ARG;
-    if (form < OZMP_FORM_AUTO || form > OZMP_FORM_FP8_MMA) return OZMP_ERR_INVALID_ARG;
-    const int fm = (form == OZMP_FORM_AUTO) ? OZMP_FORM_FP8 : form;
+    if (form < OZMP_FORM_AUTO || form > OZMP_FORM_FP8_BAL) return OZMP_ERR_INVALID_ARG;
+    // balanced digits run on the tcgen05 engine of the e4m3 form (also the
+    // automatic choice, unless a problem forces more slices than they allow)
+    bool bal = (form == OZMP_FORM_FP8_BAL);
+    if (form == OZMP_FORM_AUTO) {
+        bal = true;
+        for (int i = 0; i < count; ++i)
+            if (probs[i].nslices > 63) bal = false;
+    }
+    const int fm = (form == OZMP_FORM_AUTO || bal) ? OZMP_FORM_FP8 : form;
     // argument checks of every problem
     for (int i = 0; i < count; ++i) {
         const ozmp_problem& r = probs[i];
@@ -284,7 +313,7 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
     Batch* b = nullptr;
     if (P) {
         b = (Batch*)P->batch;
-        if (!b || b->count != count || b->form != fm) return OZMP_ERR_INVALID_ARG;
+        if (!b || b->count != count || b->form != fm || b->bal != bal) return OZMP_ERR_INVALID_ARG;
         for (int i = 0; i < count; ++i) {
             const ozmp_plan_s& s = b->subs[i];
             if (s.prec != probs[i].prec || s.m != probs[i].m || s.n != probs[i].n || s.k != probs[i].k)
@@ -297,6 +326,7 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
         if (!b) return OZMP_ERR_NOMEM;
         b->count = count;
         b->form = fm;
+        b->bal = bal;
         b->subs.resize(count);
         b->ws_off.resize(count);
         b->bn.resize(count, 256);
@@ -305,7 +335,7 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
         for (int i = 0; i < count; ++i) {
             const ozmp_problem& r = probs[i];
             ozmp_plan_s& s = b->subs[i];
-            ozmp_status e = plan_init(&s, r.prec, r.m, r.n, r.k, fm, r.nslices, stream);
+            ozmp_status e = plan_init(&s, r.prec, r.m, r.n, r.k, bal ? (int)OZMP_FORM_FP8_BAL : fm, r.nslices, stream);
             if (e == OZMP_OK && s.big) e = OZMP_ERR_UNSUPPORTED;   // windows wider than the batched splitter's
             if (e != OZMP_OK) { destroy_batch(b); return e; }
             b->q[i] = s.q;
@@ -334,7 +364,7 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
                 if (b->subs[i].is_f32 == t && b->subs[i].m > 0 && b->subs[i].n > 0 && b->subs[i].k > 0) {
                     g.ids.push_back(i);
                     g.s_max = std::max(g.s_max, b->subs[i].s);
-                    if ((4 * b->subs[i].s + 65 + 63) / 64 > 4) g.nw = 6;
+                    if ((b->subs[i].beta * b->subs[i].s + 65 + 63) / 64 > 4) g.nw = 6;
                 }
             if (!g.ids.empty()) b->groups.push_back(g);
         }
@@ -503,6 +533,7 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
         p.q = s.q; p.is_f32 = s.is_f32; p.s = s.s; p.beta = s.beta; p.ppd = s.ppd; p.acc_words = s.acc_words;
         p.bn = b->bn[i];
         p.defer = b->fin_blocks > 0 ? 1 : 0;
+        p.eoff = b->bal ? 2 : 0;
     }
 
     // ---------------------------------------------------------------- graph
@@ -531,11 +562,9 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
         for (Group& g : b->groups) {
             const size_t sm = (size_t)g.s_max * 32 * 16 * 4;
             if (g.is_f32) {
-                cudaFuncSetAttribute(k_b_split_rows<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-                cudaFuncSetAttribute(k_b_split_rows<float, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                if (b->bal) set_split_smem<float, OZMP_FORM_FP8_BAL>(sm); else set_split_smem<float, OZMP_FORM_FP8>(sm);
             } else {
-                cudaFuncSetAttribute(k_b_split_rows<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-                cudaFuncSetAttribute(k_b_split_rows<double, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                if (b->bal) set_split_smem<double, OZMP_FORM_FP8_BAL>(sm); else set_split_smem<double, OZMP_FORM_FP8>(sm);
             }
         }
         tc_set_smem();
@@ -561,23 +590,13 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
                     if (g.is_f32) {
                         k_b_exp_rows<float><<<g.blocks[1], 256, 0, cs>>>(sp, pre[1], cnt, status);
                         k_b_exp_cols<float><<<g.blocks[2], 256, 0, cs>>>(sp, pre[2], cnt, status);
-                        if (g.nw == 4) {
-                            k_b_split_rows<float, 4><<<g.blocks[3], 256, sm, cs>>>(sp, pre[3], cnt);
-                            k_b_split_cols<float, 4><<<g.blocks[4], 256, 0, cs>>>(sp, pre[4], cnt);
-                        } else {
-                            k_b_split_rows<float, 6><<<g.blocks[3], 256, sm, cs>>>(sp, pre[3], cnt);
-                            k_b_split_cols<float, 6><<<g.blocks[4], 256, 0, cs>>>(sp, pre[4], cnt);
-                        }
+                        if (b->bal) split_group<float, OZMP_FORM_FP8_BAL>(g.nw, g.blocks, sp, pre, cnt, sm, cs);
+                        else split_group<float, OZMP_FORM_FP8>(g.nw, g.blocks, sp, pre, cnt, sm, cs);
                     } else {
                         k_b_exp_rows<double><<<g.blocks[1], 256, 0, cs>>>(sp, pre[1], cnt, status);
                         k_b_exp_cols<double><<<g.blocks[2], 256, 0, cs>>>(sp, pre[2], cnt, status);
-                        if (g.nw == 4) {
-                            k_b_split_rows<double, 4><<<g.blocks[3], 256, sm, cs>>>(sp, pre[3], cnt);
-                            k_b_split_cols<double, 4><<<g.blocks[4], 256, 0, cs>>>(sp, pre[4], cnt);
-                        } else {
-                            k_b_split_rows<double, 6><<<g.blocks[3], 256, sm, cs>>>(sp, pre[3], cnt);
-                            k_b_split_cols<double, 6><<<g.blocks[4], 256, 0, cs>>>(sp, pre[4], cnt);
-                        }
+                        if (b->bal) split_group<double, OZMP_FORM_FP8_BAL>(g.nw, g.blocks, sp, pre, cnt, sm, cs);
+                        else split_group<double, OZMP_FORM_FP8>(g.nw, g.blocks, sp, pre, cnt, sm, cs);
                     }
                 }
                 if (b->grid > 0) {

@@ -549,6 +549,7 @@ cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t st) {
     p.T = g.T;
     p.m = g.m; p.n = g.n; p.mp = g.mp; p.np = g.np; p.kp = g.kp; p.ldc = g.ldc;
     p.q = g.q; p.is_f32 = g.is_f32; p.s = g.s; p.beta = g.beta; p.ppd = g.ppd; p.acc_words = g.acc_words;
+    p.eoff = g.eoff;
     p.bn = tc::BN;
     p.d_only = g.d_only;
     p.sacc = g.sacc;

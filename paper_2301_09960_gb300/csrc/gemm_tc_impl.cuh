@@ -254,7 +254,7 @@ __device__ __forceinline__ void finish_element(const GemmArgs& g, int nl, const 
     }
     const int Ei = g.E[i], Fj = g.F[j];
     const bool nz = (Ei != OZMP_EXP_ZERO && Fj != OZMP_EXP_ZERO);
-    const int U = nz ? Ei + Fj - g.beta * (g.s + 1) : 0;
+    const int U = nz ? Ei + Fj + g.eoff - g.beta * (g.s + 1) : 0;
     const size_t at = (size_t)(i + j * g.ldc);
     bool ok = true;
     if (g.is_f32) {
@@ -292,6 +292,7 @@ struct Prob {
     int* cnt;              // split tiles: chunks finished per slot, zeroed before the launch
     int64_t m, n, mp, np, kp, ldc;
     int q, is_f32, s, beta, ppd, acc_words, bn, d_only;
+    int eoff;              // exponent offset of the digit weights (2: balanced digits)
     int defer;             // 1: the limbs are rounded into C by a separate pass after the launch
 };
 
@@ -303,7 +304,8 @@ __device__ __forceinline__ GemmArgs as_gemm_args(const Prob& p, uint32_t* status
     g.is_f32 = p.is_f32;
     g.m = p.m; g.n = p.n; g.k = 0; g.mp = p.mp; g.np = p.np; g.kp = p.kp;
     g.E = p.E; g.F = p.F; g.Adig = nullptr; g.Bdig = nullptr;
-    g.s = p.s; g.beta = p.beta; g.ppd = p.ppd; g.group_start = 0; g.acc_words = p.acc_words; g.ngroups = 0;
+    g.s = p.s; g.beta = p.beta; g.eoff = p.eoff; g.ppd = p.ppd; g.group_start = 0; g.acc_words = p.acc_words;
+    g.ngroups = 0;
     g.acc = p.acc;
     for (int c = 0; c < OZMP_MAX_COMPONENTS; ++c) g.C[c] = p.C[c];
     g.ldc = p.ldc;

@@ -22,6 +22,7 @@ struct SplitArgs {
     void* Bdig;
     int s, beta;
     int big;               // the many-component / wide-window splitter (split_big.cu)
+    int bal;               // balanced radix-32 e4m3 digits (beta = 5)
 };
 
 struct GemmArgs {
@@ -34,6 +35,7 @@ struct GemmArgs {
     const void* Adig;
     const void* Bdig;
     int s, beta;
+    int eoff;              // digit t of a row weighs 2^(E + eoff/2 - beta t): 0, or 2 for balanced digits
     int ppd;               // slice pairs summed in the tensor-core accumulator before a drain
     uint64_t group_start;  // bit (d - 2): diagonal d opens a new group (diagonals run s+1 .. 2)
     int acc_words;         // 64-bit words of the per-element exact accumulator

@@ -58,20 +58,29 @@ __device__ __forceinline__ int bitlen(uint64_t x) { return 64 - __clzll((long lo
 // ----------------------------------------------------------------------------
 // multiword two's complement helpers (NW words, word 0 least significant)
 // ----------------------------------------------------------------------------
+// (the carries travel in 128-bit sums, so the compiler owns the carry chain:
+// separate inline-asm add.cc / addc.cc statements carry no dependency on the
+// condition code and may be interleaved with other chains)
 template <int NW>
 __device__ __forceinline__ void mw_add(uint64_t (&w)[NW], const uint64_t (&p)[NW]) {
-    asm("add.cc.u64 %0, %0, %1;" : "+l"(w[0]) : "l"(p[0]));
+    uint64_t c = 0;
 #pragma unroll
-    for (int j = 1; j < NW - 1; ++j) asm("addc.cc.u64 %0, %0, %1;" : "+l"(w[j]) : "l"(p[j]));
-    asm("addc.u64 %0, %0, %1;" : "+l"(w[NW - 1]) : "l"(p[NW - 1]));
+    for (int j = 0; j < NW; ++j) {
+        const unsigned __int128 t = (unsigned __int128)w[j] + p[j] + c;
+        w[j] = (uint64_t)t;
+        c = (uint64_t)(t >> 64);
+    }
 }
 
 template <int NW>
 __device__ __forceinline__ void mw_sub(uint64_t (&w)[NW], const uint64_t (&p)[NW]) {
-    asm("sub.cc.u64 %0, %0, %1;" : "+l"(w[0]) : "l"(p[0]));
+    uint64_t b = 0;
 #pragma unroll
-    for (int j = 1; j < NW - 1; ++j) asm("subc.cc.u64 %0, %0, %1;" : "+l"(w[j]) : "l"(p[j]));
-    asm("subc.u64 %0, %0, %1;" : "+l"(w[NW - 1]) : "l"(p[NW - 1]));
+    for (int j = 0; j < NW; ++j) {
+        const unsigned __int128 t = (unsigned __int128)w[j] - p[j] - b;
+        w[j] = (uint64_t)t;
+        b = (uint64_t)(t >> 64) & 1u;   // a borrow wraps the 128-bit difference
+    }
 }
 
 template <int NW>

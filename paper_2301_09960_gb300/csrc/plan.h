@@ -29,6 +29,7 @@ struct ozmp_plan_s {
     int tc_cg;                                   // 2: the schedule is over CTA-pair tiles
     int tc_dyn;                                  // items taken from a counter (else per-CTA lists)
     int big;                                     // the many-component splitter (q > 4 or wide windows)
+    int bal;                                     // balanced radix-32 e4m3 digits (FORM_FP8_BAL, beta = 5)
     // tcgen05 form, for tests of the bounded waits (OZMP_TC_WAIT_LIMIT, OZMP_TC_INJECT_STALL)
     long long tc_wait_limit;
     int tc_inject_stall;
@@ -95,7 +96,7 @@ inline int bitlen128(unsigned __int128 x) {
 inline ozmp_status fill_schedule(ozmp_plan_s* p) {
     // largest digit magnitude and the exact-accumulation limit of the engine
     const bool e4m3 = (p->form == OZMP_FORM_FP8 || p->form == OZMP_FORM_FP8_MMA);
-    uint64_t dmax = e4m3 ? 15u : ((1u << p->beta) - 1u);
+    uint64_t dmax = p->bal ? 16u : e4m3 ? 15u : ((1u << p->beta) - 1u);
     unsigned __int128 limit = e4m3 ? ((unsigned __int128)1 << 24)
                             : (p->form == OZMP_FORM_INT8) ? (unsigned __int128)2147483647u
                             : ((unsigned __int128)1 << 53);
@@ -201,6 +202,7 @@ inline SplitArgs split_args(ozmp_plan_s* p, const void* const* A, int64_t lda, c
     a.s = p->s;
     a.beta = p->beta;
     a.big = p->big;
+    a.bal = p->bal;
     return a;
 }
 
@@ -215,6 +217,7 @@ inline GemmArgs gemm_args(ozmp_plan_s* p) {
     g.Adig = w + p->off_Adig;
     g.Bdig = w + p->off_Bdig;
     g.s = p->s; g.beta = p->beta; g.ppd = p->ppd; g.group_start = p->group_start;
+    g.eoff = p->bal ? 2 : 0;
     g.acc_words = p->acc_words; g.ngroups = p->ngroups;
     g.acc = (p->ngroups > 1 || p->form == OZMP_FORM_FP8) ? (int64_t*)(w + p->off_acc) : nullptr;
     g.status = (uint32_t*)(w + p->off_status);
@@ -327,33 +330,43 @@ inline ozmp_status zero_c(ozmp_plan_s* p, void* const* C, int64_t ldc) {
 // drain/group schedule and the workspace layout.  No memory is allocated.
 inline ozmp_status plan_init(ozmp_plan_s* p, int prec, int64_t m, int64_t n, int64_t k, int form, int nslices,
                              ozmp_stream stream) {
+    memset(p, 0, sizeof(*p));
     int q = prec_q(prec);
     if (!q || m < 0 || n < 0 || k < 0 || nslices < 0 || nslices > OZMP_MAX_SLICES) return OZMP_ERR_INVALID_ARG;
-    if (form < OZMP_FORM_AUTO || form > OZMP_FORM_FP8_MMA) return OZMP_ERR_INVALID_ARG;
-    memset(p, 0, sizeof(*p));
+    if (form < OZMP_FORM_AUTO || form > OZMP_FORM_FP8_BAL) return OZMP_ERR_INVALID_ARG;
     p->prec = prec;
     p->q = q;
     p->is_f32 = (prec == OZMP_TS);
-    p->form = (form == OZMP_FORM_AUTO) ? OZMP_FORM_FP8 : form;
+    // balanced digits run on the tcgen05 engine of the e4m3 form, beta = 5;
+    // the automatic form takes them wherever their splitter applies (q <= 4,
+    // s <= 63), else the 4-bit digits
+    p->bal = (form == OZMP_FORM_FP8_BAL || (form == OZMP_FORM_AUTO && q <= 4 && nslices <= 63)) ? 1 : 0;
+    p->form = (form == OZMP_FORM_AUTO || p->bal) ? OZMP_FORM_FP8 : form;
     p->m = m; p->n = n; p->k = k;
-    p->beta = (p->form == OZMP_FORM_FP64) ? beta_fp64(k) : (p->form == OZMP_FORM_INT8 ? 7 : 4);
+    p->beta = (p->form == OZMP_FORM_FP64) ? beta_fp64(k)
+            : (p->form == OZMP_FORM_INT8 ? 7 : (p->bal ? 5 : 4));
     p->db = (p->form == OZMP_FORM_FP64) ? 8 : 1;
-    // slice limits: the register-resident splitter holds beta s <= 376 (7-word
-    // windows) and 4 components; the tcgen05 form goes on with the
-    // many-component splitter up to beta s + 65 <= 1024 (16-word windows)
+    // slice limits: the register-resident splitters hold 4 components,
+    // windows of beta s + 65 bits in 7 words (binary64 digits: beta s <= 376)
+    // or 6 words (1-byte digits), and write at most 64 e4m3 slices (63
+    // balanced ones); the tcgen05 form goes on with the many-component
+    // splitter up to beta s + 65 <= 1024 (16-word windows)
     const bool tc = (p->form == OZMP_FORM_FP8);
     if (q > 4 && !tc) return OZMP_ERR_UNSUPPORTED;
-    const int maxs = tc ? (1024 - 65) / 4 : (p->form == OZMP_FORM_INT8 ? 36 : 64);
-    const int maxbits = tc ? 1024 - 65 : 376;
+    // balanced digits: the register-resident splitter only (q <= 4, 6-word windows)
+    if (p->bal && q > 4) return OZMP_ERR_UNSUPPORTED;
+    const int maxs = p->bal ? (6 * 64 - 65) / 5 : tc ? (1024 - 65) / 4 : (p->form == OZMP_FORM_INT8 ? 36 : 64);
+    const int maxbits = p->bal ? 6 * 64 - 65 : tc ? 1024 - 65 : 376;
     if (nslices == 0) {
         int bits = prec_target_bits(prec) + ceil_log2(k > 0 ? k : 1) + 16;
-        nslices = (bits + p->beta - 1) / p->beta;
+        // balanced digits keep 5 s - 1 bits below 2^E (the top digit is at most 16)
+        nslices = p->bal ? (bits + 1 + 4) / 5 : (bits + p->beta - 1) / p->beta;
         if (nslices > maxs) nslices = maxs;
         while (nslices > 1 && nslices * p->beta > maxbits) --nslices;
     }
     if (nslices > maxs || nslices * p->beta > maxbits) return OZMP_ERR_UNSUPPORTED;
     p->s = nslices;
-    p->big = (q > 4 || nslices * p->beta > 376) ? 1 : 0;
+    p->big = (!p->bal && (q > 4 || nslices > 64)) ? 1 : 0;
     p->mp = roundup(m, 128);
     p->np = roundup(n, p->form == OZMP_FORM_FP8 ? 256 : 128);
     p->kp = roundup(k, 128);

@@ -4,6 +4,7 @@
 namespace ozmp {
 
 cudaError_t launch_digits_fp8(const SplitArgs& g, cudaStream_t st);
+cudaError_t launch_digits_fp8bal(const SplitArgs& g, cudaStream_t st);
 cudaError_t launch_digits_int8(const SplitArgs& g, cudaStream_t st);
 cudaError_t launch_digits_fp64(const SplitArgs& g, cudaStream_t st);
 cudaError_t launch_exponents_big(const SplitArgs& g, cudaStream_t st);
@@ -36,7 +37,7 @@ static cudaError_t exponents_impl(const SplitArgs& g, cudaStream_t st) {
 
 cudaError_t launch_split(const SplitArgs& g, cudaStream_t st) {
     if (g.big) {
-        // more than 4 components or a window wider than 448 bits (split_big.cu)
+        // more than 4 components or a window wider than the register splitter's (split_big.cu)
         init_exponents(g, st);
         cudaError_t e = launch_exponents_big(g, st);
         if (e != cudaSuccess) return e;
@@ -49,6 +50,7 @@ cudaError_t launch_split(const SplitArgs& g, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     if (g.form == OZMP_FORM_FP64) return launch_digits_fp64(g, st);
     if (g.form == OZMP_FORM_INT8) return launch_digits_int8(g, st);
+    if (g.bal) return launch_digits_fp8bal(g, st);
     return launch_digits_fp8(g, st);   // FORM_FP8 and FORM_FP8_MMA share the e4m3 digits
 }
 

@@ -6,8 +6,11 @@
 // E_i = max_p floor(log2|a_ip|) + 1 of the exact element values, and the
 // slices are the base-2^beta digits of |a_ip| 2^(beta s - E_i) truncated
 // toward zero (sign of a_ip), found with exact integer arithmetic on the
-// IEEE encodings.
+// IEEE encodings.  The balanced e4m3 form writes the same truncated value,
+// floor(|a_ip| 2^(5 s - 1 - E_i)), in balanced radix-32 digits.
 #pragma once
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include "ozmp_internal.cuh"
 #include "kernels.h"
 
@@ -152,6 +155,7 @@ template <int FORM>
 struct DigitTraits;
 template <> struct DigitTraits<OZMP_FORM_INT8> { static constexpr int BETA = 7; static constexpr int MAXS = 36; };
 template <> struct DigitTraits<OZMP_FORM_FP8> { static constexpr int BETA = 4; static constexpr int MAXS = 64; };
+template <> struct DigitTraits<OZMP_FORM_FP8_BAL> { static constexpr int BETA = 5; static constexpr int MAXS = 63; };
 
 // the digit windows of four elements -> one 32-bit word of slice t
 template <int FORM, int NW>
@@ -200,6 +204,82 @@ __device__ __forceinline__ void pack_fp8_quad(uint64_t (&w)[4][NW], const int (&
             if (8 * h + 4 - b <= s) put(8 * h + 4 - b, th[b]);
             if (8 * h + 8 - b <= s) put(8 * h + 8 - b, tl[b]);
         }
+    }
+}
+
+// bit 4 of every 5-bit digit group t = 1, 2, ... of a top-aligned window
+// (group t at bits [64 NW - 5 t, 64 NW - 5 t + 5)), word j
+__host__ __device__ constexpr uint64_t bal_sixteens(int nw, int j) {
+    uint64_t r = 0;
+    for (int t = 1; 64 * nw - 5 * t >= 0; ++t) {
+        const int b = 64 * nw - 5 * t + 4;
+        if (b >= 64 * j && b < 64 * j + 64) r |= 1ull << (b - 64 * j);
+    }
+    return r;
+}
+
+// The balanced radix-32 e4m3 digits of four elements (consecutive k), all
+// slices: calls put(t, word) for t = 1 .. s with byte e of `word` = e4m3 code
+// of digit t of element e.  The magnitude window holds
+// floor(|x| 2^(64 NW - 1 - E)); group t of its top 5 s bits is digit t of
+// N = floor(|x| 2^(5 s - 1 - E)) in plain radix 32.  Adding 16 to every
+// group (G = window + sum_t 16 2^(64 NW - 5 t), nothing added below the
+// lowest group, so no carry enters it) makes the groups of G the balanced
+// digits plus 16: d_t = g_t - 16 in [-16, 15], and the carry out of the top
+// group turns d_1 into 16.  Each g goes through binary16 as 1024 + g (exact),
+// one fused multiply-add applies -16 and the element's sign (exact: the
+// result is an integer of magnitude <= 16, a zero digit comes out +0), and
+// the conversion to e4m3 is exact for these integers.
+template <int NW, typename Put>
+__device__ __forceinline__ void pack_bal_quad(uint64_t (&w)[4][NW], const int (&sign)[4], int s, Put&& put) {
+    constexpr int TMAX = (64 * NW - 65) / 5;
+    const int lo = 64 * NW - 5 * s;   // lowest bit of the lowest group (>= 65)
+    uint64_t H[NW];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+        const uint64_t keep = (lo <= 64 * j) ? ~0ull : (lo >= 64 * j + 64 ? 0ull : (~0ull << (lo - 64 * j)));
+        H[j] = bal_sixteens(NW, j) & keep;
+    }
+    uint32_t top[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        // the top word gets bit 63 of H and never equals its old value: it
+        // wrapped (the carry out of the top group) iff it came out smaller
+        const uint64_t before = w[e][NW - 1];
+        mw_add<NW>(w[e], H);
+        top[e] = (w[e][NW - 1] < before) ? 32u : 0u;
+    }
+    // per pair of elements: binary16 multipliers (+-1) and addends (-+1040)
+    __half2 mul[2], add[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float s0 = sign[2 * h] < 0 ? -1.f : 1.f, s1 = sign[2 * h + 1] < 0 ? -1.f : 1.f;
+        mul[h] = __floats2half2_rn(s0, s1);
+        add[h] = __floats2half2_rn(-1040.f * s0, -1040.f * s1);
+    }
+#pragma unroll
+    for (int t = 1; t <= TMAX; ++t) {
+        if (t > s) break;
+        const int pos = 64 * NW - 5 * t;
+        const int wi = pos >> 6, off = pos & 63;
+        uint32_t g[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            uint64_t x = w[e][wi] >> off;
+            if (off > 59) x |= w[e][wi + 1] << (64 - off);
+            g[e] = ((uint32_t)x & 31u) | (t == 1 ? top[e] : 0u);
+        }
+        uint32_t word = 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t bits = 0x64006400u | g[2 * h] | (g[2 * h + 1] << 16);   // 1024 + g, two lanes
+            __half2 v = *reinterpret_cast<const __half2*>(&bits);
+            v = __hfma2(v, mul[h], add[h]);
+            const __nv_fp8x2_storage_t c8 =
+                __nv_cvt_halfraw2_to_fp8x2(static_cast<__half2_raw>(v), __NV_SATFINITE, __NV_E4M3);
+            word |= (uint32_t)c8 << (16 * h);
+        }
+        put(t, word);
     }
 }
 
@@ -261,6 +341,8 @@ __device__ __forceinline__ void split_rows_b1_body(Operand<T> a, int64_t m, int6
         for (int e = 0; e < 4; ++e) sign[e] = window_loaded<T, NW>(v[e], q, Erow, w[e]);
         if constexpr (FORM == OZMP_FORM_FP8) {
             pack_fp8_quad<NW>(w, sign, s, [&](int t, uint32_t word) { sw[((t - 1) * TI + ri) * QW + qd] = word; });
+        } else if constexpr (FORM == OZMP_FORM_FP8_BAL) {
+            pack_bal_quad<NW>(w, sign, s, [&](int t, uint32_t word) { sw[((t - 1) * TI + ri) * QW + qd] = word; });
         } else {
 #pragma unroll
             for (int t = 1; t <= DigitTraits<FORM>::MAXS; ++t)
@@ -302,6 +384,10 @@ __device__ __forceinline__ void split_cols_b1_body(Operand<T> b, int64_t k, int6
     for (int e = 0; e < 4; ++e) sign[e] = window_loaded<T, NW>(v[e], q, Ecol, w[e]);
     if constexpr (FORM == OZMP_FORM_FP8) {
         pack_fp8_quad<NW>(w, sign, s, [&](int t, uint32_t word) {
+            *reinterpret_cast<uint32_t*>(dig + ((size_t)(t - 1) * np + j) * kp + p0) = word;
+        });
+    } else if constexpr (FORM == OZMP_FORM_FP8_BAL) {
+        pack_bal_quad<NW>(w, sign, s, [&](int t, uint32_t word) {
             *reinterpret_cast<uint32_t*>(dig + ((size_t)(t - 1) * np + j) * kp + p0) = word;
         });
     } else {
@@ -393,11 +479,12 @@ static cudaError_t digits_b1_q(const SplitArgs& g, cudaStream_t st) {
 // the int8 form keeps it a run-time value
 template <typename T, int FORM, int NW>
 static cudaError_t digits_b1(const SplitArgs& g, cudaStream_t st) {
-    if constexpr (FORM == OZMP_FORM_FP8 && sizeof(T) == 8) {
+    constexpr bool e4m3 = (FORM == OZMP_FORM_FP8 || FORM == OZMP_FORM_FP8_BAL);
+    if constexpr (e4m3 && sizeof(T) == 8) {
         if (g.q == 2) return digits_b1_q<T, FORM, NW, 2>(g, st);
         if (g.q == 3) return digits_b1_q<T, FORM, NW, 3>(g, st);
         return digits_b1_q<T, FORM, NW, 4>(g, st);
-    } else if constexpr (FORM == OZMP_FORM_FP8) {
+    } else if constexpr (e4m3) {
         return digits_b1_q<T, FORM, NW, 3>(g, st);
     } else {
         return digits_b1_q<T, FORM, NW, 0>(g, st);

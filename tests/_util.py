@@ -17,7 +17,7 @@ def digits_to_int(arr, form):
         return v.astype(np.int64)
     if form == "int8":
         return arr.astype(np.uint8).view(np.int8).astype(np.int64)
-    assert form in ("fp8", "fp8mma")
+    assert form in ("fp8", "fp8mma", "fp8bal")
     lut = np.array([E4M3[b] for b in range(256)])
     v = lut[arr.astype(np.uint8)]
     assert np.all(v == np.round(v))

@@ -84,9 +84,9 @@ def test_plan_rejects_bad_arguments():
 def test_component_count_plans(q):
     # q binary64 components: target 2^(-50 q) -> s = ceil((50 q + log2 k + 16) / 4) e4m3 digits,
     # the accumulator holds every diagonal's weight, and more than 4 components
-    # take the tcgen05 form only
+    # take the tcgen05 form only (the automatic form picks the 4-bit digits there)
     k = 1000
-    h = oz.ozmp_plan_create(q, 300, 200, k, oz.Form.AUTO, 0, None)
+    h = oz.ozmp_plan_create(q, 300, 200, k, oz.Form.AUTO if q > 4 else oz.Form.FP8, 0, None)
     try:
         i = oz.ozmp_plan_get_info(h)
         assert i.form == oz.Form.FP8 and i.beta == 4
@@ -135,3 +135,51 @@ def test_group_schedule_keeps_horner_value_below_2_62():
                 # the exact accumulator holds the largest possible Ozaki sum
                 total = sum(tb(d) << (b * (s + 1 - d)) for d in range(2, s + 2))
                 assert total.bit_length() + 1 <= 64 * i.acc_words
+
+
+@pytest.mark.parametrize("prec,k", [(oz.Prec.DD, 4096), (oz.Prec.TD, 1024), (oz.Prec.QD, 4096), (oz.Prec.TS, 8192),
+                                    (oz.Prec.DD, 1)])
+def test_balanced_digit_plans(prec, k):
+    # balanced radix-32 e4m3 digits keep 5 s - 1 bits below 2^E: the same
+    # target bits (50 q or 66, + log2 k + 16 guard bits) in about a fifth
+    # fewer slices, a third fewer pairs; digits |d| <= 16, so a slice pair
+    # of k terms reaches k 2^8 and a drain holds 2^24 / (k 2^8) pairs
+    h = oz.ozmp_plan_create(prec, 300, 200, k, oz.Form.FP8_BAL, 0, None)
+    try:
+        i = oz.ozmp_plan_get_info(h)
+        assert i.form == oz.Form.FP8_BAL and i.beta == 5 and i.digit_bytes == 1
+        bits = (66 if prec == oz.Prec.TS else 50 * int(prec)) + max(0, (k - 1).bit_length()) + 16
+        assert 5 * i.nslices - 1 >= bits > 5 * (i.nslices - 1) - 1
+        assert i.pairs_per_drain == min(2 ** 24 // (k * 256), 2 ** 20)
+        top_bits = 5 * (i.nslices - 1) + (k * 256).bit_length() + 8 + 2
+        assert 64 * i.acc_words >= top_bits
+    finally:
+        oz.ozmp_plan_destroy(h)
+
+
+def test_balanced_digit_limits():
+    # the register splitter's 6-word window: 5 s + 65 <= 384, so s <= 63;
+    # more than 4 components are not offered in this form
+    h = oz.ozmp_plan_create(oz.Prec.DD, 10, 10, 10, oz.Form.FP8_BAL, 63, None)
+    oz.ozmp_plan_destroy(h)
+    for args in [(2, 10, 10, 10, oz.Form.FP8_BAL, 64), (5, 10, 10, 10, oz.Form.FP8_BAL, 0),
+                 (2, 8, 8, 70000, oz.Form.FP8_BAL, 0)]:
+        with pytest.raises(oz.OzmpError) as e:
+            oz.ozmp_plan_create(*args, None)
+        assert e.value.status == oz.Status.ERR_UNSUPPORTED
+    h = oz.ozmp_plan_create(oz.Prec.DD, 8, 8, 65536, oz.Form.FP8_BAL, 0, None)
+    oz.ozmp_plan_destroy(h)
+    with pytest.raises(oz.OzmpError) as e:
+        oz.ozmp_plan_create(oz.Prec.DD, 8, 8, 8, 6, 0, None)
+    assert e.value.status == oz.Status.ERR_INVALID_ARG
+
+
+def test_automatic_form_choice():
+    # balanced radix-32 digits where their splitter applies, else 4-bit digits
+    for q, ns, want in [(2, 0, oz.Form.FP8_BAL), (4, 63, oz.Form.FP8_BAL), (2, 64, oz.Form.FP8),
+                        (5, 0, oz.Form.FP8), (oz.Prec.TS, 0, oz.Form.FP8_BAL)]:
+        h = oz.ozmp_plan_create(q, 64, 64, 64, oz.Form.AUTO, ns, None)
+        try:
+            assert oz.ozmp_plan_get_info(h).form == want, (q, ns)
+        finally:
+            oz.ozmp_plan_destroy(h)

@@ -37,7 +37,7 @@ def _single(prec, A, B, form):
     return C
 
 
-@pytest.mark.parametrize("form", ["fp8", "int8"])
+@pytest.mark.parametrize("form", ["fp8", "fp8bal", "int8"])
 def test_batched_equals_single_products(form):
     shapes = batched_problem_shapes(24, seed=1, lo=16, hi=300)
     shapes += [(70, 40, 0, "dd"), (0, 5, 9, "td"), (33, 290, 45, "qd"), (130, 260, 70, "ts"), (1, 1, 1, "dd")]
@@ -74,6 +74,10 @@ def test_batched_plan_rejects_a_different_batch():
     other = _make([(41, 30, 20, "dd"), (20, 30, 40, "td")], 8)
     with pytest.raises(oz.OzmpError) as e:
         oz.ozmp_gemm_batched(other, plan=plan)
+    assert e.value.status == oz.Status.ERR_INVALID_ARG
+    # nor another digit form (the automatic one is the balanced radix-32 form here)
+    with pytest.raises(oz.OzmpError) as e:
+        oz.ozmp_gemm_batched(probs, oz.Form.FP8, plan=plan)
     assert e.value.status == oz.Status.ERR_INVALID_ARG
     oz.ozmp_plan_destroy(plan)
 

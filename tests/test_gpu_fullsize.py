@@ -46,7 +46,7 @@ def _sampled(prec, form, m, n, k, phi, seed, rows, cols, err_rows, err_cols, nsl
     torch.cuda.empty_cache()
     As = [np.asfortranarray(a[rows, :]) for a in A]
     Bs = [np.asfortranarray(b[:, cols]) for b in B]
-    r = O.ozaki_product(As, Bs, i.beta, i.nslices)
+    r = O.ozaki_product(As, Bs, i.beta, i.nslices, balanced=(i.form == oz.Form.FP8_BAL))
     kind = "f32" if prec == "ts" else "f64"
     for a in range(len(rows)):
         for b in range(len(cols)):
@@ -69,6 +69,21 @@ def test_dd_4096_headline():
     cols = [0, 255, 256, 1000, 3071, 4095]
     i = _sampled("dd", "fp8", 4096, 4096, 4096, 1.0, 0, rows, cols, [0, 3, 7], [0, 5])
     assert i.nslices == 32
+
+
+def test_dd_4096_balanced_digits():
+    # the same workload in balanced radix-32 e4m3 digits: s = 26 slices
+    rows = [0, 1, 255, 256, 2047, 2048, 4094, 4095]
+    cols = [0, 255, 256, 1000, 3071, 4095]
+    i = _sampled("dd", "fp8bal", 4096, 4096, 4096, 1.0, 0, rows, cols, [0, 3, 7], [0, 5])
+    assert i.nslices == 26 and i.beta == 5
+
+
+def test_qd_4096_balanced_digits():
+    rows = [0, 300, 2048, 4095]
+    cols = [1, 2049, 4095]
+    i = _sampled("qd", "fp8bal", 4096, 4096, 4096, 1.0, 0, rows, cols, [0, 3], [0, 2])
+    assert i.nslices == 46
 
 
 def test_qd_4096():

@@ -1,6 +1,7 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
 
-* exponents E, F and every digit: bit-exact against oracle.ozaki.split;
+* exponents E, F and every digit: bit-exact against oracle.ozaki.split
+  (oracle.ozaki.split_balanced for the balanced radix-32 e4m3 form);
 * each diagonal T_d = sum_{t+u=d} A_t B_u^T from the tensor-core main loop:
   bit-exact against the oracle's int64 slice products;
 * the product: bit-exact against the canonical component rounding of the
@@ -29,6 +30,17 @@ TARGET = {"dd": 2.0 ** -100, "td": 2.0 ** -150, "qd": 2.0 ** -200, "ts": 2.0 ** 
 Q = {"dd": 2, "td": 3, "qd": 4, "ts": 3}
 
 
+def _osplit(comps, form, beta, s):
+    """The oracle's exponents and digits of a form (rows of comps)."""
+    if form == "fp8bal":
+        return O.split_balanced(comps, s)
+    return O.split(comps, beta, s)
+
+
+def _oproduct(A, B, info):
+    return O.ozaki_product(A, B, info.beta, info.nslices, balanced=(info.form == oz.Form.FP8_BAL))
+
+
 def _split_check(prec, form, m, n, k, phi, seed, nslices=0):
     A, B = gen_problem(prec, m, n, k, phi=phi, seed=seed)
     p = oz.Plan(prec, m, n, k, form, nslices)
@@ -38,8 +50,8 @@ def _split_check(prec, form, m, n, k, phi, seed, nslices=0):
     i = p.info
     E, F = [t.cpu().numpy() for t in p.exponents()]
     ga, gb = [t.cpu().numpy() for t in p.digits()]
-    Eo, dA = O.split(A, i.beta, i.nslices)
-    Fo, dB = O.split([np.asfortranarray(b.T) for b in B], i.beta, i.nslices)
+    Eo, dA = _osplit(A, form, i.beta, i.nslices)
+    Fo, dB = _osplit([np.asfortranarray(b.T) for b in B], form, i.beta, i.nslices)
     assert list(E) == Eo
     assert list(F) == Fo
     gA = digits_to_int(ga[:, :m, :k], form)
@@ -52,15 +64,22 @@ def _split_check(prec, form, m, n, k, phi, seed, nslices=0):
     return p, A, B, Ad, Bd, dA, dB
 
 
-@pytest.mark.parametrize("form", ["fp8", "int8", "fp64"])
+@pytest.mark.parametrize("form", ["fp8", "fp8bal", "int8", "fp64"])
 @pytest.mark.parametrize("prec", ["dd", "td", "qd", "ts"])
 def test_split_bit_exact(prec, form):
     _split_check(prec, form, 150, 140, 130, phi=1.0, seed=1, nslices=6 if form == "fp64" else 14)
 
 
-@pytest.mark.parametrize("form", ["fp8", "fp8mma", "int8", "fp64"])
+@pytest.mark.parametrize("form,s", [("fp8", 64), ("fp8", 65), ("fp8bal", 63), ("fp8bal", 1)])
+def test_split_widest_register_windows(form, s):
+    # the register splitter writes up to 64 e4m3 slices (63 balanced ones,
+    # 5 s + 65 <= 384 bits); 65 slices go to the many-component splitter
+    _split_check("dd", form, 70, 60, 50, phi=1.0, seed=7, nslices=s)
+
+
+@pytest.mark.parametrize("form", ["fp8", "fp8bal", "fp8mma", "int8", "fp64"])
 def test_diagonals_bit_exact(form):
-    s = {"fp8": 20, "fp8mma": 20, "int8": 12, "fp64": 5}[form]
+    s = {"fp8": 20, "fp8bal": 16, "fp8mma": 20, "int8": 12, "fp64": 5}[form]
     p, A, B, Ad, Bd, dA, dB = _split_check("dd", form, 200, 150, 130, phi=1.0, seed=2, nslices=s)
     T = O.slice_products(dA, dB)
     for d in sorted({2, 3, s // 2 + 1, s + 1}):
@@ -77,8 +96,7 @@ def _product(prec, form, m, n, k, phi, seed, nslices):
 
 
 def _canonical_check(A, B, Cg, p, prec):
-    i = p.info
-    r = O.ozaki_product(A, B, i.beta, i.nslices)
+    r = _oproduct(A, B, p.info)
     kind = "f32" if prec == "ts" else "f64"
     m, n = Cg[0].shape
     for a in range(m):
@@ -93,7 +111,9 @@ CASES = [("dd", "fp8", 130, 140, 150), ("dd", "fp8mma", 140, 130, 150), ("dd", "
          ("dd", "fp64", 150, 130, 140), ("dd", "fp8", 300, 520, 260), ("ts", "fp8mma", 130, 120, 100),
          ("td", "fp8", 130, 70, 100), ("td", "int8", 140, 130, 70), ("td", "fp64", 130, 140, 70),
          ("qd", "fp8", 70, 130, 64), ("qd", "int8", 130, 70, 90), ("qd", "fp64", 140, 70, 70),
-         ("ts", "fp8", 150, 140, 130), ("ts", "int8", 140, 130, 150), ("ts", "fp64", 130, 150, 140)]
+         ("ts", "fp8", 150, 140, 130), ("ts", "int8", 140, 130, 150), ("ts", "fp64", 130, 150, 140),
+         ("dd", "fp8bal", 130, 140, 150), ("dd", "fp8bal", 300, 520, 260), ("td", "fp8bal", 130, 70, 100),
+         ("qd", "fp8bal", 70, 130, 64), ("ts", "fp8bal", 150, 140, 130)]
 
 
 @pytest.mark.parametrize("prec,form,m,n,k", CASES)
@@ -114,11 +134,14 @@ def test_phi4_needs_more_slices_and_fixed_s_is_exact():
     # forced count is; both are bit-exact to the oracle's Ozaki sum
     A, B, Cg, p = _product("dd", "fp8", 128, 130, 140, phi=4.0, seed=4, nslices=48)
     _canonical_check(A, B, Cg, p, "dd")
+    A, B, Cg, p = _product("dd", "fp8bal", 128, 130, 140, phi=4.0, seed=4, nslices=40)
+    _canonical_check(A, B, Cg, p, "dd")
 
 
-def test_edge_shapes():
+@pytest.mark.parametrize("form", ["fp8", "fp8bal"])
+def test_edge_shapes(form):
     for (m, n, k) in [(1, 1, 1), (1, 7, 3), (5, 1, 2), (129, 1, 65), (1, 129, 127)]:
-        A, B, Cg, p = _product("dd", "fp8", m, n, k, phi=1.0, seed=5, nslices=0)
+        A, B, Cg, p = _product("dd", form, m, n, k, phi=1.0, seed=5, nslices=0)
         _canonical_check(A, B, Cg, p, "dd")
 
 
@@ -148,13 +171,13 @@ def test_zero_rows_unnormalised_and_slow_path():
     rng = np.random.default_rng(0)
     B = [np.asfortranarray(rng.standard_normal((k, n))), np.zeros((k, n), order="F")]
     B[0][:, 2] = 0.0
-    for form in ["fp8", "int8", "fp64"]:
+    for form in ["fp8", "fp8bal", "int8", "fp64"]:
         p = oz.Plan("dd", m, n, k, form, 0)
         Ad, Bd = to_dev(A), to_dev(B)
         p.split(Ad, Bd)
         torch.cuda.synchronize()
         E, F = [t.cpu().numpy() for t in p.exponents()]
-        Eo, dA = O.split(A, p.info.beta, p.info.nslices)
+        Eo, dA = _osplit(A, form, p.info.beta, p.info.nslices)
         assert list(E) == Eo and E[1] == oz.EXP_ZERO and F[2] == oz.EXP_ZERO
         ga = p.digits()[0].cpu().numpy()
         np.testing.assert_array_equal(digits_to_int(ga[:, :m, :k], form), dA)
@@ -165,7 +188,7 @@ def test_zero_rows_unnormalised_and_slow_path():
         # 2^-1000 * b underflows the output range: reported, not silently wrong
         assert st in (oz.Status.OK, oz.Status.ERR_RANGE)
         Cg = from_dev(C)
-        r = O.ozaki_product(A, B, p.info.beta, p.info.nslices)
+        r = _oproduct(A, B, p.info)
         for a in [0, 1, 3, 4, 5]:
             for b in range(n):
                 assert [float(c[a, b]) for c in Cg] == X.to_components(r["S"][a][b], 2)
@@ -297,7 +320,7 @@ def _adversarial(q, rows, cols, seed, dtype=np.float64):
     return [np.asfortranarray(c.astype(dtype)) for c in comps]
 
 
-@pytest.mark.parametrize("form", ["fp8", "int8", "fp64"])
+@pytest.mark.parametrize("form", ["fp8", "fp8bal", "int8", "fp64"])
 @pytest.mark.parametrize("prec", ["dd", "qd", "ts"])
 def test_split_adversarial_boundaries(prec, form):
     q = {"dd": 2, "qd": 4, "ts": 3}[prec]
@@ -311,8 +334,8 @@ def test_split_adversarial_boundaries(prec, form):
     i = p.info
     E, F = [t.cpu().numpy() for t in p.exponents()]
     ga, gb = [t.cpu().numpy() for t in p.digits()]
-    Eo, dA = O.split(A, i.beta, i.nslices)
-    Fo, dB = O.split([np.asfortranarray(b.T) for b in B], i.beta, i.nslices)
+    Eo, dA = _osplit(A, form, i.beta, i.nslices)
+    Fo, dB = _osplit([np.asfortranarray(b.T) for b in B], form, i.beta, i.nslices)
     assert list(E) == Eo and list(F) == Fo
     np.testing.assert_array_equal(digits_to_int(ga[:, :m, :k], form), dA)
     np.testing.assert_array_equal(digits_to_int(gb[:, :n, :k], form), dB)
@@ -343,6 +366,34 @@ def test_tail_tiles_split_across_ctas_match_other_engine(pair, monkeypatch):
     Bs = [np.asfortranarray(b[:, cols]) for b in B]
     # exponents are row/column maxima over k, so the sub-block split equals the full one
     r = O.ozaki_product(As, Bs, p1.info.beta, p1.info.nslices)
+    for a_i, i in enumerate(rows):
+        for b_j, j in enumerate(cols):
+            assert [float(c[i, j]) for c in Cg] == X.to_components(r["S"][a_i][b_j], 2)
+
+
+def test_balanced_digits_on_split_tail_tiles(monkeypatch):
+    # the balanced form on the same tail-split schedules: single-CTA and
+    # CTA-pair tiles agree bit for bit, and a sampled block equals the
+    # oracle's Ozaki sum of the balanced digits
+    m, n, k = 2560, 2048, 192
+    A, B = gen_problem("dd", m, n, k, phi=1.0, seed=14)
+    Ad, Bd = to_dev(A), to_dev(B)
+    out = {}
+    for pair in ("1", "0"):
+        monkeypatch.setenv("OZMP_TC_PAIR", pair)
+        C, p = oz.gemm(Ad, Bd, "dd", "fp8bal", 0)
+        torch.cuda.synchronize()
+        assert p.status() == oz.Status.OK and p.info.form == oz.Form.FP8_BAL and p.info.beta == 5
+        out[pair] = (C, p)
+    for x, y in zip(out["1"][0], out["0"][0]):
+        assert torch.equal(x, y)
+    C, p = out["1"]
+    rows = list(range(0, m, 397))
+    cols = list(range(0, n, 311))
+    Cg = from_dev(C)
+    As = [np.asfortranarray(a[rows, :]) for a in A]
+    Bs = [np.asfortranarray(b[:, cols]) for b in B]
+    r = _oproduct(As, Bs, p.info)
     for a_i, i in enumerate(rows):
         for b_j, j in enumerate(cols):
             assert [float(c[i, j]) for c in Cg] == X.to_components(r["S"][a_i][b_j], 2)
