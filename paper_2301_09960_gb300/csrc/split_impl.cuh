@@ -218,6 +218,16 @@ __host__ __device__ constexpr uint64_t bal_sixteens(int nw, int j) {
     return r;
 }
 
+// the words of that pattern as a constant table (evaluated by the compiler:
+// a constexpr function called in a run-time expression need not be)
+template <int NW>
+struct BalSixteens {
+    uint64_t w[NW];
+    constexpr BalSixteens() : w() {
+        for (int j = 0; j < NW; ++j) w[j] = bal_sixteens(NW, j);
+    }
+};
+
 // The balanced radix-32 e4m3 digits of four elements (consecutive k), all
 // slices: calls put(t, word) for t = 1 .. s with byte e of `word` = e4m3 code
 // of digit t of element e.  The magnitude window holds
@@ -234,11 +244,12 @@ template <int NW, typename Put>
 __device__ __forceinline__ void pack_bal_quad(uint64_t (&w)[4][NW], const int (&sign)[4], int s, Put&& put) {
     constexpr int TMAX = (64 * NW - 65) / 5;
     const int lo = 64 * NW - 5 * s;   // lowest bit of the lowest group (>= 65)
+    constexpr BalSixteens<NW> P16;
     uint64_t H[NW];
 #pragma unroll
     for (int j = 0; j < NW; ++j) {
         const uint64_t keep = (lo <= 64 * j) ? ~0ull : (lo >= 64 * j + 64 ? 0ull : (~0ull << (lo - 64 * j)));
-        H[j] = bal_sixteens(NW, j) & keep;
+        H[j] = P16.w[j] & keep;
     }
     uint32_t top[4];
 #pragma unroll
