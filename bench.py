@@ -448,11 +448,12 @@ def main():
     Bh = [torch.from_numpy(b.T.copy()).pin_memory() for b in B]
     Ch = [torch.empty((n, m), dtype=dt).pin_memory() for _ in range(q)]
     # Steps are independent products, so they are pipelined as a serving
-    # loop would: the product of step i runs on the compute stream while the
-    # copy stream brings in step i+1's operands and takes out step i-1's
-    # result; device operands and results are double-buffered.  Every step
-    # still copies its inputs in from pinned host memory and its result out
-    # inside the timed region.
+    # loop would: the product of step i runs on the compute stream while one
+    # copy stream brings in step i+1's operands and another takes out step
+    # i-1's result (two streams, so that an upload never queues behind a
+    # download that waits for a product); device operands and results are
+    # double-buffered.  Every step still copies its inputs in from pinned
+    # host memory and its result out inside the timed region.
     bufs = [([torch.empty((k, m), dtype=dt, device="cuda") for _ in range(q)],
              [torch.empty((n, k), dtype=dt, device="cuda") for _ in range(q)],
              [torch.empty((n, m), dtype=dt, device="cuda") for _ in range(q)]) for _ in range(2)]
@@ -460,7 +461,7 @@ def main():
     d2h = sum(t.numel() * t.element_size() for t in Ch)
     e2e_steps = max(1, min(args.steps, 10))
     comp = torch.cuda.current_stream()
-    cs = torch.cuda.Stream()
+    cs_in, cs_out = torch.cuda.Stream(), torch.cuda.Stream()
     ev_in = [torch.cuda.Event() for _ in range(2)]
     ev_done = [torch.cuda.Event() for _ in range(2)]
     ev_out = [torch.cuda.Event() for _ in range(2)]
@@ -469,24 +470,24 @@ def main():
     def e2e_step(i):
         sidx = i % 2
         Ad2, Bd2, Cd2 = bufs[sidx]
-        with torch.cuda.stream(cs):
+        with torch.cuda.stream(cs_in):
             if used[sidx]:
-                cs.wait_event(ev_done[sidx])        # the product that last read this set
+                cs_in.wait_event(ev_done[sidx])     # the product that last read this set
             for x, y in zip(Ad2, Ah):
                 x.copy_(y, non_blocking=True)
             for x, y in zip(Bd2, Bh):
                 x.copy_(y, non_blocking=True)
-            ev_in[sidx].record(cs)
+            ev_in[sidx].record(cs_in)
         comp.wait_event(ev_in[sidx])
         if used[sidx]:
             comp.wait_event(ev_out[sidx])           # the result of this set has been read out
         plan.execute([x.T for x in Ad2], [x.T for x in Bd2], [x.T for x in Cd2])
         ev_done[sidx].record(comp)
-        with torch.cuda.stream(cs):
-            cs.wait_event(ev_done[sidx])
+        with torch.cuda.stream(cs_out):
+            cs_out.wait_event(ev_done[sidx])
             for x, y in zip(Ch, Cd2):
                 x.copy_(y, non_blocking=True)
-            ev_out[sidx].record(cs)
+            ev_out[sidx].record(cs_out)
         used[sidx] = True
 
     e2e_step(0)
@@ -551,8 +552,8 @@ def main():
         "stage_ms": {"split": split_ms, "products": gemm_ms, "product_kernel": kernel_ms},
         "e2e": {"value": e2e_val, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_ms, "steps": e2e_steps,
-                "pipelined": "operands of step i+1 copied in and the result of step i-1 copied out on a second "
-                             "stream during step i's product (double-buffered device operands)"},
+                "pipelined": "operands of step i+1 copied in and the result of step i-1 copied out on two copy "
+                             "streams during step i's product (double-buffered device operands)"},
         # per step: 5 split kernels (exponent init, row and column exponents, row and
         # column digits) + the slice-product kernel + (tcgen05 form) its rounding pass
         "gpu_launches": (7 if oz.Form(info.form) in (oz.Form.FP8, oz.Form.FP8_BAL) else 6) * args.steps,
@@ -582,36 +583,46 @@ def main():
                          "vs": "exact product rounded to 512 bits, same block", "target": 2.0 ** -100}
 
     if rank == 0 and ws == 1 and not args.no_variants:
-        del Ad, Bd, C, Ad2, Bd2, Cd2
+        del Ad, Bd, C, bufs, plan
         torch.cuda.empty_cache()
-        var = []
-        for vp, vf in [("dd", "fp8"), ("dd", "fp8mma"), ("dd", "int8"), ("dd", "fp64"), ("qd", "fp8bal"),
-                       ("qd", "fp8"), ("qd", "fp8mma"), ("qd", "int8"), ("qd", "fp64")]:
-            try:
-                var.append(run_variant(oz, torch, vp, vf, args.n, args.phi, 1, 1))
-            except Exception as ex:  # report, do not hide
-                var.append({"prec": vp, "form": vf, "error": repr(ex)[:200]})
-        line["variants"] = var
-        # more components (Sec. 5's multiple precisions beyond QD): q binary64
-        # words, about 53 q bits, target 2^(-50 q); one timed pass at 2048^3
-        md = []
-        for q in (8, 16):
-            try:
-                r = run_variant(oz, torch, f"q{q}", "fp8", 2048, args.phi, 1, 1)
-                r["bits"] = 53 * q
-                md.append(r)
-            except Exception as ex:
-                md.append({"prec": f"q{q}", "form": "fp8", "error": repr(ex)[:200]})
-        line["multiprecision_2048"] = md
-        line["lu_4096"] = lu_variant(oz, torch)
-        line["literal_vs_truncating_1024"] = literal_variant(oz, torch)
-        line["config2_td_qd_1024"] = config2(oz, torch)
-        line["config4_batched512"] = config4(oz, torch)
+        try:
+            add_variants(line, oz, torch, args)
+        except Exception as ex:  # the headline line is printed whatever a side measurement does
+            line["variants_error"] = repr(ex)[:300]
 
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
+
+
+def add_variants(line, oz, torch, args):
+    """Side measurements of the default run (rank 0, one GPU): the other
+    forms and precisions, more components, LU, Algorithm 1 as printed, TD/QD
+    at 1024 and the batched problems."""
+    var = []
+    for vp, vf in [("dd", "fp8"), ("dd", "fp8mma"), ("dd", "int8"), ("dd", "fp64"), ("qd", "fp8bal"),
+                   ("qd", "fp8"), ("qd", "fp8mma"), ("qd", "int8"), ("qd", "fp64")]:
+        try:
+            var.append(run_variant(oz, torch, vp, vf, args.n, args.phi, 1, 1))
+        except Exception as ex:  # report, do not hide
+            var.append({"prec": vp, "form": vf, "error": repr(ex)[:200]})
+    line["variants"] = var
+    # more components (Sec. 5's multiple precisions beyond QD): q binary64
+    # words, about 53 q bits, target 2^(-50 q); one timed pass at 2048^3
+    md = []
+    for q in (8, 16):
+        try:
+            r = run_variant(oz, torch, f"q{q}", "fp8", 2048, args.phi, 1, 1)
+            r["bits"] = 53 * q
+            md.append(r)
+        except Exception as ex:
+            md.append({"prec": f"q{q}", "form": "fp8", "error": repr(ex)[:200]})
+    line["multiprecision_2048"] = md
+    line["lu_4096"] = lu_variant(oz, torch)
+    line["literal_vs_truncating_1024"] = literal_variant(oz, torch)
+    line["config2_td_qd_1024"] = config2(oz, torch)
+    line["config4_batched512"] = config4(oz, torch)
 
 
 if __name__ == "__main__":
