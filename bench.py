@@ -516,13 +516,12 @@ def main():
     else:
         peak, peak_note = 1.05, "DMMA mma.sync f64 microbenchmark on this GB300 (no MEASURED_PEAKS entry)"
     sbytes = splitter_bytes(q, w, m, n, k, info.nslices, info.digit_bytes)
-    # DRAM bytes per launch of the product kernel, from the ncu capture in
-    # profiles/k_gemm_tc_bal_dd4096_s12.md (the same kernel and operands with
-    # 12 slices: 78 pairs, 12 drains per tile) scaled to this launch: operand
-    # reads by pairs, limb writes by drains; only for the workload captured there
+    # DRAM bytes (read + write) of one launch of the product kernel, from the
+    # one-pass ncu capture of this workload's launch in
+    # profiles/k_gemm_tc_bal_dd4096_s12.md; only for the workload captured there
     traffic = None
     if oz.Form(info.form) == oz.Form.FP8_BAL and prec == "dd" and m == n == k == 4096 and info.nslices == 26:
-        traffic = 9.353e9 * info.npairs / 78 + 1.609e9 * 36 / 12
+        traffic = 67.429e9 + 5.014e9
 
     line = {
         "metric": metric, "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
