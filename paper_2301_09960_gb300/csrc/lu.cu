@@ -93,6 +93,11 @@ __device__ __forceinline__ void stage(const Mat& A, int n, double* S) {
 // of U then column k of L, each entry one exact dot product rounded once
 // (a warp per entry, its lanes sharing the terms);
 // l_ik = RN_q(RN_q(a_ik - sum) * RN_q(1 / u_kk)).
+// The numerators of column k use only finished entries (l_it, u_tk, t < k),
+// so one pass computes them beside row k of U; the warp that finishes u_kk
+// computes its reciprocal while the other warps go on, and every l_ik is
+// then one multiplication, all in parallel.  The values are those of the
+// sequential order.
 constexpr int LU_WARPS = 16;
 
 template <int Q>
@@ -107,43 +112,40 @@ __global__ void __launch_bounds__(32 * LU_WARPS) k_base_lu(Mat A, int n, uint32_
     bool bad = false;
     double out[Q];
     for (int k = 0; k < n; ++k) {
-        // row k of U: u_kj = a_kj - sum_{t<k} l_kt u_tj, j = k .. n-1
-        for (int j = k + warp; j < n; j += LU_WARPS) {
+        // entries e < n - k: u_kj, j = k + e (e = 0 first: its warp then takes
+        // the reciprocal); entries e >= n - k: the numerator of l_ik,
+        // i = k + 1 + (e - (n - k)), stored in place of a_ik
+        const int nu = n - k, ne = 2 * (n - k) - 1;
+        for (int e = warp; e < ne; e += LU_WARPS) {
+            const bool urow = e < nu;
+            const int i = urow ? k : k + 1 + (e - nu);
+            const int j = urow ? k + e : k;
             xacc::warp_exact_round<W<Q>::NW>(Q, [&](auto& v, int part) {
                 if (part == 0)
-                    for (int c = 0; c < Q; ++c) v.value(S[SIDX(c, k, j)]);
+                    for (int c = 0; c < Q; ++c) v.value(S[SIDX(c, i, j)]);
                 for (int t = part; t < k; t += 32)
                     for (int c1 = 0; c1 < Q; ++c1)
-                        for (int c2 = 0; c2 < Q; ++c2) v.product(S[SIDX(c1, k, t)], S[SIDX(c2, t, j)], true);
+                        for (int c2 = 0; c2 < Q; ++c2) v.product(S[SIDX(c1, i, t)], S[SIDX(c2, t, j)], true);
             }, out, bad);
-            if (lane == 0)
-#pragma unroll
-                for (int c = 0; c < Q; ++c) S[SIDX(c, k, j)] = out[c];
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double d[Q];
-#pragma unroll
-            for (int c = 0; c < Q; ++c) d[c] = S[SIDX(c, k, k)];
-            if (d[0] == 0.0) bad = true;
-            else recip_q<Q>(d, R, bad);
-        }
-        __syncthreads();
-        // column k of L: l_ik = (a_ik - sum_{t<k} l_it u_tk) / u_kk, i = k+1 .. n-1
-        for (int i = k + 1 + warp; i < n; i += LU_WARPS) {
-            double num[Q];
-            xacc::warp_exact_round<W<Q>::NW>(Q, [&](auto& v, int part) {
-                if (part == 0)
-                    for (int c = 0; c < Q; ++c) v.value(S[SIDX(c, i, k)]);
-                for (int t = part; t < k; t += 32)
-                    for (int c1 = 0; c1 < Q; ++c1)
-                        for (int c2 = 0; c2 < Q; ++c2) v.product(S[SIDX(c1, i, t)], S[SIDX(c2, t, k)], true);
-            }, num, bad);
             if (lane == 0) {
-                mul_round<Q>(num, R, out, bad);
 #pragma unroll
-                for (int c = 0; c < Q; ++c) S[SIDX(c, i, k)] = out[c];
+                for (int c = 0; c < Q; ++c) S[SIDX(c, i, j)] = out[c];
+                if (e == 0) {
+                    if (out[0] == 0.0) bad = true;
+                    else recip_q<Q>(out, R, bad);
+                }
             }
+            __syncwarp();
+        }
+        __syncthreads();
+        // column k of L: l_ik = RN_q(num_ik * r), one thread per entry
+        for (int i = k + 1 + (int)threadIdx.x; i < n; i += (int)blockDim.x) {
+            double num[Q], rr[Q];
+#pragma unroll
+            for (int c = 0; c < Q; ++c) { num[c] = S[SIDX(c, i, k)]; rr[c] = R[c]; }
+            mul_round<Q>(num, rr, out, bad);
+#pragma unroll
+            for (int c = 0; c < Q; ++c) S[SIDX(c, i, k)] = out[c];
         }
         __syncthreads();
     }
