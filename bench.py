@@ -23,7 +23,7 @@ Printed: one JSON line (rank 0).  Besides the contract keys it carries
                    (DD and QD; balanced and 4-bit e4m3 / int8 / binary64
                    digits) at 4096^3;
   multiprecision_2048 -- 8 and 16 binary64 components (424 / 848 bits)
-                   at 2048^3, e4m3 digits on tcgen05;
+                   at 2048^3, balanced and 4-bit e4m3 digits on tcgen05;
   lu_4096       -- the LU application: DD n = 4096 and TD n = 2048 LU
                    without pivoting on Ozaki products, and the solve;
   literal_vs_truncating_1024 -- Algorithm 1 as printed against the
@@ -611,12 +611,13 @@ def add_variants(line, oz, torch, args):
     # words, about 53 q bits, target 2^(-50 q); one timed pass at 2048^3
     md = []
     for q in (8, 16):
-        try:
-            r = run_variant(oz, torch, f"q{q}", "fp8", 2048, args.phi, 1, 1)
-            r["bits"] = 53 * q
-            md.append(r)
-        except Exception as ex:
-            md.append({"prec": f"q{q}", "form": "fp8", "error": repr(ex)[:200]})
+        for form in ("fp8bal", "fp8"):
+            try:
+                r = run_variant(oz, torch, f"q{q}", form, 2048, args.phi, 1, 1)
+                r["bits"] = 53 * q
+                md.append(r)
+            except Exception as ex:
+                md.append({"prec": f"q{q}", "form": form, "error": repr(ex)[:200]})
     line["multiprecision_2048"] = md
     line["lu_4096"] = lu_variant(oz, torch)
     line["literal_vs_truncating_1024"] = literal_variant(oz, torch)

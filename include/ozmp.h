@@ -74,7 +74,7 @@ typedef enum { OZMP_DD = 2, OZMP_TD = 3, OZMP_QD = 4, OZMP_TS = 103 } ozmp_prec;
 
 /* digit form of the slice products */
 typedef enum {
-    OZMP_FORM_AUTO = 0,     /* fastest exact form on this GPU: FP8_BAL for q <= 4 and s <= 63, else FP8 */
+    OZMP_FORM_AUTO = 0,     /* fastest exact form on this GPU: FP8_BAL up to 191 slices, else FP8 */
     OZMP_FORM_FP64 = 1,     /* binary64 digits, beta = max{b: k (2^b - 1)^2 <= 2^53}, DMMA */
     OZMP_FORM_INT8 = 2,     /* int8 digits, beta = 7, IMMA int32 accumulation */
     OZMP_FORM_FP8  = 3,     /* e4m3 digits, beta = 4, tcgen05 kind::f8f6f4, binary32 accumulation in TMEM */
@@ -87,9 +87,9 @@ typedef enum {
 /* all-zero row/column exponent */
 #define OZMP_EXP_ZERO ((int32_t)(-2147483647 - 1))
 /* largest slice count accepted as an argument; each form provides fewer:
- * FP8 (tcgen05) up to 239 (beta s + 65 <= 1024 window bits), FP8_BAL 63,
- * FP8_MMA 64, INT8 36, FP64 up to beta s <= 376; above the form's limit
- * plan creation returns OZMP_ERR_UNSUPPORTED */
+ * FP8 (tcgen05) up to 239 and FP8_BAL up to 191 (beta s + 65 <= 1024 window
+ * bits), FP8_MMA 64, INT8 36, FP64 up to beta s <= 376; above the form's
+ * limit plan creation returns OZMP_ERR_UNSUPPORTED */
 #define OZMP_MAX_SLICES 256
 
 /* cudaStream_t, passed as an opaque pointer (NULL = the legacy default stream) */
@@ -219,8 +219,8 @@ ozmp_status ozmp_gemm_dd_noalloc(int64_t m, int64_t n, int64_t k, const double* 
  *   ozmp_plan_get_status (one word for the whole batch).
  * The problem array and the component-pointer arrays it points to are read
  * during the call only.  Batched problems hold at most 4 components and
- * 64 slices (else OZMP_ERR_UNSUPPORTED); larger ones go through
- * single-problem plans.  form FP8_BAL runs every problem in balanced
+ * 64 four-bit or 63 balanced slices (else OZMP_ERR_UNSUPPORTED); larger ones
+ * go through single-problem plans.  form FP8_BAL runs every problem in balanced
  * radix-32 digits; a plan is reused only with the form it was made for.
  */
 typedef struct {

@@ -55,6 +55,27 @@ __device__ __forceinline__ bool decode(float x, Comp& c) {
 
 __device__ __forceinline__ int bitlen(uint64_t x) { return 64 - __clzll((long long)x); }
 
+// bit 4 of every 5-bit digit group t = 1, 2, ... of a top-aligned window
+// (group t at bits [64 NW - 5 t, 64 NW - 5 t + 5)), word j
+__host__ __device__ constexpr uint64_t bal_sixteens(int nw, int j) {
+    uint64_t r = 0;
+    for (int t = 1; 64 * nw - 5 * t >= 0; ++t) {
+        const int b = 64 * nw - 5 * t + 4;
+        if (b >= 64 * j && b < 64 * j + 64) r |= 1ull << (b - 64 * j);
+    }
+    return r;
+}
+
+// the words of that pattern as a constant table (evaluated by the compiler:
+// a constexpr function called in a run-time expression need not be)
+template <int NW>
+struct BalSixteens {
+    uint64_t w[NW];
+    constexpr BalSixteens() : w() {
+        for (int j = 0; j < NW; ++j) w[j] = bal_sixteens(NW, j);
+    }
+};
+
 // ----------------------------------------------------------------------------
 // multiword two's complement helpers (NW words, word 0 least significant)
 // ----------------------------------------------------------------------------

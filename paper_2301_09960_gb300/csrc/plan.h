@@ -338,9 +338,9 @@ inline ozmp_status plan_init(ozmp_plan_s* p, int prec, int64_t m, int64_t n, int
     p->q = q;
     p->is_f32 = (prec == OZMP_TS);
     // balanced digits run on the tcgen05 engine of the e4m3 form, beta = 5;
-    // the automatic form takes them wherever their splitter applies (q <= 4,
-    // s <= 63), else the 4-bit digits
-    p->bal = (form == OZMP_FORM_FP8_BAL || (form == OZMP_FORM_AUTO && q <= 4 && nslices <= 63)) ? 1 : 0;
+    // the automatic form takes them up to their largest slice count (191),
+    // and the 4-bit digits beyond it
+    p->bal = (form == OZMP_FORM_FP8_BAL || (form == OZMP_FORM_AUTO && nslices <= (1024 - 65) / 5)) ? 1 : 0;
     p->form = (form == OZMP_FORM_AUTO || p->bal) ? OZMP_FORM_FP8 : form;
     p->m = m; p->n = n; p->k = k;
     p->beta = (p->form == OZMP_FORM_FP64) ? beta_fp64(k)
@@ -353,10 +353,8 @@ inline ozmp_status plan_init(ozmp_plan_s* p, int prec, int64_t m, int64_t n, int
     // splitter up to beta s + 65 <= 1024 (16-word windows)
     const bool tc = (p->form == OZMP_FORM_FP8);
     if (q > 4 && !tc) return OZMP_ERR_UNSUPPORTED;
-    // balanced digits: the register-resident splitter only (q <= 4, 6-word windows)
-    if (p->bal && q > 4) return OZMP_ERR_UNSUPPORTED;
-    const int maxs = p->bal ? (6 * 64 - 65) / 5 : tc ? (1024 - 65) / 4 : (p->form == OZMP_FORM_INT8 ? 36 : 64);
-    const int maxbits = p->bal ? 6 * 64 - 65 : tc ? 1024 - 65 : 376;
+    const int maxs = tc ? (1024 - 65) / p->beta : (p->form == OZMP_FORM_INT8 ? 36 : 64);
+    const int maxbits = tc ? 1024 - 65 : 376;
     if (nslices == 0) {
         int bits = prec_target_bits(prec) + ceil_log2(k > 0 ? k : 1) + 16;
         // balanced digits keep 5 s - 1 bits below 2^E (the top digit is at most 16)
@@ -366,7 +364,7 @@ inline ozmp_status plan_init(ozmp_plan_s* p, int prec, int64_t m, int64_t n, int
     }
     if (nslices > maxs || nslices * p->beta > maxbits) return OZMP_ERR_UNSUPPORTED;
     p->s = nslices;
-    p->big = (!p->bal && (q > 4 || nslices > 64)) ? 1 : 0;
+    p->big = (q > 4 || nslices > (p->bal ? 63 : 64)) ? 1 : 0;
     p->mp = roundup(m, 128);
     p->np = roundup(n, p->form == OZMP_FORM_FP8 ? 256 : 128);
     p->kp = roundup(k, 128);

@@ -1,7 +1,7 @@
 // Splitter for many components: exponent reduce (K1) and exact truncating
-// e4m3 digit split (K2) for operands of up to OZMP_MAX_COMPONENTS binary64
-// components, or digit windows wider than the register-resident path's
-// (beta s + 65 > 448 bits).
+// e4m3 digit split (K2, 4-bit or balanced radix-32 digits) for operands of up
+// to OZMP_MAX_COMPONENTS binary64 components, or more slices than the
+// register-resident path writes (64 four-bit, 63 balanced).
 //
 // Paper, Sec. 3, Algorithm 1 (mu, tau and the slice extraction), carried to
 // the multiple precisions of Sec. 5.  Same definitions as the q <= 4 path:
@@ -163,14 +163,16 @@ __device__ __forceinline__ int exponent_n(const double (&v)[QB], int q, bool& ok
     return slow_exponent_n(v, q);
 }
 
-// |x| in an NW-word window whose bit 64 NW - 1 has weight 2^(Erow - 1), so
-// that digit t (1-based) is the nibble at bits [64 NW - 4 t, 64 NW - 4 t + 4).
+// |x| in an NW-word window whose bit 64 NW - 1 has weight 2^(Erow - 1) (with
+// NIB; 2^Erow without), so that 4-bit digit t (1-based) is the nibble at bits
+// [64 NW - 4 t, 64 NW - 4 t + 4), or balanced radix-32 group t is at bits
+// [64 NW - 5 t, 64 NW - 5 t + 5).
 // Word 0 lies below every digit (64 NW >= 4 s + 65) and absorbs truncation:
 // bits of components below the window change the truncated magnitude only
 // through a borrow or carry out of word 0, possible only when word 0 is
 // within q of 0 or of 2^64; those cases take the full-range sum.
 // Returns the sign of x (0 for zero or an all-zero row).
-template <int NW>
+template <int NW, bool NIB = true>
 __device__ __forceinline__ int window_n(const double (&v)[QB], int q, int Erow, uint64_t (&w)[NW]) {
 #pragma unroll
     for (int j = 0; j < NW; ++j) w[j] = 0;
@@ -204,7 +206,7 @@ __device__ __forceinline__ int window_n(const double (&v)[QB], int q, int Erow, 
 #pragma unroll
         for (int j = 0; j < NW; ++j) w[j] = tmp[j];
     }
-    mw_shl<NW>(w, 1);   // nibble-align the digits (the top bit is 0 for a magnitude below 2^Erow)
+    if (NIB) mw_shl<NW>(w, 1);   // nibble-align the digits (the top bit is 0 for a magnitude below 2^Erow)
     return sg;
 }
 
@@ -227,6 +229,44 @@ __device__ __forceinline__ void emit_digits(const uint64_t (&w)[NW], int sg, int
             const int t = jj * 16 + nb + 1;
             if (t <= s) out[(t - 1) * stride] = (uint8_t)e4m3_nibble((uint32_t)(word >> (60 - 4 * nb)) & 15u, neg);
         }
+    }
+}
+
+// e4m3 code of a digit d in [-16, 16] (all exact in e4m3; zero is +0)
+__device__ __forceinline__ uint32_t e4m3_small(int d) {
+    const uint32_t m = (uint32_t)(d < 0 ? -d : d);
+    const uint32_t code = m == 16u ? 0x58u : e4m3_nibble(m, false);
+    return (d < 0) ? (code | 0x80u) : code;
+}
+
+// the s balanced radix-32 digits of one element into shared memory: the
+// groups of the magnitude window plus 16 at every group (nothing added below
+// the lowest one) are the balanced digits plus 16, the carry out of the top
+// group making the top digit 16; each digit then takes the sign of x
+template <int NW>
+__device__ __forceinline__ void emit_digits_bal(uint64_t (&w)[NW], int sg, int s, uint8_t* out, int stride) {
+    constexpr int TMAX = (64 * NW - 65) / 5;
+    const int lo = 64 * NW - 5 * s;
+    constexpr BalSixteens<NW> P16;
+    uint64_t H[NW];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+        const uint64_t keep = (lo <= 64 * j) ? ~0ull : (lo >= 64 * j + 64 ? 0ull : (~0ull << (lo - 64 * j)));
+        H[j] = P16.w[j] & keep;
+    }
+    const uint64_t before = w[NW - 1];
+    mw_add<NW>(w, H);
+    const int top = (w[NW - 1] < before) ? 32 : 0;   // the top word carries bit 63 of H
+    const int sgn = sg < 0 ? -1 : 1;
+#pragma unroll
+    for (int t = 1; t <= TMAX; ++t) {
+        if (t > s) break;
+        const int pos = 64 * NW - 5 * t;
+        const int wi = pos >> 6, off = pos & 63;
+        uint64_t x = w[wi] >> off;
+        if (off > 59) x |= w[wi + 1] << (64 - off);
+        const int g = (int)((uint32_t)x & 31u) + (t == 1 ? top : 0);
+        out[(t - 1) * stride] = (uint8_t)e4m3_small(sgn * (g - 16));
     }
 }
 
@@ -282,7 +322,7 @@ __global__ void __launch_bounds__(NT) k_exp_cols_n(Op b, int64_t k, int64_t n, i
 //   ROWS: A (column-major m x k, element (i, p) at i + p lda), lines = rows;
 //   else: B (column-major k x n, element (p, j) at p + j ldb), lines = columns.
 // ---------------------------------------------------------------------------
-template <int NW, bool ROWS>
+template <int NW, bool ROWS, bool BAL>
 __global__ void __launch_bounds__(NT) k_split_n(Op op, int64_t lines, int64_t k, const int32_t* Ex, uint8_t* dig,
                                                 int64_t lp, int64_t kp, int s) {
     extern __shared__ __align__(16) uint8_t sd[];
@@ -299,8 +339,9 @@ __global__ void __launch_bounds__(NT) k_split_n(Op op, int64_t lines, int64_t k,
         load_comps(op, inside, ROWS ? (line + p * op.ld) : (p + line * op.ld), v);
         const int Er = (line < lines) ? Ex[line] : OZMP_EXP_ZERO;
         uint64_t w[NW];
-        const int sg = window_n<NW>(v, op.q, inside ? Er : OZMP_EXP_ZERO, w);
-        emit_digits<NW>(w, sg, s, sd + rl * TC + cp, TR * TC);
+        const int sg = window_n<NW, !BAL>(v, op.q, inside ? Er : OZMP_EXP_ZERO, w);
+        if (BAL) emit_digits_bal<NW>(w, sg, s, sd + rl * TC + cp, TR * TC);
+        else emit_digits<NW>(w, sg, s, sd + rl * TC + cp, TR * TC);
     }
     __syncthreads();
     const int words = s * TR * (TC / 4);
@@ -319,22 +360,23 @@ static Op make_op(const void* const* comps, int q, int64_t ld) {
     return o;
 }
 
-template <int NW>
+template <int NW, bool BAL>
 static cudaError_t digits(const SplitArgs& g, cudaStream_t st) {
     const size_t smem = (size_t)g.s * TR * TC;
-    cudaError_t e = cudaFuncSetAttribute(k_split_n<NW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_split_n<NW, true, BAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_split_n<NW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_split_n<NW, false, BAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (g.m > 0) {
         const Op a = make_op(g.A, g.q, g.lda);
         dim3 gr((unsigned)(g.mp / TR), (unsigned)(g.kp / TC));
-        k_split_n<NW, true><<<gr, NT, smem, st>>>(a, g.m, g.k, g.E, (uint8_t*)g.Adig, g.mp, g.kp, g.s);
+        k_split_n<NW, true, BAL><<<gr, NT, smem, st>>>(a, g.m, g.k, g.E, (uint8_t*)g.Adig, g.mp, g.kp, g.s);
     }
     if (g.n > 0) {
         const Op b = make_op(g.B, g.q, g.ldb);
         dim3 gr((unsigned)(g.np / TR), (unsigned)(g.kp / TC));
-        k_split_n<NW, false><<<gr, NT, smem, st>>>(b, g.n, g.k, g.F, (uint8_t*)g.Bdig, g.np, g.kp, g.s);
+        k_split_n<NW, false, BAL><<<gr, NT, smem, st>>>(b, g.n, g.k, g.F, (uint8_t*)g.Bdig, g.np, g.kp, g.s);
     }
     return cudaGetLastError();
 }
@@ -357,14 +399,20 @@ cudaError_t launch_exponents_big(const SplitArgs& g, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// e4m3 digits; the window has 8, 12 or 16 words (4 s + 65 bits at least)
+// e4m3 digits (4-bit, or balanced radix-32 with g.bal); the window has 8,
+// 12 or 16 words (beta s + 65 bits at least)
 cudaError_t launch_digits_big(const SplitArgs& g, cudaStream_t st) {
     const int need = (g.beta * g.s + 65 + 63) / 64;
     if (g.form != OZMP_FORM_FP8 && g.form != OZMP_FORM_FP8_MMA) return cudaErrorInvalidValue;
-    if (g.is_f32 || need > 16) return cudaErrorInvalidValue;
-    if (need <= 8) return big::digits<8>(g, st);
-    if (need <= 12) return big::digits<12>(g, st);
-    return big::digits<16>(g, st);
+    if (g.is_f32 || need > 16 || (g.bal && g.beta != 5)) return cudaErrorInvalidValue;
+    if (g.bal) {
+        if (need <= 8) return big::digits<8, true>(g, st);
+        if (need <= 12) return big::digits<12, true>(g, st);
+        return big::digits<16, true>(g, st);
+    }
+    if (need <= 8) return big::digits<8, false>(g, st);
+    if (need <= 12) return big::digits<12, false>(g, st);
+    return big::digits<16, false>(g, st);
 }
 
 }  // namespace ozmp

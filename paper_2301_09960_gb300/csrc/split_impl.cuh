@@ -207,27 +207,6 @@ __device__ __forceinline__ void pack_fp8_quad(uint64_t (&w)[4][NW], const int (&
     }
 }
 
-// bit 4 of every 5-bit digit group t = 1, 2, ... of a top-aligned window
-// (group t at bits [64 NW - 5 t, 64 NW - 5 t + 5)), word j
-__host__ __device__ constexpr uint64_t bal_sixteens(int nw, int j) {
-    uint64_t r = 0;
-    for (int t = 1; 64 * nw - 5 * t >= 0; ++t) {
-        const int b = 64 * nw - 5 * t + 4;
-        if (b >= 64 * j && b < 64 * j + 64) r |= 1ull << (b - 64 * j);
-    }
-    return r;
-}
-
-// the words of that pattern as a constant table (evaluated by the compiler:
-// a constexpr function called in a run-time expression need not be)
-template <int NW>
-struct BalSixteens {
-    uint64_t w[NW];
-    constexpr BalSixteens() : w() {
-        for (int j = 0; j < NW; ++j) w[j] = bal_sixteens(NW, j);
-    }
-};
-
 // The balanced radix-32 e4m3 digits of four elements (consecutive k), all
 // slices: calls put(t, word) for t = 1 .. s with byte e of `word` = e4m3 code
 // of digit t of element e.  The magnitude window holds

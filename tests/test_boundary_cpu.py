@@ -84,9 +84,9 @@ def test_plan_rejects_bad_arguments():
 def test_component_count_plans(q):
     # q binary64 components: target 2^(-50 q) -> s = ceil((50 q + log2 k + 16) / 4) e4m3 digits,
     # the accumulator holds every diagonal's weight, and more than 4 components
-    # take the tcgen05 form only (the automatic form picks the 4-bit digits there)
+    # take the tcgen05 form only
     k = 1000
-    h = oz.ozmp_plan_create(q, 300, 200, k, oz.Form.AUTO if q > 4 else oz.Form.FP8, 0, None)
+    h = oz.ozmp_plan_create(q, 300, 200, k, oz.Form.FP8, 0, None)
     try:
         i = oz.ozmp_plan_get_info(h)
         assert i.form == oz.Form.FP8 and i.beta == 4
@@ -158,12 +158,12 @@ def test_balanced_digit_plans(prec, k):
 
 
 def test_balanced_digit_limits():
-    # the register splitter's 6-word window: 5 s + 65 <= 384, so s <= 63;
-    # more than 4 components are not offered in this form
-    h = oz.ozmp_plan_create(oz.Prec.DD, 10, 10, 10, oz.Form.FP8_BAL, 63, None)
-    oz.ozmp_plan_destroy(h)
-    for args in [(2, 10, 10, 10, oz.Form.FP8_BAL, 64), (5, 10, 10, 10, oz.Form.FP8_BAL, 0),
-                 (2, 8, 8, 70000, oz.Form.FP8_BAL, 0)]:
+    # windows of 5 s + 65 <= 1024 bits (the many-component splitter's 16
+    # words), so s <= 191, for any component count
+    for q, s in [(2, 63), (2, 64), (2, 191), (5, 0), (16, 0)]:
+        h = oz.ozmp_plan_create(q, 10, 10, 10, oz.Form.FP8_BAL, s, None)
+        oz.ozmp_plan_destroy(h)
+    for args in [(2, 10, 10, 10, oz.Form.FP8_BAL, 192), (2, 8, 8, 70000, oz.Form.FP8_BAL, 0)]:
         with pytest.raises(oz.OzmpError) as e:
             oz.ozmp_plan_create(*args, None)
         assert e.value.status == oz.Status.ERR_UNSUPPORTED
@@ -175,9 +175,10 @@ def test_balanced_digit_limits():
 
 
 def test_automatic_form_choice():
-    # balanced radix-32 digits where their splitter applies, else 4-bit digits
-    for q, ns, want in [(2, 0, oz.Form.FP8_BAL), (4, 63, oz.Form.FP8_BAL), (2, 64, oz.Form.FP8),
-                        (5, 0, oz.Form.FP8), (oz.Prec.TS, 0, oz.Form.FP8_BAL)]:
+    # balanced radix-32 digits up to their largest slice count, else 4-bit digits
+    for q, ns, want in [(2, 0, oz.Form.FP8_BAL), (4, 63, oz.Form.FP8_BAL), (2, 191, oz.Form.FP8_BAL),
+                        (2, 192, oz.Form.FP8), (5, 0, oz.Form.FP8_BAL), (16, 0, oz.Form.FP8_BAL),
+                        (oz.Prec.TS, 0, oz.Form.FP8_BAL)]:
         h = oz.ozmp_plan_create(q, 64, 64, 64, oz.Form.AUTO, ns, None)
         try:
             assert oz.ozmp_plan_get_info(h).form == want, (q, ns)

@@ -1,7 +1,8 @@
 """GPU parity for more than four binary64 components (and digit windows
 wider than the register-resident splitter's), against the CPU oracle.
 
-* exponents and every e4m3 digit: bit-exact against oracle.ozaki.split;
+* exponents and every e4m3 digit (4-bit or balanced radix-32): bit-exact
+  against oracle.ozaki.split / split_balanced;
 * the product: bit-exact against the canonical q-component rounding of the
   oracle's exact Ozaki sum, on whole small problems and on sampled blocks of
   multi-tile ones (row and column exponents are maxima over the full k, so a
@@ -28,14 +29,27 @@ from _util import digits_to_int, from_dev, to_dev
 pytestmark = pytest.mark.gpu
 
 
-def _gemm(q, m, n, k, seed, nslices=0, prec=None):
+def _gemm(q, m, n, k, seed, nslices=0, prec=None, form="fp8"):
     prec = prec or f"q{q}"
     A, B = gen_problem(prec, m, n, k, phi=1.0, seed=seed)
     Ad, Bd = to_dev(A), to_dev(B)
-    C, p = oz.gemm(Ad, Bd, prec, "fp8", nslices)
+    C, p = oz.gemm(Ad, Bd, prec, form, nslices)
     torch.cuda.synchronize()
     assert p.status() == oz.Status.OK
     return A, B, from_dev(C), p, Ad, Bd
+
+
+def _osplit(comps, form, beta, s):
+    return O.split_balanced(comps, s) if form == "fp8bal" else O.split(comps, beta, s)
+
+
+def _oproduct(A, B, info):
+    return O.ozaki_product(A, B, info.beta, info.nslices, balanced=(info.form == oz.Form.FP8_BAL))
+
+
+def _auto_slices(q, k, form):
+    bits = 50 * q + max(0, (k - 1).bit_length()) + 16
+    return -(-(bits + 1) // 5) if form == "fp8bal" else -(-bits // 4)
 
 
 def _rows_cols(A, B, rows, cols):
@@ -55,30 +69,32 @@ def _fraction_error(A, B, Cg, rows, cols):
     return num, den
 
 
+@pytest.mark.parametrize("form", ["fp8", "fp8bal"])
 @pytest.mark.parametrize("q,m,n,k", [(5, 70, 60, 50), (8, 70, 60, 50), (16, 40, 36, 30)])
-def test_split_bit_exact(q, m, n, k):
+def test_split_bit_exact(q, m, n, k, form):
     A, B = gen_problem(f"q{q}", m, n, k, phi=1.0, seed=21 + q)
-    p = oz.Plan(q, m, n, k, "fp8", 0)
+    p = oz.Plan(q, m, n, k, form, 0)
     p.split(to_dev(A), to_dev(B))
     torch.cuda.synchronize()
     i = p.info
-    assert i.nslices == -(-(50 * q + max(0, (k - 1).bit_length()) + 16) // 4)
+    assert i.nslices == _auto_slices(q, k, form)
     E, F = [t.cpu().numpy() for t in p.exponents()]
     ga, gb = [t.cpu().numpy() for t in p.digits()]
-    Eo, dA = O.split(A, i.beta, i.nslices)
-    Fo, dB = O.split([np.asfortranarray(b.T) for b in B], i.beta, i.nslices)
+    Eo, dA = _osplit(A, form, i.beta, i.nslices)
+    Fo, dB = _osplit([np.asfortranarray(b.T) for b in B], form, i.beta, i.nslices)
     assert list(E) == Eo and list(F) == Fo
-    np.testing.assert_array_equal(digits_to_int(ga[:, :m, :k], "fp8"), dA)
-    np.testing.assert_array_equal(digits_to_int(gb[:, :n, :k], "fp8"), dB)
-    assert not digits_to_int(ga[:, m:, :], "fp8").any() and not digits_to_int(ga[:, :, k:], "fp8").any()
-    assert not digits_to_int(gb[:, n:, :], "fp8").any() and not digits_to_int(gb[:, :, k:], "fp8").any()
+    np.testing.assert_array_equal(digits_to_int(ga[:, :m, :k], form), dA)
+    np.testing.assert_array_equal(digits_to_int(gb[:, :n, :k], form), dB)
+    assert not digits_to_int(ga[:, m:, :], form).any() and not digits_to_int(ga[:, :, k:], form).any()
+    assert not digits_to_int(gb[:, n:, :], form).any() and not digits_to_int(gb[:, :, k:], form).any()
 
 
+@pytest.mark.parametrize("form", ["fp8", "fp8bal"])
 @pytest.mark.parametrize("q,m,n,k", [(5, 70, 60, 50), (8, 50, 40, 36), (16, 24, 20, 18)])
-def test_product_bit_exact_and_within_target(q, m, n, k):
-    A, B, Cg, p, _, _ = _gemm(q, m, n, k, seed=40 + q)
+def test_product_bit_exact_and_within_target(q, m, n, k, form):
+    A, B, Cg, p, _, _ = _gemm(q, m, n, k, seed=40 + q, form=form)
     i = p.info
-    r = O.ozaki_product(A, B, i.beta, i.nslices)
+    r = _oproduct(A, B, i)
     for a in range(m):
         for b in range(n):
             assert [float(c[a, b]) for c in Cg] == X.to_components(r["S"][a][b], q, "f64"), (a, b)
@@ -87,14 +103,15 @@ def test_product_bit_exact_and_within_target(q, m, n, k):
     assert num <= den * Fraction(1, 2 ** (100 * q))
 
 
-def test_multi_tile_q8_sampled_blocks():
+@pytest.mark.parametrize("form", ["fp8", "fp8bal"])
+def test_multi_tile_q8_sampled_blocks(form):
     # 300 x 520 x 260: two row tiles, three column tiles, ragged in every direction
     q, m, n, k = 8, 300, 520, 260
-    A, B, Cg, p, _, _ = _gemm(q, m, n, k, seed=77)
+    A, B, Cg, p, _, _ = _gemm(q, m, n, k, seed=77, form=form)
     i = p.info
     rows, cols = [0, 1, 127, 128, 255, 256, 299], [0, 255, 256, 300, 511, 519]
     As, Bs = _rows_cols(A, B, rows, cols)
-    r = O.ozaki_product(As, Bs, i.beta, i.nslices)
+    r = _oproduct(As, Bs, i)
     for a_i, a in enumerate(rows):
         for b_j, b in enumerate(cols):
             assert [float(c[a, b]) for c in Cg] == X.to_components(r["S"][a_i][b_j], q, "f64"), (a, b)
@@ -102,15 +119,17 @@ def test_multi_tile_q8_sampled_blocks():
     assert num <= den * Fraction(1, 2 ** (100 * q))
 
 
-def test_wide_window_with_few_components():
-    # DD with 120 slices: beta s = 480 > 376 takes the many-component splitter
+@pytest.mark.parametrize("form,s", [("fp8", 120), ("fp8bal", 100)])
+def test_wide_window_with_few_components(form, s):
+    # DD with more slices than the register splitter writes (64 four-bit,
+    # 63 balanced): the many-component splitter
     m, n, k = 130, 140, 100
-    A, B, Cg, p, _, _ = _gemm(2, m, n, k, seed=5, nslices=120, prec="dd")
+    A, B, Cg, p, _, _ = _gemm(2, m, n, k, seed=5, nslices=s, prec="dd", form=form)
     i = p.info
-    assert i.nslices == 120
+    assert i.nslices == s
     rows, cols = [0, 17, 64, 129], [0, 33, 127, 139]
     As, Bs = _rows_cols(A, B, rows, cols)
-    r = O.ozaki_product(As, Bs, i.beta, i.nslices)
+    r = _oproduct(As, Bs, i)
     for a_i, a in enumerate(rows):
         for b_j, b in enumerate(cols):
             assert [float(c[a, b]) for c in Cg] == X.to_components(r["S"][a_i][b_j], 2, "f64"), (a, b)
@@ -118,7 +137,8 @@ def test_wide_window_with_few_components():
 
 def test_plain_entry_point_matches_plan():
     q, m, n, k = 6, 90, 70, 80
-    A, B, Cg, p, Ad, Bd = _gemm(q, m, n, k, seed=3)
+    A, B, Cg, p, Ad, Bd = _gemm(q, m, n, k, seed=3, form="auto")
+    assert p.info.form == oz.Form.FP8_BAL
     C2 = [torch.empty((n, m), dtype=torch.float64, device="cuda").T for _ in range(q)]
     oz.ozmp_gemm_md(Ad, Bd, C2)
     torch.cuda.synchronize()
