@@ -11,8 +11,8 @@ to 32 x 32) and solves the panels with recursive triangular solves whose
 updates are Ozaki products too.  Every operation that is not an Ozaki
 product is an exact value rounded once, canonically, into q binary64
 components (exact.to_components); the Ozaki products are the exact Ozaki
-sums (ozaki.ozaki_product, e4m3 digits, beta = 4, the slice count of the
-precision's target) rounded the same way.  This module restates those
+sums (ozaki.ozaki_product with balanced radix-32 e4m3 digits, beta = 5,
+the slice count of the precision's target) rounded the same way.  This module restates those
 definitions with exact dyadic arithmetic, operation by operation, so that
 its factors are the exact values the definitions give.
 """
@@ -34,10 +34,10 @@ def half(n: int) -> int:
 
 
 def slices_for(q: int, k: int) -> int:
-    """Automatic slice count of the e4m3 form: target 2^(-50 q), guard
-    log2 k + 16 bits, beta = 4."""
+    """Automatic slice count of the balanced e4m3 form: target 2^(-50 q),
+    guard log2 k + 16 bits, 5 s - 1 bits kept below 2^E."""
     lg = max(0, (k - 1).bit_length())
-    return -(-(50 * q + lg + 16) // 4)
+    return -(-(50 * q + lg + 16 + 1) // 5)
 
 
 def newton_steps(q: int) -> int:
@@ -120,7 +120,7 @@ def gemm_sub(M, cr, cc, ar, ac, br, bc, m, n, k):
     q = M.q
     A = block(M, ar, ac, m, k)
     B = block(M, br, bc, k, n)
-    r = O.ozaki_product(A, B, O.BETA_FP8, slices_for(q, k))
+    r = O.ozaki_product(A, B, O.BETA_BAL, slices_for(q, k), balanced=True)
     for i in range(m):
         for j in range(n):
             p = canon(r["S"][i][j], q)

@@ -351,7 +351,7 @@ static void gemm_sub(Ctx& x, const Mat& C, const Mat& A, const Mat& B, int64_t m
     ozmp_plan p;
     auto it = x.plans.find(key);
     if (it == x.plans.end()) {
-        if (ozmp_plan_create(&p, OZMP_PREC_Q(x.q), m, n, k, OZMP_FORM_FP8, 0, x.st) != OZMP_OK) { x.failed = true; return; }
+        if (ozmp_plan_create(&p, OZMP_PREC_Q(x.q), m, n, k, OZMP_FORM_FP8_BAL, 0, x.st) != OZMP_OK) { x.failed = true; return; }
         x.plans[key] = p;
     } else {
         p = it->second;
