@@ -109,14 +109,16 @@ def test_td_qd_1024_binary64_slices(prec):
 
 
 @pytest.mark.slow
-def test_qd_8192_8192_16384():
+@pytest.mark.parametrize("form", ["fp8", "fp8bal"])
+def test_qd_8192_8192_16384(form):
     rows = [0, 4097, 8191]
     cols = [0, 8191]
-    _sampled("qd", "fp8", 8192, 8192, 16384, 1.0, 0, rows, cols, [0], [0, 1])
+    _sampled("qd", form, 8192, 8192, 16384, 1.0, 0, rows, cols, [0], [0, 1])
 
 
 @pytest.mark.slow
-def test_ts_8192():
+@pytest.mark.parametrize("form", ["fp8", "fp8bal"])
+def test_ts_8192(form):
     rows = [0, 4096, 8191]
     cols = [7, 8191]
-    _sampled("ts", "fp8", 8192, 8192, 8192, 1.0, 0, rows, cols, [0, 2], [0, 1])
+    _sampled("ts", form, 8192, 8192, 8192, 1.0, 0, rows, cols, [0, 2], [0, 1])
