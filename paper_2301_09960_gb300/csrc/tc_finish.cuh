@@ -7,25 +7,36 @@
 namespace ozmp {
 namespace tc {
 
-// Rounding pass of the single-problem path: one thread per element of C
-// normalises the element's carry-save limbs 0 .. nl-1 (from its tile's split
-// slot when the tile was split into chunks, else from acc) and rounds them
-// canonically into the q components.  Bound by the limb reads.
+// Rounding pass of the single-problem path: one thread per row i of C and
+// FIN_J consecutive columns j normalises each element's carry-save limbs
+// 0 .. nl-1 (from its tile's split slot when the tile was split into chunks,
+// else from acc) and rounds them canonically into the q components.  The
+// row's tile coordinates are computed once per thread.  Bound by the limb
+// reads and the rounding arithmetic.
+constexpr int FIN_J = 8;
+
 template <int NW>
 __global__ void __launch_bounds__(256) k_tc_finish(const GemmArgs g, int nl, const int* tile_slot, int tile_rows,
                                                    int slot_limbs) {
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (i >= g.m) return;
     const size_t sstride = (size_t)BN * BM;
-    for (int64_t j = blockIdx.y; j < g.n; j += gridDim.y) {
-        const int slot =
-            tile_slot ? tile_slot[(i / tile_rows) + (j / BN) * (g.mp / tile_rows)] : -1;
-        if (slot < 0) {
-            finish_element<NW>(g, nl, g.acc, (size_t)g.mp * g.np, (size_t)j * g.mp + i, i, j, 0, 0, false);
-        } else {
-            const int cta = slot * (tile_rows / BM) + (int)((i % tile_rows) / BM);
-            finish_element<NW>(g, nl, g.sacc + (size_t)cta * slot_limbs * sstride, sstride,
-                               (size_t)(j % BN) * BM + (size_t)(i % BM), i, j, 0, 0, false);
+    const int64_t trow = i / tile_rows, ntrow = g.mp / tile_rows;
+    const int cta_in = (int)((i % tile_rows) / BM);
+    const size_t irow = (size_t)(i % BM);
+    for (int64_t j0 = (int64_t)blockIdx.y * FIN_J; j0 < g.n; j0 += (int64_t)gridDim.y * FIN_J) {
+#pragma unroll 1
+        for (int jj = 0; jj < FIN_J; ++jj) {
+            const int64_t j = j0 + jj;
+            if (j >= g.n) break;
+            const int slot = tile_slot ? tile_slot[trow + (j / BN) * ntrow] : -1;
+            if (slot < 0) {
+                finish_element<NW>(g, nl, g.acc, (size_t)g.mp * g.np, (size_t)j * g.mp + i, i, j, 0, 0, false);
+            } else {
+                const int cta = slot * (tile_rows / BM) + cta_in;
+                finish_element<NW>(g, nl, g.sacc + (size_t)cta * slot_limbs * sstride, sstride,
+                                   (size_t)(j % BN) * BM + irow, i, j, 0, 0, false);
+            }
         }
     }
 }
@@ -36,7 +47,8 @@ __global__ void __launch_bounds__(256) k_tc_finish(const GemmArgs g, int nl, con
     case NWV: tc::k_tc_finish<NWV><<<fg, 256, 0, st>>>(g, nl, ts, rows, slot_limbs); break;
 
 inline dim3 tc_finish_grid(const GemmArgs& g) {
-    return dim3((unsigned)((g.m + 255) / 256), (unsigned)(g.n < 65535 ? g.n : 65535));
+    const int64_t cy = (g.n + tc::FIN_J - 1) / tc::FIN_J;
+    return dim3((unsigned)((g.m + 255) / 256), (unsigned)(cy < 65535 ? (cy > 0 ? cy : 1) : 65535));
 }
 
 }  // namespace ozmp
