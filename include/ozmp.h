@@ -218,9 +218,9 @@ ozmp_status ozmp_gemm_dd_noalloc(int64_t m, int64_t n, int64_t k, const double* 
  *   between calls.  Destroy with ozmp_plan_destroy; status with
  *   ozmp_plan_get_status (one word for the whole batch).
  * The problem array and the component-pointer arrays it points to are read
- * during the call only.  Batched problems hold at most 4 components and
- * 64 four-bit or 63 balanced slices (else OZMP_ERR_UNSUPPORTED); larger ones
- * go through single-problem plans.  form FP8_BAL runs every problem in balanced
+ * during the call only.  Batched problems hold at most 4 components,
+ * 64 four-bit or 63 balanced slices and m n < 2^31 elements of C (else
+ * OZMP_ERR_UNSUPPORTED); larger ones go through single-problem plans.  form FP8_BAL runs every problem in balanced
  * radix-32 digits; a plan is reused only with the form it was made for.
  */
 typedef struct {

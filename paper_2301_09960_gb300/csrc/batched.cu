@@ -90,12 +90,17 @@ __global__ void __launch_bounds__(256) k_b_exp_cols(const BSplit* P, const int* 
 }
 
 // FORM: OZMP_FORM_FP8 (4-bit digits) or OZMP_FORM_FP8_BAL (balanced radix-32 digits)
+// The digit launches cover only the tiles that hold values: rows i < m
+// (tiles of 32) and values p < k (chunks of 64) of A, columns j < n and
+// values p < k (quads) of B.  The batched workspace is zeroed when the plan
+// is built, so the rest of the padding keeps zero digits without being
+// written.
 template <typename T, int NW, int FORM>
 __global__ void __launch_bounds__(256) k_b_split_rows(const BSplit* P, const int* pre, int count) {
     const int p = find_prob(pre, count, blockIdx.x);
     const BSplit& s = P[p];
     const int lb = blockIdx.x - pre[p];
-    const int nbx = (int)(s.mp / 32);
+    const int nbx = (int)((s.m + 31) / 32);
     split_rows_b1_body<T, FORM, NW>(opA<T>(s), s.m, s.k, s.E, s.Adig, s.mp, s.kp, s.s,
                                     (int64_t)(lb % nbx), (int64_t)(lb / nbx));
 }
@@ -105,7 +110,7 @@ __global__ void __launch_bounds__(256) k_b_split_cols(const BSplit* P, const int
     const int p = find_prob(pre, count, blockIdx.x);
     const BSplit& s = P[p];
     split_cols_b1_body<T, FORM, NW>(opB<T>(s), s.k, s.n, s.F, s.Bdig, s.np, s.kp, s.s,
-                                    (int64_t)(blockIdx.x - pre[p]), (int64_t)0);
+                                    (int64_t)(blockIdx.x - pre[p]), (int64_t)0, (s.k + 3) / 4);
 }
 
 template <typename T, int FORM>
@@ -129,19 +134,40 @@ static void split_group(int nw, const int (&blocks)[5], const BSplit* sp, const 
 
 }  // namespace ozmp
 
-// Rounding pass of the batched products: block b belongs to problem
-// ids[x], x the last with pre[x] <= b; one thread per element of its C
-// normalises the element's limbs and rounds them into the q components.
+// Rounding pass of the batched products whose accumulators have NW words:
+// block b belongs to problem ids[x], x the last with pre[x] <= b (found once
+// per block, its launch fields staged in shared memory); one thread per
+// element of its C (column-major order) normalises the element's limbs and
+// rounds them into the q components.
+template <int NW>
 __global__ void __launch_bounds__(256) k_b_finish(const tc::Prob* probs, const int* ids, const int* pre, int count,
                                                   uint32_t* status) {
-    const int x = find_prob(pre, count, blockIdx.x);
-    const tc::Prob& P = probs[ids[x]];
-    const int64_t e = (int64_t)(blockIdx.x - pre[x]) * blockDim.x + threadIdx.x;
-    if (e >= P.m * P.n) return;
-    const int64_t i = e % P.m, j = e / P.m;
-    const GemmArgs g = tc::as_gemm_args(P, status);
-    const int nl = (P.beta * (P.s - 1)) / 16 + 1;   // limbs 0 .. the last drain's
-    tc::finish_dispatch(g, nl, P.acc, (size_t)P.mp * P.np, (size_t)j * P.mp + i, i, j, 0, 0, false);
+    __shared__ GemmArgs g;
+    __shared__ int x;
+    if (threadIdx.x == 0) {
+        x = find_prob(pre, count, blockIdx.x);
+        g = tc::as_gemm_args(probs[ids[x]], status);
+    }
+    __syncthreads();
+    const uint32_t m = (uint32_t)g.m;
+    const uint32_t e = (uint32_t)(blockIdx.x - pre[x]) * blockDim.x + threadIdx.x;   // m n < 2^32
+    if ((uint64_t)e >= (uint64_t)g.m * (uint64_t)g.n) return;
+    const uint32_t j = e / m, i = e - j * m;
+    const int nl = (g.beta * (g.s - 1)) / 16 + 1;   // limbs 0 .. the last drain's
+    tc::finish_element<NW>(g, nl, g.acc, (size_t)g.mp * g.np, (size_t)j * g.mp + i, i, j, 0, 0, false);
+}
+
+// one launch of the rounding pass (accumulator words nw, 2 .. 7)
+static void launch_b_finish(int nw, int blocks, const tc::Prob* probs, const int* ids, const int* pre, int count,
+                            uint32_t* status, cudaStream_t cs) {
+    switch (nw) {
+        case 2: k_b_finish<2><<<blocks, 256, 0, cs>>>(probs, ids, pre, count, status); break;
+        case 3: k_b_finish<3><<<blocks, 256, 0, cs>>>(probs, ids, pre, count, status); break;
+        case 4: k_b_finish<4><<<blocks, 256, 0, cs>>>(probs, ids, pre, count, status); break;
+        case 5: k_b_finish<5><<<blocks, 256, 0, cs>>>(probs, ids, pre, count, status); break;
+        case 6: k_b_finish<6><<<blocks, 256, 0, cs>>>(probs, ids, pre, count, status); break;
+        default: k_b_finish<7><<<blocks, 256, 0, cs>>>(probs, ids, pre, count, status); break;
+    }
 }
 
 // ----------------------------------------------------------------------------
@@ -173,8 +199,10 @@ struct Batch {
     void* pinned = nullptr;        // host mirror of the pointer-carrying descriptors
     size_t pinned_bytes = 0;
     size_t off_probs = 0, off_maps = 0, off_items = 0, off_cta = 0, off_status = 0;
-    size_t off_fids = 0, off_fpre = 0;   // rounding pass: problem ids and their block prefixes
-    int fin_count = 0, fin_blocks = 0;   // (0 blocks: the product kernel rounds in place)
+    // rounding pass: per accumulator width, the problem ids and their block
+    // prefixes in meta (none: the product kernel rounds in place)
+    struct FinGroup { int nw = 0, count = 0, blocks = 0; size_t off_ids = 0, off_pre = 0; };
+    std::vector<FinGroup> fin;
     int grid = 0;
     std::vector<int> q;
     cudaGraphExec_t gexec = nullptr;
@@ -301,6 +329,7 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
         if (!q || r.m < 0 || r.n < 0 || r.k < 0 || r.nslices < 0 || r.nslices > OZMP_MAX_SLICES)
             return OZMP_ERR_INVALID_ARG;
         if (q > 4) return OZMP_ERR_UNSUPPORTED;   // the batched kernels hold at most 4 components
+        if (r.m > 0 && r.n > (int64_t)0x7fffffff / r.m) return OZMP_ERR_UNSUPPORTED;   // m n < 2^31 per problem
         if (r.lda < (r.m > 1 ? r.m : 1) || r.ldb < (r.k > 1 ? r.k : 1) || r.ldc < (r.m > 1 ? r.m : 1))
             return OZMP_ERR_INVALID_ARG;
         if (r.m > 0 && r.n > 0) {
@@ -355,6 +384,11 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
             cudaGetLastError();
             destroy_batch(b);
             return OZMP_ERR_NOMEM;
+        }
+        // zero digits in the padding of every problem, written once here
+        if (cudaMemsetAsync(b->ws, 0, b->ws_bytes ? b->ws_bytes : 256, st) != cudaSuccess) {
+            destroy_batch(b);
+            return OZMP_ERR_CUDA;
         }
         // groups by component type
         for (int t = 0; t < 2; ++t) {
@@ -418,22 +452,31 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
         b->off_cta = mo; mo = a256(mo + sizeof(int) * (cta_off.size() + 1));
         // the rounding pass over the limbs runs after the product launch (unless
         // OZMP_BATCH_DEFER=0 keeps the rounding inside the product kernel)
-        std::vector<int> fids, fpre(1, 0);
+        std::vector<std::vector<int>> fids, fpre;
         {
             const char* env = getenv("OZMP_BATCH_DEFER");
             const bool defer = !(env && env[0] == '0');
             if (fm == OZMP_FORM_FP8 && defer)
-                for (int i = 0; i < count; ++i) {
-                    const ozmp_plan_s& sx = b->subs[i];
-                    if (sx.m == 0 || sx.n == 0 || sx.k == 0) continue;
-                    fids.push_back(i);
-                    fpre.push_back(fpre.back() + (int)((sx.m * sx.n + 255) / 256));
+                for (int nw = 2; nw <= 7; ++nw) {
+                    std::vector<int> ids, pre(1, 0);
+                    for (int i = 0; i < count; ++i) {
+                        const ozmp_plan_s& sx = b->subs[i];
+                        if (sx.m == 0 || sx.n == 0 || sx.k == 0 || sx.acc_words != nw) continue;
+                        ids.push_back(i);
+                        pre.push_back(pre.back() + (int)((sx.m * sx.n + 255) / 256));
+                    }
+                    if (ids.empty()) continue;
+                    Batch::FinGroup fg;
+                    fg.nw = nw;
+                    fg.count = (int)ids.size();
+                    fg.blocks = pre.back();
+                    fg.off_ids = mo; mo = a256(mo + sizeof(int) * ids.size());
+                    fg.off_pre = mo; mo = a256(mo + sizeof(int) * pre.size());
+                    b->fin.push_back(fg);
+                    fids.push_back(ids);
+                    fpre.push_back(pre);
                 }
         }
-        b->fin_count = (int)fids.size();
-        b->fin_blocks = fpre.back();
-        b->off_fids = mo; mo = a256(mo + sizeof(int) * (fids.size() + 1));
-        b->off_fpre = mo; mo = a256(mo + sizeof(int) * fpre.size());
         b->off_status = mo; mo = a256(mo + 16);
         b->meta_bytes = mo;
         if (cudaMalloc(&b->meta, b->meta_bytes) != cudaSuccess) {
@@ -459,7 +502,8 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
                 const ozmp_plan_s& s = b->subs[g.ids[x]];
                 const int nb[5] = {(int)((std::max(s.mp, s.np) + 255) / 256),
                                    (int)(((s.m + 255) / 256) * ((s.k + 255) / 256)), (int)((s.n + 7) / 8),
-                                   (int)((s.mp / 32) * (s.kp / 64)), (int)(((s.kp / 4) * s.np + 255) / 256)};
+                                   (int)(((s.m + 31) / 32) * ((s.k + 63) / 64)),
+                                   (int)((((s.k + 3) / 4) * s.n + 255) / 256)};
                 for (int kx = 0; kx < 5; ++kx) pre[kx][x + 1] = pre[kx][x] + nb[kx];
             }
             for (int kx = 0; kx < 5; ++kx) {
@@ -482,8 +526,10 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
         }
         memcpy(host.data() + (b->off_items - b->off_maps), items.data(), sizeof(tc::WorkItem) * items.size());
         memcpy(host.data() + (b->off_cta - b->off_maps), cta_off.data(), sizeof(int) * cta_off.size());
-        if (!fids.empty()) memcpy(host.data() + (b->off_fids - b->off_maps), fids.data(), sizeof(int) * fids.size());
-        memcpy(host.data() + (b->off_fpre - b->off_maps), fpre.data(), sizeof(int) * fpre.size());
+        for (size_t x = 0; x < b->fin.size(); ++x) {
+            memcpy(host.data() + (b->fin[x].off_ids - b->off_maps), fids[x].data(), sizeof(int) * fids[x].size());
+            memcpy(host.data() + (b->fin[x].off_pre - b->off_maps), fpre[x].data(), sizeof(int) * fpre[x].size());
+        }
         if (cudaMemcpy((char*)b->meta + b->off_maps, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
             destroy_batch(b);
             return OZMP_ERR_CUDA;
@@ -532,7 +578,7 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
         p.m = s.m; p.n = s.n; p.mp = s.mp; p.np = s.np; p.kp = s.kp; p.ldc = r.ldc;
         p.q = s.q; p.is_f32 = s.is_f32; p.s = s.s; p.beta = s.beta; p.ppd = s.ppd; p.acc_words = s.acc_words;
         p.bn = b->bn[i];
-        p.defer = b->fin_blocks > 0 ? 1 : 0;
+        p.defer = b->fin.empty() ? 0 : 1;
         p.eoff = b->bal ? 2 : 0;
     }
 
@@ -616,10 +662,10 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
                     memset(&m0, 0, sizeof(m0));
                     tc_launch(sc, dummy, m0, m0, status, b->grid, cs);
                 }
-                if (b->fin_blocks > 0)
-                    k_b_finish<<<b->fin_blocks, 256, 0, cs>>>(
-                        (const tc::Prob*)((char*)b->meta + b->off_probs), (const int*)((char*)b->meta + b->off_fids),
-                        (const int*)((char*)b->meta + b->off_fpre), b->fin_count, status);
+                for (const Batch::FinGroup& fg : b->fin)
+                    launch_b_finish(fg.nw, fg.blocks, (const tc::Prob*)((char*)b->meta + b->off_probs),
+                                    (const int*)((char*)b->meta + fg.off_ids),
+                                    (const int*)((char*)b->meta + fg.off_pre), fg.count, status, cs);
             } else {
                 // other forms: the problems one after another inside the graph
                 for (int i = 0; i < count; ++i) {

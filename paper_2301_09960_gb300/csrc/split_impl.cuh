@@ -354,14 +354,18 @@ __global__ void __launch_bounds__(256) k_split_rows_b1(Operand<T> a, int64_t m, 
 }
 
 // Columns of B (contiguous along k) -> Bdig[(t * np + j) * kp + p], 1-byte
-// digits: 4 consecutive k per thread, one 32-bit store per slice.
+// digits: 4 consecutive k per thread, one 32-bit store per slice.  Thread g
+// takes column g / quads, quads = kp / 4 (the whole padded workspace), or
+// the given count (columns j < n and k < kp only, when the padding of the
+// workspace is known to hold zero digits already).
 template <typename T, int FORM, int NW, int Q = 0>
 __device__ __forceinline__ void split_cols_b1_body(Operand<T> b, int64_t k, int64_t n, const int32_t* F,
-                                                       uint8_t* dig, int64_t np, int64_t kp, int s, int64_t bx, int64_t by) {
+                                                       uint8_t* dig, int64_t np, int64_t kp, int s, int64_t bx, int64_t by,
+                                                       int64_t quads_only = 0) {
     const int q = Q ? Q : b.q;
-    const int64_t quads = kp / 4;
+    const int64_t quads = quads_only > 0 ? quads_only : kp / 4;
     int64_t g = bx * blockDim.x + threadIdx.x;
-    if (g >= quads * np) return;
+    if (g >= quads * (quads_only > 0 ? n : np)) return;
     const int64_t j = g / quads;
     const int64_t p0 = (g % quads) * 4;
     const int Ecol = (j < n) ? F[j] : OZMP_EXP_ZERO;
