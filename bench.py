@@ -346,9 +346,18 @@ def main():
     ap.add_argument("--nslices", type=int, default=0)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--side", default=None, choices=sorted(SIDE),
+                    help="run one side measurement alone (one GPU) and print its JSON")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.side:
+        import torch
+        import paper_2301_09960_gb300 as oz
+        torch.cuda.set_device(0)
+        oz.load()
+        print(json.dumps({"side": args.side, "result": SIDE[args.side](oz, torch)}))
+        return
     ws, rank, local = _dist()
     workload = f"{args.prec} gemm m=n=k={args.n}, phi={args.phi}, Eq. 1 operands (configs: DD/QD 4096^3 fp64 vs int8 slices)"
     metric = "DD/QD GEMM effective GFLOP/s (2mnk/s) and % of slice roofline, INT8 vs FP64"
@@ -593,6 +602,15 @@ def main():
         print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
+
+
+# the side measurements that can run alone (--side)
+SIDE = {
+    "config4_batched512": lambda oz, torch: config4(oz, torch),
+    "lu_4096": lambda oz, torch: lu_variant(oz, torch),
+    "literal_vs_truncating_1024": lambda oz, torch: literal_variant(oz, torch),
+    "config2_td_qd_1024": lambda oz, torch: config2(oz, torch),
+}
 
 
 def add_variants(line, oz, torch, args):
