@@ -326,6 +326,10 @@ struct Ctx {
     bool failed;
     bool dry;                           // walk the recursion only, recording the largest product
     int64_t need;
+    // the second stream of the factorisation (its own product buffer and
+    // plans): X U11 = A21 runs there beside L11 X = A12
+    Ctx* side;
+    cudaEvent_t ev_fork, ev_join;
 };
 
 static Mat host_sub(const Mat& M, int64_t i, int64_t j, int q) {
@@ -441,8 +445,22 @@ static void lu_rec(Ctx& x, const Mat& A, int64_t n) {
     }
     const int64_t n1 = half(n), n2 = n - n1;
     lu_rec(x, A, n1);
+    // the two panel solves read only L11 / U11 and write disjoint blocks:
+    // A21 on the second stream, A12 on this one, joined before the update
+    Ctx& y = x.side ? *x.side : x;
+    if (x.side && !x.dry) {
+        if (cudaEventRecord(x.ev_fork, x.st) != cudaSuccess || cudaStreamWaitEvent(y.st, x.ev_fork, 0) != cudaSuccess) {
+            x.failed = true;
+            return;
+        }
+    }
+    trsm_ru(y, A, host_sub(A, n1, 0, x.q), n1, n2);                  // A21 := A21 U11^-1 = L21
     trsm_ll(x, A, host_sub(A, 0, n1, x.q), n1, n2);                  // A12 := L11^-1 A12 = U12
-    trsm_ru(x, A, host_sub(A, n1, 0, x.q), n1, n2);                  // A21 := A21 U11^-1 = L21
+    if (x.side && !x.dry) {
+        if (cudaEventRecord(x.ev_join, y.st) != cudaSuccess || cudaStreamWaitEvent(x.st, x.ev_join, 0) != cudaSuccess)
+            x.failed = true;
+    }
+    if (y.failed) x.failed = true;
     gemm_sub(x, host_sub(A, n1, n1, x.q), host_sub(A, n1, 0, x.q), host_sub(A, 0, n1, x.q), n2, n2, n1);
     lu_rec(x, host_sub(A, n1, n1, x.q), n2);
 }
@@ -451,18 +469,17 @@ static void lu_rec(Ctx& x, const Mat& A, int64_t n) {
 struct State {
     int64_t pcap = 0;           // doubles per component of the product buffer
     double* P = nullptr;        // q * pcap doubles
+    int64_t pcap2 = 0;          // the same for the second stream
+    double* P2 = nullptr;
     uint32_t* status = nullptr;
+    cudaStream_t st2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     Ctx ctx;
+    Ctx side;
 };
 thread_local State tl;
 
-// prepare(q, st) then a dry walk of the same recursion gives the largest
-// product; allocate() then sizes the product buffer for it
-static ozmp_status prepare(int q, cudaStream_t st) {
-    if (!tl.status) {
-        if (cudaMalloc(&tl.status, 16) != cudaSuccess) { cudaGetLastError(); return OZMP_ERR_NOMEM; }
-    }
-    Ctx& x = tl.ctx;
+static void reset_ctx(Ctx& x, int q, cudaStream_t st) {
     if (x.q != q || x.st != st) {
         for (auto& kv : x.plans) ozmp_plan_destroy(kv.second);
         x.plans.clear();
@@ -473,25 +490,63 @@ static ozmp_status prepare(int q, cudaStream_t st) {
     x.failed = false;
     x.dry = true;
     x.need = 1;
+    x.side = nullptr;
+}
+
+static bool size_buffer(double*& P, int64_t& pcap, int64_t need, cudaStream_t st) {
+    if (need <= pcap) return true;
+    if (P) { cudaStreamSynchronize(st); cudaFree(P); P = nullptr; }
+    if (cudaMalloc(&P, (size_t)QL * need * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        pcap = 0;
+        return false;
+    }
+    pcap = need;
+    return true;
+}
+
+// prepare(q, st) then a dry walk of the same recursion gives the largest
+// product; allocate() then sizes the product buffer for it
+// two_streams: the factorisation's panel solves of A21 go to a second
+// stream (the triangular solves of ozmp_lu_solve run on one)
+static ozmp_status prepare(int q, cudaStream_t st, bool two_streams) {
+    if (!tl.status) {
+        if (cudaMalloc(&tl.status, 16) != cudaSuccess) { cudaGetLastError(); return OZMP_ERR_NOMEM; }
+    }
+    reset_ctx(tl.ctx, q, st);
+    if (two_streams) {
+        if (!tl.st2) {
+            if (cudaStreamCreateWithFlags(&tl.st2, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&tl.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&tl.ev_join, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                return OZMP_ERR_CUDA;
+            }
+        }
+        reset_ctx(tl.side, q, tl.st2);
+        tl.ctx.side = &tl.side;
+        tl.ctx.ev_fork = tl.ev_fork;
+        tl.ctx.ev_join = tl.ev_join;
+    }
     return OZMP_OK;
 }
 
 static ozmp_status allocate(cudaStream_t st) {
     Ctx& x = tl.ctx;
     x.dry = false;
-    if (x.failed) return OZMP_ERR_CUDA;
-    if (x.need > tl.pcap) {
-        if (tl.P) { cudaStreamSynchronize(st); cudaFree(tl.P); tl.P = nullptr; }
-        if (cudaMalloc(&tl.P, (size_t)QL * x.need * sizeof(double)) != cudaSuccess) {
-            cudaGetLastError();
-            tl.pcap = 0;
-            return OZMP_ERR_NOMEM;
-        }
-        tl.pcap = x.need;
-    }
+    if (x.failed || (x.side && x.side->failed)) return OZMP_ERR_CUDA;
+    if (!size_buffer(tl.P, tl.pcap, x.need, st)) return OZMP_ERR_NOMEM;
     for (int c = 0; c < QL; ++c) x.P.c[c] = tl.P + (size_t)c * tl.pcap;
     x.P.ld = 0;
     x.pcap = tl.pcap;
+    if (x.side) {
+        Ctx& y = *x.side;
+        y.dry = false;
+        if (!size_buffer(tl.P2, tl.pcap2, y.need, y.st)) return OZMP_ERR_NOMEM;
+        for (int c = 0; c < QL; ++c) y.P.c[c] = tl.P2 + (size_t)c * tl.pcap2;
+        y.P.ld = 0;
+        y.pcap = tl.pcap2;
+    }
     return cudaMemsetAsync(tl.status, 0, 16, st) == cudaSuccess ? OZMP_OK : OZMP_ERR_CUDA;
 }
 
@@ -499,14 +554,18 @@ static ozmp_status finish(cudaStream_t st) {
     Ctx& x = tl.ctx;
     if (cudaGetLastError() != cudaSuccess) return OZMP_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return OZMP_ERR_CUDA;
-    if (x.failed) return OZMP_ERR_CUDA;
+    if (x.side && cudaStreamSynchronize(x.side->st) != cudaSuccess) return OZMP_ERR_CUDA;
+    if (x.failed || (x.side && x.side->failed)) return OZMP_ERR_CUDA;
     uint32_t w = 0;
     if (cudaMemcpy(&w, tl.status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return OZMP_ERR_CUDA;
     ozmp_status worst = OZMP_OK;
-    for (auto& kv : x.plans) {
-        ozmp_status s = OZMP_OK;
-        if (ozmp_plan_get_status(kv.second, &s) != OZMP_OK) return OZMP_ERR_CUDA;
-        if (s != OZMP_OK && worst == OZMP_OK) worst = s;
+    for (Ctx* c : {&x, x.side}) {
+        if (!c) continue;
+        for (auto& kv : c->plans) {
+            ozmp_status s = OZMP_OK;
+            if (ozmp_plan_get_status(kv.second, &s) != OZMP_OK) return OZMP_ERR_CUDA;
+            if (s != OZMP_OK && worst == OZMP_OK) worst = s;
+        }
     }
     if (w & ST_NONFINITE) return OZMP_ERR_NONFINITE;
     if (w & ST_RANGE) return OZMP_ERR_RANGE;
@@ -538,9 +597,9 @@ extern "C" ozmp_status ozmp_lu(int q, int64_t n, double* const* A, int64_t lda, 
     if (!lu::ptrs((const void* const*)A, q)) return OZMP_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const lu::Mat M = lu::make((const void* const*)A, q, lda);
-    ozmp_status s = lu::prepare(q, st);
+    ozmp_status s = lu::prepare(q, st, true);
     if (s != OZMP_OK) return s;
-    lu::lu_rec(lu::tl.ctx, M, n);   // dry walk: the largest product
+    lu::lu_rec(lu::tl.ctx, M, n);   // dry walk: the largest product of each stream
     s = lu::allocate(st);
     if (s != OZMP_OK) return s;
     lu::lu_rec(lu::tl.ctx, M, n);
@@ -556,7 +615,7 @@ extern "C" ozmp_status ozmp_lu_solve(int q, int64_t n, int64_t nrhs, const doubl
     cudaStream_t st = (cudaStream_t)stream;
     const lu::Mat L = lu::make((const void* const*)LU, q, lda);
     const lu::Mat X = lu::make((const void* const*)B, q, ldb);
-    ozmp_status s = lu::prepare(q, st);
+    ozmp_status s = lu::prepare(q, st, false);
     if (s != OZMP_OK) return s;
     for (int pass = 0; pass < 2; ++pass) {      // dry walk, then the solve
         lu::trsm_ll(lu::tl.ctx, L, X, n, nrhs);   // L y = b
