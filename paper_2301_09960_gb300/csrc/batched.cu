@@ -143,10 +143,12 @@ template <int NW>
 __global__ void __launch_bounds__(256) k_b_finish(const tc::Prob* probs, const int* ids, const int* pre, int count,
                                                   uint32_t* status) {
     __shared__ GemmArgs g;
+    __shared__ tc::Prob P;
     __shared__ int x;
     if (threadIdx.x == 0) {
         x = find_prob(pre, count, blockIdx.x);
-        g = tc::as_gemm_args(probs[ids[x]], status);
+        P = probs[ids[x]];
+        g = tc::as_gemm_args(P, status);
     }
     __syncthreads();
     const uint32_t m = (uint32_t)g.m;
@@ -154,7 +156,15 @@ __global__ void __launch_bounds__(256) k_b_finish(const tc::Prob* probs, const i
     if ((uint64_t)e >= (uint64_t)g.m * (uint64_t)g.n) return;
     const uint32_t j = e / m, i = e - j * m;
     const int nl = (g.beta * (g.s - 1)) / 16 + 1;   // limbs 0 .. the last drain's
-    tc::finish_element<NW>(g, nl, g.acc, (size_t)g.mp * g.np, (size_t)j * g.mp + i, i, j, 0, 0, false);
+    // a tile split into pair-range chunks holds its limbs in its slot
+    const int slot = P.tile_slot ? P.tile_slot[(i / tc::BM) + (j / P.bn) * (uint32_t)(P.mp / tc::BM)] : -1;
+    if (slot < 0) {
+        tc::finish_element<NW>(g, nl, g.acc, (size_t)g.mp * g.np, (size_t)j * g.mp + i, i, j, 0, 0, false);
+    } else {
+        const size_t sstride = (size_t)P.bn * tc::BM;
+        tc::finish_element<NW>(g, nl, P.sacc + (size_t)slot * (4 * P.acc_words + 1) * sstride, sstride,
+                               (size_t)(j % P.bn) * tc::BM + (i % tc::BM), i, j, 0, 0, false);
+    }
 }
 
 // one launch of the rounding pass (accumulator words nw, 2 .. 7)
@@ -188,6 +198,11 @@ struct Group {              // problems sharing a component type (batched split 
 struct Batch {
     int count = 0, form = 0;
     bool bal = false;              // balanced radix-32 e4m3 digits (FORM_FP8_BAL)
+    // pair-range splits of the most expensive tiles: per problem, the byte
+    // offsets (into ws) of its split-limb slots and chunk counters, and the
+    // meta offset of its tile -> slot map (0: no split tile)
+    size_t off_split = 0, split_bytes = 0;
+    std::vector<size_t> sacc_off, cnt_off, tslot_off;
     std::vector<ozmp_plan_s> subs;
     std::vector<size_t> ws_off;
     std::vector<int> bn;
@@ -379,6 +394,104 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
             b->ws_off[i] = off;
             off = a256(off + s.ws_bytes);
         }
+        // items of the persistent product launch (FP8): whole tiles, and the
+        // most expensive tiles split into pair-range chunks (the pair sum is
+        // the scheme's reduction dimension, split like split-k; chunks add
+        // exactly into the tile's limb slot) until every tile is below the
+        // balanced share of a CTA or has 8 chunks; then longest processing
+        // time first over the CTAs
+        std::vector<tc::WorkItem> items;
+        std::vector<int> cta_off;
+        std::vector<std::vector<int>> tslots(count);
+        b->sacc_off.assign(count, 0);
+        b->cnt_off.assign(count, 0);
+        b->tslot_off.assign(count, 0);
+        if (fm == OZMP_FORM_FP8) {
+            struct Tl { int p, tile, nch; double cost; };
+            std::vector<Tl> tl;
+            double total = 0.0;
+            for (int i = 0; i < count; ++i) {
+                const ozmp_plan_s& s = b->subs[i];
+                if (s.m == 0 || s.n == 0 || s.k == 0) continue;
+                const int tiles = (int)((s.mp / tc::BM) * (s.np / b->bn[i]));
+                const double c = (double)(s.s * (s.s + 1) / 2) * (double)(s.kp / tc::BK) *
+                                 (b->bn[i] == 128 ? g_cost128 : g_cost256) + 4.0;
+                for (int t = 0; t < tiles; ++t) tl.push_back({i, t, 1, c});
+                total += c * tiles;
+            }
+            const int sms = tc_num_sms();
+            const char* senv = getenv("OZMP_BATCH_SPLIT");
+            const bool split_on = !(senv && senv[0] == '0');
+            if (split_on && !tl.empty()) {
+                const double share = total / (2.0 * sms);   // half a CTA's balanced load
+                typedef std::pair<double, int> Ck;           // (cost of one chunk, tile)
+                std::priority_queue<Ck> pq;
+                for (int x = 0; x < (int)tl.size(); ++x) pq.push({tl[x].cost, x});
+                while (!pq.empty()) {
+                    const Ck top = pq.top();
+                    if (top.first <= share) break;
+                    pq.pop();
+                    Tl& t = tl[top.second];
+                    const int pairs = b->subs[t.p].s * (b->subs[t.p].s + 1) / 2;
+                    if (t.nch >= 8 || t.nch >= pairs) continue;
+                    ++t.nch;
+                    pq.push({t.cost / t.nch + 4.0, top.second});
+                }
+            }
+            // slots of the split tiles, per problem, in the split region of ws
+            std::vector<int> nslots(count, 0);
+            for (Tl& t : tl)
+                if (t.nch > 1) {
+                    if (tslots[t.p].empty()) {
+                        const ozmp_plan_s& s = b->subs[t.p];
+                        tslots[t.p].assign((size_t)((s.mp / tc::BM) * (s.np / b->bn[t.p])), -1);
+                    }
+                    tslots[t.p][t.tile] = nslots[t.p]++;
+                }
+            size_t so = 0;
+            for (int i = 0; i < count; ++i) {
+                if (!nslots[i]) continue;
+                const ozmp_plan_s& s = b->subs[i];
+                b->sacc_off[i] = so;
+                so = a256(so + (size_t)nslots[i] * (4 * s.acc_words + 1) * b->bn[i] * tc::BM * 8);
+            }
+            for (int i = 0; i < count; ++i) {
+                if (!nslots[i]) continue;
+                b->cnt_off[i] = so;
+                so = a256(so + (size_t)nslots[i] * 4);
+            }
+            b->off_split = off;
+            b->split_bytes = so;
+            off = a256(off + so);
+            // the chunks, costliest first, dealt longest-processing-time first
+            struct It { int p, tile, pa, pb, slot, nch; double cost; };
+            std::vector<It> all;
+            for (const Tl& t : tl) {
+                const int pairs = b->subs[t.p].s * (b->subs[t.p].s + 1) / 2;
+                const int slot = t.nch > 1 ? tslots[t.p][t.tile] : -1;
+                for (int x = 0; x < t.nch; ++x)
+                    all.push_back({t.p, t.tile, (int)((int64_t)pairs * x / t.nch),
+                                   (int)((int64_t)pairs * (x + 1) / t.nch), slot, t.nch,
+                                   t.nch > 1 ? t.cost / t.nch + 4.0 : t.cost});
+            }
+            std::stable_sort(all.begin(), all.end(), [](const It& x, const It& y) { return x.cost > y.cost; });
+            b->grid = (int)std::min<size_t>(all.size(), (size_t)sms);
+            std::vector<std::vector<tc::WorkItem>> per(b->grid > 0 ? b->grid : 1);
+            typedef std::pair<double, int> Load;
+            std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+            for (int c = 0; c < b->grid; ++c) heap.push({0.0, c});
+            for (const It& x : all) {
+                Load l = heap.top();
+                heap.pop();
+                per[l.second].push_back(tc::WorkItem{x.p, x.tile, x.pa, x.pb, x.slot, x.nch});
+                heap.push({l.first + x.cost, l.second});
+            }
+            cta_off.push_back(0);
+            for (int c = 0; c < b->grid; ++c) {
+                for (const tc::WorkItem& w : per[c]) items.push_back(w);
+                cta_off.push_back((int)items.size());
+            }
+        }
         b->ws_bytes = off;
         if (cudaMalloc(&b->ws, b->ws_bytes ? b->ws_bytes : 256) != cudaSuccess) {
             cudaGetLastError();
@@ -402,39 +515,6 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
                 }
             if (!g.ids.empty()) b->groups.push_back(g);
         }
-        // items of the persistent product launch (FP8) and their balance
-        std::vector<tc::WorkItem> items;
-        std::vector<int> cta_off;
-        if (fm == OZMP_FORM_FP8) {
-            struct It { int p, tile; double cost; };
-            std::vector<It> all;
-            for (int i = 0; i < count; ++i) {
-                const ozmp_plan_s& s = b->subs[i];
-                if (s.m == 0 || s.n == 0 || s.k == 0) continue;
-                const int tiles = (int)((s.mp / tc::BM) * (s.np / b->bn[i]));
-                const double c = (double)(s.s * (s.s + 1) / 2) * (double)(s.kp / tc::BK) *
-                                 (b->bn[i] == 128 ? g_cost128 : g_cost256) + 4.0;
-                for (int t = 0; t < tiles; ++t) all.push_back({i, t, c});
-            }
-            std::stable_sort(all.begin(), all.end(), [](const It& x, const It& y) { return x.cost > y.cost; });
-            b->grid = (int)std::min<size_t>(all.size(), (size_t)tc_num_sms());
-            std::vector<std::vector<tc::WorkItem>> per(b->grid > 0 ? b->grid : 1);
-            typedef std::pair<double, int> Load;
-            std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-            for (int c = 0; c < b->grid; ++c) heap.push({0.0, c});
-            for (const It& x : all) {
-                Load l = heap.top();
-                heap.pop();
-                const ozmp_plan_s& sx = b->subs[x.p];
-                per[l.second].push_back(tc::WorkItem{x.p, x.tile, 0, sx.s * (sx.s + 1) / 2, -1, 1});
-                heap.push({l.first + x.cost, l.second});
-            }
-            cta_off.push_back(0);
-            for (int c = 0; c < b->grid; ++c) {
-                for (const tc::WorkItem& w : per[c]) items.push_back(w);
-                cta_off.push_back((int)items.size());
-            }
-        }
         // device meta layout
         size_t mo = 0;
         std::vector<std::vector<int>> pre_host;
@@ -450,6 +530,8 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
         b->off_maps = mo; mo = a256(mo + sizeof(CUtensorMap) * 2 * count);
         b->off_items = mo; mo = a256(mo + sizeof(tc::WorkItem) * (items.size() + 1));
         b->off_cta = mo; mo = a256(mo + sizeof(int) * (cta_off.size() + 1));
+        for (int i = 0; i < count; ++i)
+            if (!tslots[i].empty()) { b->tslot_off[i] = mo; mo = a256(mo + sizeof(int) * tslots[i].size()); }
         // the rounding pass over the limbs runs after the product launch (unless
         // OZMP_BATCH_DEFER=0 keeps the rounding inside the product kernel)
         std::vector<std::vector<int>> fids, fpre;
@@ -526,6 +608,9 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
         }
         memcpy(host.data() + (b->off_items - b->off_maps), items.data(), sizeof(tc::WorkItem) * items.size());
         memcpy(host.data() + (b->off_cta - b->off_maps), cta_off.data(), sizeof(int) * cta_off.size());
+        for (int i = 0; i < count; ++i)
+            if (!tslots[i].empty())
+                memcpy(host.data() + (b->tslot_off[i] - b->off_maps), tslots[i].data(), sizeof(int) * tslots[i].size());
         for (size_t x = 0; x < b->fin.size(); ++x) {
             memcpy(host.data() + (b->fin[x].off_ids - b->off_maps), fids[x].data(), sizeof(int) * fids[x].size());
             memcpy(host.data() + (b->fin[x].off_pre - b->off_maps), fpre[x].data(), sizeof(int) * fpre[x].size());
@@ -580,6 +665,11 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
         p.bn = b->bn[i];
         p.defer = b->fin.empty() ? 0 : 1;
         p.eoff = b->bal ? 2 : 0;
+        if (b->tslot_off.size() == (size_t)count && b->tslot_off[i]) {
+            p.sacc = (int64_t*)((char*)b->ws + b->off_split + b->sacc_off[i]);
+            p.cnt = (int*)((char*)b->ws + b->off_split + b->cnt_off[i]);
+            p.tile_slot = (const int*)((char*)b->meta + b->tslot_off[i]);
+        }
     }
 
     // ---------------------------------------------------------------- graph
@@ -645,6 +735,8 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
                         else split_group<double, OZMP_FORM_FP8>(g.nw, g.blocks, sp, pre, cnt, sm, cs);
                     }
                 }
+                if (b->split_bytes)
+                    cudaMemsetAsync((char*)b->ws + b->off_split, 0, b->split_bytes, cs);
                 if (b->grid > 0) {
                     tc::Sched sc;
                     sc.probs = (const tc::Prob*)((char*)b->meta + b->off_probs);

@@ -290,6 +290,7 @@ struct Prob {
     int64_t* T;            // diagnostic output (d_only)
     int64_t* sacc;         // split tiles: [slot][nlimbs][bn][BM] limbs, zeroed before the launch
     int* cnt;              // split tiles: chunks finished per slot, zeroed before the launch
+    const int* tile_slot;  // batched mode: split-limb slot of each tile, or -1 (null: no split tile)
     int64_t m, n, mp, np, kp, ldc;
     int q, is_f32, s, beta, ppd, acc_words, bn, d_only;
     int eoff;              // exponent offset of the digit weights (2: balanced digits)

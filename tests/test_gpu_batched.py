@@ -92,3 +92,21 @@ def test_batched_rejects_more_than_four_components_and_wide_windows():
     with pytest.raises(oz.OzmpError) as e:
         oz.ozmp_gemm_batched(probs)
     assert e.value.status == oz.Status.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("split", ["1", "0"])
+def test_few_large_problems_split_into_pair_ranges(split, monkeypatch):
+    # a batch of few tiles: the autotuner splits the tiles' pair walks into
+    # chunks that add exactly into limb slots (OZMP_BATCH_SPLIT=0: whole
+    # tiles); either way the results equal the single products bit for bit
+    monkeypatch.setenv("OZMP_BATCH_SPLIT", split)
+    shapes = [(520, 600, 300, "dd"), (260, 300, 200, "td"), (130, 70, 90, "qd")]
+    probs = _make(shapes, 300)
+    plan = oz.ozmp_gemm_batched(probs)
+    torch.cuda.synchronize()
+    assert oz.ozmp_plan_get_status(plan) == oz.Status.OK
+    for (prec, A, B, C, ns), (m, n, k, _) in zip(probs, shapes):
+        ref = _single(prec, A, B, "auto")
+        for x, y in zip(C, ref):
+            assert torch.equal(x, y), (prec, m, n, k)
+    oz.ozmp_plan_destroy(plan)
