@@ -94,12 +94,15 @@ def test_batched_rejects_more_than_four_components_and_wide_windows():
     assert e.value.status == oz.Status.ERR_UNSUPPORTED
 
 
-@pytest.mark.parametrize("split", ["1", "0"])
-def test_few_large_problems_split_into_pair_ranges(split, monkeypatch):
+@pytest.mark.parametrize("split,defer", [("1", "1"), ("0", "1"), ("1", "0")])
+def test_few_large_problems_split_into_pair_ranges(split, defer, monkeypatch):
     # a batch of few tiles: the autotuner splits the tiles' pair walks into
     # chunks that add exactly into limb slots (OZMP_BATCH_SPLIT=0: whole
-    # tiles); either way the results equal the single products bit for bit
+    # tiles); the split tiles are rounded by the rounding pass, or with
+    # OZMP_BATCH_DEFER=0 by the last chunk to finish; every way the results
+    # equal the single products bit for bit
     monkeypatch.setenv("OZMP_BATCH_SPLIT", split)
+    monkeypatch.setenv("OZMP_BATCH_DEFER", defer)
     shapes = [(520, 600, 300, "dd"), (260, 300, 200, "td"), (130, 70, 90, "qd")]
     probs = _make(shapes, 300)
     plan = oz.ozmp_gemm_batched(probs)
