@@ -429,7 +429,8 @@ bool tc_make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t kp, u
 }
 
 int tc_schedule(int ntiles, int pairs, int sms, int* items, int* off, int* nitems, int* nslots, bool regroup,
-                int tm, int group) {
+                int tm, int group, int maxc) {
+    if (maxc < 1 || maxc > TC_MAX_CHUNKS) maxc = TC_MAX_CHUNKS;
     if (sms < 1) sms = 1;
     // tile order: bands of `group` row tiles, column by column within a band
     // (group <= 0: plain column-major order of the tiles)
@@ -447,7 +448,7 @@ int tc_schedule(int ntiles, int pairs, int sms, int* items, int* off, int* nitem
     // chunks per tail tile: minimise waves + ceil(r c / sms) / c (+ a small per-chunk cost)
     int best_c = 1;
     double best = 1e30;
-    for (int c = 1; c <= 8 && c <= pairs; ++c) {
+    for (int c = 1; c <= maxc && c <= pairs; ++c) {
         if (r == 0 && c > 1) break;
         const double span = waves + (r ? (double)((r * c + sms - 1) / sms) / c : 0.0) + 0.002 * c;
         if (span < best - 1e-9) { best = span; best_c = c; }

@@ -69,8 +69,10 @@ struct GemmArgs {
 // prob, tile, pa, pb, slot, nchunks), regrouped per CTA with CTA offsets when
 // `regroup` (else in creation order for the dynamic feed); returns the grid.
 // Tiles are taken in bands of `group` of the tm row tiles (0: column-major).
+// maxc: pair-range chunks of one tail tile at most (0: TC_MAX_CHUNKS).
+constexpr int TC_MAX_CHUNKS = 32;
 int tc_schedule(int ntiles, int pairs, int sms, int* items, int* off, int* nitems, int* nslots, bool regroup,
-                int tm, int group);
+                int tm, int group, int maxc = 0);
 int tc_num_sms();
 int tc_num_pair_slots();   // co-resident clusters of two CTAs of the tcgen05 pair form
 

@@ -263,11 +263,11 @@ inline ozmp_status plan_schedule(ozmp_plan_s* p) {
     const int ntiles = (int)((p->mp / (128 * p->tc_cg)) * (p->np / 256));
     const int pairs = p->s * (p->s + 1) / 2;
     const int sms = p->tc_cg == 2 ? tc_num_pair_slots() : tc_num_sms();
-    p->sched_host = new (std::nothrow) int[(size_t)6 * ntiles * 8 + sms + 1 + ntiles];
+    p->sched_host = new (std::nothrow) int[(size_t)6 * ntiles * TC_MAX_CHUNKS + sms + 1 + ntiles];
     p->sched_ntiles = ntiles;
     if (!p->sched_host) return OZMP_ERR_NOMEM;
     int* items = p->sched_host;
-    int* off = p->sched_host + (size_t)6 * ntiles * 8;
+    int* off = p->sched_host + (size_t)6 * ntiles * TC_MAX_CHUNKS;
     // test hooks of the bounded waits: a smaller poll limit, and a stage whose
     // copies are never issued so that the waits on it run out
     const char* wl = getenv("OZMP_TC_WAIT_LIMIT");
@@ -277,9 +277,10 @@ inline ozmp_status plan_schedule(ozmp_plan_s* p) {
     const char* dyn = getenv("OZMP_TC_DYNAMIC");
     p->tc_dyn = !(dyn && dyn[0] == '0');
     const char* grp = getenv("OZMP_TC_GROUP");
+    const char* mxc = getenv("OZMP_TC_MAX_CHUNKS");
     const int tm = (int)(p->mp / (128 * p->tc_cg));
     p->sched_grid = tc_schedule(ntiles, pairs, sms, items, off, &p->sched_items, &p->sched_slots, !p->tc_dyn, tm,
-                                grp ? atoi(grp) : 0);
+                                grp ? atoi(grp) : 0, mxc ? atoi(mxc) : 0);
     p->sched_slots *= p->tc_cg;
     // CTA offsets right after the items in the host copy
     int* off2 = items + 6 * p->sched_items;
