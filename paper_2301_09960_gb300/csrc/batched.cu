@@ -398,8 +398,8 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
         // most expensive tiles split into pair-range chunks (the pair sum is
         // the scheme's reduction dimension, split like split-k; chunks add
         // exactly into the tile's limb slot) until every tile is below the
-        // balanced share of a CTA or has 8 chunks; then longest processing
-        // time first over the CTAs
+        // balanced share of a CTA or has TC_MAX_CHUNKS chunks; then longest
+        // processing time first over the CTAs
         std::vector<tc::WorkItem> items;
         std::vector<int> cta_off;
         std::vector<std::vector<int>> tslots(count);
@@ -433,7 +433,7 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
                     pq.pop();
                     Tl& t = tl[top.second];
                     const int pairs = b->subs[t.p].s * (b->subs[t.p].s + 1) / 2;
-                    if (t.nch >= 8 || t.nch >= pairs) continue;
+                    if (t.nch >= TC_MAX_CHUNKS || t.nch >= pairs) continue;
                     ++t.nch;
                     pq.push({t.cost / t.nch + 4.0, top.second});
                 }
