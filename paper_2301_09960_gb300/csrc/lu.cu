@@ -98,10 +98,14 @@ __device__ __forceinline__ void stage(const Mat& A, int n, double* S) {
 // computes its reciprocal while the other warps go on, and every l_ik is
 // then one multiplication, all in parallel.  The values are those of the
 // sequential order.
-constexpr int LU_WARPS = 16;
+// warps of the base LU: 32 (a phase of up to 63 entries in two rounds) for
+// two components, 16 where the exact windows need more registers
+template <int Q>
+struct LuWarps { static constexpr int N = Q == 2 ? 32 : 16; };
 
 template <int Q>
-__global__ void __launch_bounds__(32 * LU_WARPS) k_base_lu(Mat A, int n, uint32_t* status) {
+__global__ void __launch_bounds__(32 * LuWarps<Q>::N) k_base_lu(Mat A, int n, uint32_t* status) {
+    constexpr int LU_WARPS = LuWarps<Q>::N;
     __shared__ double S[Q * NB * NB];
     __shared__ double R[Q];
     __shared__ int bad_any;
@@ -436,9 +440,9 @@ static void lu_rec(Ctx& x, const Mat& A, int64_t n) {
     if (n <= NB) {
         if (!x.dry) {
             switch (x.q) {
-                case 2: k_base_lu<2><<<1, 32 * LU_WARPS, 0, x.st>>>(A, (int)n, x.status); break;
-                case 3: k_base_lu<3><<<1, 32 * LU_WARPS, 0, x.st>>>(A, (int)n, x.status); break;
-                default: k_base_lu<4><<<1, 32 * LU_WARPS, 0, x.st>>>(A, (int)n, x.status); break;
+                case 2: k_base_lu<2><<<1, 32 * LuWarps<2>::N, 0, x.st>>>(A, (int)n, x.status); break;
+                case 3: k_base_lu<3><<<1, 32 * LuWarps<3>::N, 0, x.st>>>(A, (int)n, x.status); break;
+                default: k_base_lu<4><<<1, 32 * LuWarps<4>::N, 0, x.st>>>(A, (int)n, x.status); break;
             }
         }
         return;
