@@ -88,8 +88,8 @@ typedef enum {
 #define OZMP_EXP_ZERO ((int32_t)(-2147483647 - 1))
 /* largest slice count accepted as an argument; each form provides fewer:
  * FP8 (tcgen05) up to 239 and FP8_BAL up to 191 (beta s + 65 <= 1024 window
- * bits), FP8_MMA 64, INT8 36, FP64 up to beta s <= 376; above the form's
- * limit plan creation returns OZMP_ERR_UNSUPPORTED */
+ * bits; TS: 64 and 63), FP8_MMA 64, INT8 36, FP64 up to beta s <= 376; above
+ * the form's limit plan creation returns OZMP_ERR_UNSUPPORTED */
 #define OZMP_MAX_SLICES 256
 
 /* cudaStream_t, passed as an opaque pointer (NULL = the legacy default stream) */

@@ -366,6 +366,7 @@ inline ozmp_status plan_init(ozmp_plan_s* p, int prec, int64_t m, int64_t n, int
     if (nslices > maxs || nslices * p->beta > maxbits) return OZMP_ERR_UNSUPPORTED;
     p->s = nslices;
     p->big = (q > 4 || nslices > (p->bal ? 63 : 64)) ? 1 : 0;
+    if (p->big && p->is_f32) return OZMP_ERR_UNSUPPORTED;   // the many-component splitter reads binary64
     p->mp = roundup(m, 128);
     p->np = roundup(n, p->form == OZMP_FORM_FP8 ? 256 : 128);
     p->kp = roundup(k, 128);

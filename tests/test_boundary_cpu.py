@@ -184,3 +184,15 @@ def test_automatic_form_choice():
             assert oz.ozmp_plan_get_info(h).form == want, (q, ns)
         finally:
             oz.ozmp_plan_destroy(h)
+
+
+def test_triple_single_slice_limits():
+    # binary32 components go through the register splitter only: up to 63
+    # balanced or 64 four-bit slices
+    for form, s in [(oz.Form.FP8_BAL, 63), (oz.Form.FP8, 64)]:
+        h = oz.ozmp_plan_create(oz.Prec.TS, 10, 10, 10, form, s, None)
+        oz.ozmp_plan_destroy(h)
+    for form, s in [(oz.Form.FP8_BAL, 64), (oz.Form.FP8, 65)]:
+        with pytest.raises(oz.OzmpError) as e:
+            oz.ozmp_plan_create(oz.Prec.TS, 10, 10, 10, form, s, None)
+        assert e.value.status == oz.Status.ERR_UNSUPPORTED
