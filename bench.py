@@ -261,7 +261,7 @@ def lu_variant(oz, torch):
     return out
 
 
-def config2(oz, torch):
+def td_qd_1024_variant(oz, torch):
     """TD and QD 1024^3, binary64 slices (and e4m3 slices), with the simple
     multi-component GEMM as the side baseline (one timed pass each)."""
     out = []
@@ -289,7 +289,7 @@ def config2(oz, torch):
     return out
 
 
-def config4(oz, torch):
+def batched_512_variant(oz, torch):
     """512 uneven DD/TD problems (m, n, k log-uniform in [32, 768], seed 1):
     one graph replay of the batched plan vs a loop of single calls."""
     from ozmp_inputs import batched_problem_shapes, gen_problem
@@ -359,7 +359,7 @@ def main():
         print(json.dumps({"side": args.side, "result": SIDE[args.side](oz, torch)}))
         return
     ws, rank, local = _dist()
-    workload = f"{args.prec} gemm m=n=k={args.n}, phi={args.phi}, Eq. 1 operands (configs: DD/QD 4096^3 fp64 vs int8 slices)"
+    workload = f"{args.prec} gemm m=n=k={args.n}, phi={args.phi}, Eq. 1 operands"
     metric = "DD/QD GEMM effective GFLOP/s (2mnk/s) and % of slice roofline, INT8 vs FP64"
 
     if args.impl == "reference":
@@ -606,10 +606,10 @@ def main():
 
 # the side measurements that can run alone (--side)
 SIDE = {
-    "config4_batched512": lambda oz, torch: config4(oz, torch),
+    "batched_512_problems": lambda oz, torch: batched_512_variant(oz, torch),
     "lu_4096": lambda oz, torch: lu_variant(oz, torch),
     "literal_vs_truncating_1024": lambda oz, torch: literal_variant(oz, torch),
-    "config2_td_qd_1024": lambda oz, torch: config2(oz, torch),
+    "td_qd_1024": lambda oz, torch: td_qd_1024_variant(oz, torch),
 }
 
 
@@ -639,8 +639,8 @@ def add_variants(line, oz, torch, args):
     line["multiprecision_2048"] = md
     line["lu_4096"] = lu_variant(oz, torch)
     line["literal_vs_truncating_1024"] = literal_variant(oz, torch)
-    line["config2_td_qd_1024"] = config2(oz, torch)
-    line["config4_batched512"] = config4(oz, torch)
+    line["td_qd_1024"] = td_qd_1024_variant(oz, torch)
+    line["batched_512_problems"] = batched_512_variant(oz, torch)
 
 
 if __name__ == "__main__":
