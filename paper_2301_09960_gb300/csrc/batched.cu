@@ -143,12 +143,19 @@ template <int NW>
 __global__ void __launch_bounds__(256) k_b_finish(const tc::Prob* probs, const int* ids, const int* pre, int count,
                                                   uint32_t* status) {
     __shared__ GemmArgs g;
-    __shared__ tc::Prob P;
     __shared__ int x;
+    // the split-tile fields of the problem
+    __shared__ const int* tslot;
+    __shared__ int64_t* sacc;
+    __shared__ int bn, slot_limbs;
     if (threadIdx.x == 0) {
         x = find_prob(pre, count, blockIdx.x);
-        P = probs[ids[x]];
-        g = tc::as_gemm_args(P, status);
+        const tc::Prob& Pg = probs[ids[x]];
+        g = tc::as_gemm_args(Pg, status);
+        tslot = Pg.tile_slot;
+        sacc = Pg.sacc;
+        bn = Pg.bn;
+        slot_limbs = 4 * Pg.acc_words + 1;
     }
     __syncthreads();
     const uint32_t m = (uint32_t)g.m;
@@ -156,14 +163,16 @@ __global__ void __launch_bounds__(256) k_b_finish(const tc::Prob* probs, const i
     if ((uint64_t)e >= (uint64_t)g.m * (uint64_t)g.n) return;
     const uint32_t j = e / m, i = e - j * m;
     const int nl = (g.beta * (g.s - 1)) / 16 + 1;   // limbs 0 .. the last drain's
-    // a tile split into pair-range chunks holds its limbs in its slot
-    const int slot = P.tile_slot ? P.tile_slot[(i / tc::BM) + (j / P.bn) * (uint32_t)(P.mp / tc::BM)] : -1;
+    // a tile split into pair-range chunks holds its limbs in its slot (tiles
+    // are 128 rows by 128 or 256 columns)
+    static_assert(tc::BM == 128, "row tiles of 128");
+    const int slot = tslot ? tslot[(i >> 7) + (j >> (bn == 256 ? 8 : 7)) * (uint32_t)(g.mp >> 7)] : -1;
     if (slot < 0) {
         tc::finish_element<NW>(g, nl, g.acc, (size_t)g.mp * g.np, (size_t)j * g.mp + i, i, j, 0, 0, false);
     } else {
-        const size_t sstride = (size_t)P.bn * tc::BM;
-        tc::finish_element<NW>(g, nl, P.sacc + (size_t)slot * (4 * P.acc_words + 1) * sstride, sstride,
-                               (size_t)(j % P.bn) * tc::BM + (i % tc::BM), i, j, 0, 0, false);
+        const size_t sstride = (size_t)bn * tc::BM;
+        tc::finish_element<NW>(g, nl, sacc + (size_t)slot * slot_limbs * sstride, sstride,
+                               (size_t)(j & (uint32_t)(bn - 1)) * tc::BM + (i & 127u), i, j, 0, 0, false);
     }
 }
 
