@@ -287,9 +287,67 @@ __device__ __forceinline__ int window_of(const Operand<T>& op, bool inside, int6
     return digit_window<NW, T>(c, v, op.q, Erow, w);
 }
 
-// the same on components already loaded (zeros outside the matrix)
-template <typename T, int NW>
+// bits [o, o + 64) of the 128-bit value s1:s0 (zeros outside it)
+__device__ __forceinline__ uint64_t bits128(uint64_t s0, uint64_t s1, int o) {
+    if (o <= -64 || o >= 128) return 0ull;
+    if (o < 0) return s0 << (-o);
+    if (o == 0) return s0;
+    if (o < 64) return (s0 >> o) | (s1 << (64 - o));
+    if (o == 64) return s1;
+    return s1 >> (o - 64);
+}
+
+// Two binary64 components whose exponents differ by at most 74: their exact
+// sum S as a signed 128-bit integer at the smaller one's exponent, then
+// floor(|S| 2^(e - L)) placed in the window in one shift (the exact
+// truncated magnitude, every word exact).  Returns false, leaving w alone,
+// when the components are further apart.
+template <int NW>
+__device__ __forceinline__ bool window_two(double hi, double lo, int Erow, uint64_t (&w)[NW], int& sg) {
+    Comp a, b;
+    decode(hi, a);
+    decode(lo, b);
+    if (b.M && (!a.M || b.e > a.e)) { const Comp t = a; a = b; b = t; }   // a: the larger exponent
+    if (!a.M || Erow == OZMP_EXP_ZERO) {
+#pragma unroll
+        for (int j = 0; j < NW; ++j) w[j] = 0;
+        sg = 0;
+        return true;
+    }
+    unsigned __int128 S;
+    int es;
+    bool neg;
+    if (!b.M) {
+        S = a.M; es = a.e; neg = a.neg != 0;
+    } else {
+        const int d = a.e - b.e;
+        if (d > 74) return false;   // 53 + 74 bits fit the signed 128-bit sum
+        __int128 sa = (__int128)((unsigned __int128)a.M << d);
+        if (a.neg) sa = -sa;
+        __int128 sb = (__int128)b.M;
+        if (b.neg) sb = -sb;
+        const __int128 t = sa + sb;
+        neg = t < 0;
+        S = neg ? (unsigned __int128)(-t) : (unsigned __int128)t;
+        es = b.e;
+    }
+    const int L = Erow - (64 * NW - 1);   // weight of window bit 0
+    const int sh = es - L;
+    const uint64_t s0 = (uint64_t)S, s1 = (uint64_t)(S >> 64);
+#pragma unroll
+    for (int j = 0; j < NW; ++j) w[j] = bits128(s0, s1, 64 * j - sh);
+    sg = S == 0 ? 0 : (neg ? -1 : 1);
+    return true;
+}
+
+// the same on components already loaded (zeros outside the matrix); two
+// binary64 components known at compile time (Q = 2) first try the 128-bit frame
+template <typename T, int NW, int Q = 0>
 __device__ __forceinline__ int window_loaded(const T (&v)[4], int q, int Erow, uint64_t (&w)[NW]) {
+    if constexpr (Q == 2 && sizeof(T) == 8) {
+        int sg;
+        if (window_two<NW>((double)v[0], (double)v[1], Erow, w, sg)) return sg;
+    }
     Comp c[4];
     int Ptop;
     decode_all<T>(v, q, c, Ptop);
@@ -328,7 +386,7 @@ __device__ __forceinline__ void split_rows_b1_body(Operand<T> a, int64_t m, int6
             load_raw<T>(a, q, i < m && p < k, i + p * a.ld, v[e]);
         }
 #pragma unroll
-        for (int e = 0; e < 4; ++e) sign[e] = window_loaded<T, NW>(v[e], q, Erow, w[e]);
+        for (int e = 0; e < 4; ++e) sign[e] = window_loaded<T, NW, Q>(v[e], q, Erow, w[e]);
         if constexpr (FORM == OZMP_FORM_FP8) {
             pack_fp8_quad<NW>(w, sign, s, [&](int t, uint32_t word) { sw[((t - 1) * TI + ri) * QW + qd] = word; });
         } else if constexpr (FORM == OZMP_FORM_FP8_BAL) {
@@ -375,7 +433,7 @@ __device__ __forceinline__ void split_cols_b1_body(Operand<T> b, int64_t k, int6
 #pragma unroll
     for (int e = 0; e < 4; ++e) load_raw<T>(b, q, j < n && p0 + e < k, p0 + e + j * b.ld, v[e]);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) sign[e] = window_loaded<T, NW>(v[e], q, Ecol, w[e]);
+    for (int e = 0; e < 4; ++e) sign[e] = window_loaded<T, NW, Q>(v[e], q, Ecol, w[e]);
     if constexpr (FORM == OZMP_FORM_FP8) {
         pack_fp8_quad<NW>(w, sign, s, [&](int t, uint32_t word) {
             *reinterpret_cast<uint32_t*>(dig + ((size_t)(t - 1) * np + j) * kp + p0) = word;
