@@ -122,3 +122,14 @@ def test_ts_8192(form):
     rows = [0, 4096, 8191]
     cols = [7, 8191]
     _sampled("ts", form, 8192, 8192, 8192, 1.0, 0, rows, cols, [0, 2], [0, 1])
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("form,k", [("fp8bal", 65536), ("fp8", 74565)])
+def test_k_at_the_exact_accumulation_limit(form, k):
+    # the largest k of each e4m3 form: a slice product of k terms reaches
+    # 2^24 (k 16^2 or k 15^2 rounded down), so every drain holds one pair
+    rows = [0, 37, 63]
+    cols = [0, 50, 95]
+    i = _sampled("dd", form, 64, 96, k, 1.0, 0, rows, cols, [0, 2], [0, 2])
+    assert i.pairs_per_drain == 1
