@@ -187,6 +187,7 @@ inline ozmp_status check_ld(const ozmp_plan_s* p, int64_t lda, int64_t ldb, int6
 
 inline SplitArgs split_args(ozmp_plan_s* p, const void* const* A, int64_t lda, const void* const* B, int64_t ldb) {
     SplitArgs a;
+    memset(&a, 0, sizeof(a));
     a.form = p->form;
     a.q = p->q;
     a.is_f32 = p->is_f32 != 0;
