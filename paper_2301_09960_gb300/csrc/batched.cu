@@ -669,7 +669,7 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
         p.E = (const int32_t*)(w + s.off_E); p.F = (const int32_t*)(w + s.off_F);
         p.acc = (int64_t*)(w + s.off_acc);
         for (int c = 0; c < OZMP_MAX_COMPONENTS; ++c) p.C[c] = c < s.q ? r.C[c] : nullptr;
-        p.m = s.m; p.n = s.n; p.k = s.k; p.mp = s.mp; p.np = s.np; p.kp = s.kp; p.ldc = r.ldc;
+        p.m = s.m; p.n = s.n; p.mp = s.mp; p.np = s.np; p.kp = s.kp; p.ldc = r.ldc;
         p.q = s.q; p.is_f32 = s.is_f32; p.s = s.s; p.beta = s.beta; p.ppd = s.ppd; p.acc_words = s.acc_words;
         p.bn = b->bn[i];
         p.defer = b->fin.empty() ? 0 : 1;

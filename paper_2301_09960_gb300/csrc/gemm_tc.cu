@@ -185,10 +185,6 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                 item_at<CG>(sc, &single, &tmA, &tmB, idx, it, rank);
                 const Prob p = *it.p;
                 const uint32_t idesc = idesc_e4m3(BM * CG, it.bn);
-                // K = 32 steps of the last chunk that hold digits: the rest of
-                // the chunk is zero padding and adds nothing
-                const int64_t krem = p.k - (int64_t)(it.KT - 1) * BK;
-                const int kk_last = (p.k > 0 && krem < BK) ? (int)((krem + 31) / 32) : BK / 32;
                 Walk w = Walk::at(it.dhi, it.pa);
                 int since = 0;
                 bool fresh = true;
@@ -201,10 +197,8 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                         tc_fence_after();
                         const uint64_t ad = desc_sw128(saddr(sA + (size_t)st * STAGE_A));
                         const uint64_t bd = desc_sw128(saddr(sB + (size_t)st * SB));
-                        const int nkk = (kc == it.KT - 1) ? kk_last : BK / 32;
 #pragma unroll
                         for (int kk = 0; kk < BK / 32; ++kk) {
-                            if (kk >= nkk) break;
                             const uint32_t acc = (fresh && kk == 0) ? 0u : 1u;
                             if (CG == 2)
                                 mma_e4m3_tc_pair(dcol, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, acc);
@@ -554,7 +548,7 @@ cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t st) {
     p.E = g.E; p.F = g.F; p.acc = g.acc;
     for (int c = 0; c < OZMP_MAX_COMPONENTS; ++c) p.C[c] = g.C[c];
     p.T = g.T;
-    p.m = g.m; p.n = g.n; p.k = g.k; p.mp = g.mp; p.np = g.np; p.kp = g.kp; p.ldc = g.ldc;
+    p.m = g.m; p.n = g.n; p.mp = g.mp; p.np = g.np; p.kp = g.kp; p.ldc = g.ldc;
     p.q = g.q; p.is_f32 = g.is_f32; p.s = g.s; p.beta = g.beta; p.ppd = g.ppd; p.acc_words = g.acc_words;
     p.eoff = g.eoff;
     p.bn = tc::BN;

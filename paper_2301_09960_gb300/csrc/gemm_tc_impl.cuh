@@ -292,7 +292,6 @@ struct Prob {
     int* cnt;              // split tiles: chunks finished per slot, zeroed before the launch
     const int* tile_slot;  // batched mode: split-limb slot of each tile, or -1 (null: no split tile)
     int64_t m, n, mp, np, kp, ldc;
-    int64_t k;             // digits beyond k are zero padding (0: treat all kp as digits)
     int q, is_f32, s, beta, ppd, acc_words, bn, d_only;
     int eoff;              // exponent offset of the digit weights (2: balanced digits)
     int defer;             // 1: the limbs are rounded into C by a separate pass after the launch
