@@ -28,7 +28,7 @@ static cudaError_t exponents_impl(const SplitArgs& g, cudaStream_t st) {
         dim3 gr((unsigned)((g.m + 255) / 256), (unsigned)((g.k + kchunk - 1) / kchunk));
         k_exp_rows<T, Q><<<gr, 256, 0, st>>>(a, g.m, g.k, kchunk, g.E, g.status);
     }
-    if (g.n > 0 && g.k > 0) {
+    if (g.n > 0 && g.k > 0 && cols_fused_smem(g) == 0) {   // else the column digit pass reduces them
         const int split = (int)((g.k + 1023) / 1024 < 8 ? (g.k + 1023) / 1024 : 8);
         k_exp_cols<T, Q><<<(unsigned)((g.n * split + 7) / 8), 256, 0, st>>>(b, g.k, g.n, g.F, g.status, split);
     }

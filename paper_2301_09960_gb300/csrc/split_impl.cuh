@@ -207,10 +207,27 @@ __device__ __forceinline__ void pack_fp8_quad(uint64_t (&w)[4][NW], const int (&
     }
 }
 
+// 32-bit word i of a multiword value (zero outside it)
+template <int NW>
+__device__ __forceinline__ uint32_t word32_of(const uint64_t (&w)[NW], int i) {
+    return (i < 0 || i >= 2 * NW) ? 0u : (uint32_t)(w[i >> 1] >> (32 * (i & 1)));
+}
+
+// bits [pos, pos + 32) of a multiword value, zeros outside it (pos >= -32).
+// With pos a compile-time constant (an unrolled digit loop) the two words are
+// fixed registers and this is a single funnel shift.
+template <int NW>
+__device__ __forceinline__ uint32_t bits32_at(const uint64_t (&w)[NW], int pos) {
+    const int i = (pos + 32) / 32 - 1;     // floor(pos / 32) for pos >= -32
+    const int r = pos - 32 * i;
+    return __funnelshift_r(word32_of<NW>(w, i), word32_of<NW>(w, i + 1), r);
+}
+
 // The balanced radix-32 e4m3 digits of four elements (consecutive k), all
 // slices: calls put(t, word) for t = 1 .. s with byte e of `word` = e4m3 code
 // of digit t of element e.  The magnitude window holds
-// floor(|x| 2^(64 NW - 1 - E)); group t of its top 5 s bits is digit t of
+// floor(|x| 2^(64 NW - 1 - E)) with at least GUARD bits below the lowest
+// group; group t of its top 5 s bits is digit t of
 // N = floor(|x| 2^(5 s - 1 - E)) in plain radix 32.  Adding 16 to every
 // group (G = window + sum_t 16 2^(64 NW - 5 t), nothing added below the
 // lowest group, so no carry enters it) makes the groups of G the balanced
@@ -218,11 +235,13 @@ __device__ __forceinline__ void pack_fp8_quad(uint64_t (&w)[4][NW], const int (&
 // group turns d_1 into 16.  Each g goes through binary16 as 1024 + g (exact),
 // one fused multiply-add applies -16 and the element's sign (exact: the
 // result is an integer of magnitude <= 16, a zero digit comes out +0), and
-// the conversion to e4m3 is exact for these integers.
-template <int NW, typename Put>
+// the conversion to e4m3 is exact for these integers.  Two elements share
+// one binary16 pair: element 2h's group is cut out at bit 0 and element
+// 2h + 1's at bit 16, each by one funnel shift.
+template <int NW, int GUARD, typename Put>
 __device__ __forceinline__ void pack_bal_quad(uint64_t (&w)[4][NW], const int (&sign)[4], int s, Put&& put) {
-    constexpr int TMAX = (64 * NW - 65) / 5;
-    const int lo = 64 * NW - 5 * s;   // lowest bit of the lowest group (>= 65)
+    constexpr int TMAX = (64 * NW - GUARD) / 5;
+    const int lo = 64 * NW - 5 * s;   // lowest bit of the lowest group (>= GUARD)
     constexpr BalSixteens<NW> P16;
     uint64_t H[NW];
 #pragma unroll
@@ -230,14 +249,14 @@ __device__ __forceinline__ void pack_bal_quad(uint64_t (&w)[4][NW], const int (&
         const uint64_t keep = (lo <= 64 * j) ? ~0ull : (lo >= 64 * j + 64 ? 0ull : (~0ull << (lo - 64 * j)));
         H[j] = P16.w[j] & keep;
     }
-    uint32_t top[4];
+    uint32_t top[2] = {0u, 0u};
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         // the top word gets bit 63 of H and never equals its old value: it
         // wrapped (the carry out of the top group) iff it came out smaller
         const uint64_t before = w[e][NW - 1];
         mw_add<NW>(w[e], H);
-        top[e] = (w[e][NW - 1] < before) ? 32u : 0u;
+        if (w[e][NW - 1] < before) top[e >> 1] |= (e & 1) ? 0x200000u : 0x20u;
     }
     // per pair of elements: binary16 multipliers (+-1) and addends (-+1040)
     __half2 mul[2], add[2];
@@ -251,25 +270,18 @@ __device__ __forceinline__ void pack_bal_quad(uint64_t (&w)[4][NW], const int (&
     for (int t = 1; t <= TMAX; ++t) {
         if (t > s) break;
         const int pos = 64 * NW - 5 * t;
-        const int wi = pos >> 6, off = pos & 63;
-        uint32_t g[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            uint64_t x = w[e][wi] >> off;
-            if (off > 59) x |= w[e][wi + 1] << (64 - off);
-            g[e] = ((uint32_t)x & 31u) | (t == 1 ? top[e] : 0u);
-        }
-        uint32_t word = 0;
+        uint32_t c[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const uint32_t bits = 0x64006400u | g[2 * h] | (g[2 * h + 1] << 16);   // 1024 + g, two lanes
+            const uint32_t x0 = bits32_at<NW>(w[2 * h], pos);         // group at bits 0..4
+            const uint32_t x1 = bits32_at<NW>(w[2 * h + 1], pos - 16);  // group at bits 16..20
+            uint32_t bits = (x0 & 0x1Fu) | (x1 & 0x1F0000u) | 0x64006400u;   // 1024 + g, two lanes
+            if (t == 1) bits |= top[h];
             __half2 v = *reinterpret_cast<const __half2*>(&bits);
             v = __hfma2(v, mul[h], add[h]);
-            const __nv_fp8x2_storage_t c8 =
-                __nv_cvt_halfraw2_to_fp8x2(static_cast<__half2_raw>(v), __NV_SATFINITE, __NV_E4M3);
-            word |= (uint32_t)c8 << (16 * h);
+            c[h] = (uint32_t)__nv_cvt_halfraw2_to_fp8x2(static_cast<__half2_raw>(v), __NV_SATFINITE, __NV_E4M3);
         }
-        put(t, word);
+        put(t, __byte_perm(c[0], c[1], 0x5410));
     }
 }
 
@@ -359,17 +371,65 @@ __device__ __forceinline__ int window_loaded(const T (&v)[4], int q, int Erow, u
     return digit_window<NW, T>(c, v, q, Erow, w);
 }
 
+// Two binary64 components: the top three words of the four-word window, that
+// is floor(|x| 2^(191 - E)) with no guard bits, which is all that balanced
+// digits of up to 38 slices read.  The 128-bit frame gives it directly;
+// components more than 74 binades apart take the general window.
+template <typename T>
+__device__ __forceinline__ int window_top3(const T (&v)[4], int Erow, uint64_t (&w3)[3]) {
+    int sg;
+    if (window_two<3>((double)v[0], (double)v[1], Erow, w3, sg)) return sg;
+    uint64_t w4[4];
+    sg = window_loaded<T, 4, 0>(v, 2, Erow, w4);
+    w3[0] = w4[1];
+    w3[1] = w4[2];
+    w3[2] = w4[3];
+    return sg;
+}
+
+// balanced digits of two binary64 components read a three-word window
+template <typename T, int FORM, int NW, int Q>
+constexpr bool kDigitsDD3 = FORM == OZMP_FORM_FP8_BAL && Q == 2 && sizeof(T) == 8 && NW == 4;
+
+// the digits of four loaded elements (consecutive k) that share the exponent
+// Ex: put(t, word) for t = 1 .. s, byte e of word = digit t of element e
+template <typename T, int FORM, int NW, int Q, typename Put>
+__device__ __forceinline__ void quad_digits(const T (&v)[4][4], int q, int Ex, int s, Put&& put) {
+    int sign[4];
+    if constexpr (kDigitsDD3<T, FORM, NW, Q>) {
+        uint64_t w3[4][3];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) sign[e] = window_top3<T>(v[e], Ex, w3[e]);
+        pack_bal_quad<3, 0>(w3, sign, s, put);
+    } else {
+        uint64_t w[4][NW];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) sign[e] = window_loaded<T, NW, Q>(v[e], q, Ex, w[e]);
+        if constexpr (FORM == OZMP_FORM_FP8) {
+            pack_fp8_quad<NW>(w, sign, s, put);
+        } else if constexpr (FORM == OZMP_FORM_FP8_BAL) {
+            pack_bal_quad<NW, 65>(w, sign, s, put);
+        } else {
+#pragma unroll
+            for (int t = 1; t <= DigitTraits<FORM>::MAXS; ++t)
+                if (t <= s) put(t, pack4<FORM, NW>(w, sign, t));
+        }
+    }
+}
+
 // Rows of A (column-major) -> Adig[(t * mp + i) * kp + p], 1-byte digits.
 // Tile: 32 rows x 64 columns, 256 threads; thread (row ri, quad) handles
 // 4 consecutive columns of one row (two quads per thread); the 4 digits of
-// a slice go to shared memory as one word [t][ri][quad], then the tile is
-// written K-contiguous.
+// a slice go to shared memory as one word, then the tile is written
+// K-contiguous in 16-byte pieces.  Word qd of tile row ri sits at position
+// qd ^ (ri >> 1) of its 16-word row: the 32 rows of a warp's store then fall
+// in 32 different banks, and so do the words of a warp's read-out.
 template <typename T, int FORM, int NW, int Q = 0>
 __device__ __forceinline__ void split_rows_b1_body(Operand<T> a, int64_t m, int64_t k, const int32_t* E,
                                                        uint8_t* dig, int64_t mp, int64_t kp, int s, int64_t bx, int64_t by) {
     const int q = Q ? Q : a.q;
     constexpr int TI = 32, TP = 64, QW = TP / 4;    // 16 words per tile row
-    extern __shared__ __align__(16) uint32_t sw[];  // [s][TI][QW]
+    extern __shared__ __align__(16) uint32_t sw[];  // [s][TI][QW], swizzled rows
     const int64_t i0 = bx * TI, p0 = by * TP;
     const int ri = threadIdx.x & 31;
     const int64_t i = i0 + ri;
@@ -377,31 +437,28 @@ __device__ __forceinline__ void split_rows_b1_body(Operand<T> a, int64_t m, int6
 #pragma unroll 1
     for (int h = 0; h < 2; ++h) {
         const int qd = (threadIdx.x >> 5) + 8 * h;
-        uint64_t w[4][NW];
-        int sign[4];
+        uint32_t* const srow = sw + ri * QW + (qd ^ (ri >> 1));
         T v[4][4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int64_t p = p0 + 4 * qd + e;
             load_raw<T>(a, q, i < m && p < k, i + p * a.ld, v[e]);
         }
-#pragma unroll
-        for (int e = 0; e < 4; ++e) sign[e] = window_loaded<T, NW, Q>(v[e], q, Erow, w[e]);
-        if constexpr (FORM == OZMP_FORM_FP8) {
-            pack_fp8_quad<NW>(w, sign, s, [&](int t, uint32_t word) { sw[((t - 1) * TI + ri) * QW + qd] = word; });
-        } else if constexpr (FORM == OZMP_FORM_FP8_BAL) {
-            pack_bal_quad<NW>(w, sign, s, [&](int t, uint32_t word) { sw[((t - 1) * TI + ri) * QW + qd] = word; });
-        } else {
-#pragma unroll
-            for (int t = 1; t <= DigitTraits<FORM>::MAXS; ++t)
-                if (t <= s) sw[((t - 1) * TI + ri) * QW + qd] = pack4<FORM, NW>(w, sign, t);
-        }
+        quad_digits<T, FORM, NW, Q>(v, q, Erow, s, [&](int t, uint32_t word) { srow[(t - 1) * TI * QW] = word; });
     }
     __syncthreads();
-    const int total = s * TI * QW;
+    // 16 bytes (four words) per thread and step: a warp covers 8 rows x 4 pieces
+    const int total = s * TI * 4;
     for (int x = threadIdx.x; x < total; x += 256) {
-        const int t = x / (TI * QW), r = (x / QW) % TI, c = x % QW;
-        *reinterpret_cast<uint32_t*>(dig + ((size_t)t * mp + (i0 + r)) * kp + p0 + 4 * c) = sw[x];
+        const int t = x / (TI * 4), r = (x >> 2) % TI, c4 = x & 3;
+        const uint32_t* row = sw + (t * TI + r) * QW;
+        const int z = r >> 1;
+        uint4 u;
+        u.x = row[(4 * c4 + 0) ^ z];
+        u.y = row[(4 * c4 + 1) ^ z];
+        u.z = row[(4 * c4 + 2) ^ z];
+        u.w = row[(4 * c4 + 3) ^ z];
+        *reinterpret_cast<uint4*>(dig + ((size_t)t * mp + (i0 + r)) * kp + p0 + 16 * c4) = u;
     }
 }
 
@@ -427,33 +484,132 @@ __device__ __forceinline__ void split_cols_b1_body(Operand<T> b, int64_t k, int6
     const int64_t j = g / quads;
     const int64_t p0 = (g % quads) * 4;
     const int Ecol = (j < n) ? F[j] : OZMP_EXP_ZERO;
-    uint64_t w[4][NW];
-    int sign[4];
     T v[4][4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) load_raw<T>(b, q, j < n && p0 + e < k, p0 + e + j * b.ld, v[e]);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) sign[e] = window_loaded<T, NW, Q>(v[e], q, Ecol, w[e]);
-    if constexpr (FORM == OZMP_FORM_FP8) {
-        pack_fp8_quad<NW>(w, sign, s, [&](int t, uint32_t word) {
-            *reinterpret_cast<uint32_t*>(dig + ((size_t)(t - 1) * np + j) * kp + p0) = word;
-        });
-    } else if constexpr (FORM == OZMP_FORM_FP8_BAL) {
-        pack_bal_quad<NW>(w, sign, s, [&](int t, uint32_t word) {
-            *reinterpret_cast<uint32_t*>(dig + ((size_t)(t - 1) * np + j) * kp + p0) = word;
-        });
-    } else {
-#pragma unroll
-        for (int t = 1; t <= DigitTraits<FORM>::MAXS; ++t)
-            if (t <= s)
-                *reinterpret_cast<uint32_t*>(dig + ((size_t)(t - 1) * np + j) * kp + p0) = pack4<FORM, NW>(w, sign, t);
-    }
+    uint8_t* const base = dig + (size_t)j * kp + p0;
+    const size_t slice = (size_t)np * kp;
+    quad_digits<T, FORM, NW, Q>(v, q, Ecol, s, [&](int t, uint32_t word) {
+        *reinterpret_cast<uint32_t*>(base + (size_t)(t - 1) * slice) = word;
+    });
 }
 
 template <typename T, int FORM, int NW, int Q>
 __global__ void __launch_bounds__(256) k_split_cols_b1(Operand<T> b, int64_t k, int64_t n, const int32_t* F,
                                                        uint8_t* dig, int64_t np, int64_t kp, int s) {
     split_cols_b1_body<T, FORM, NW, Q>(b, k, n, F, dig, np, kp, s, (int64_t)blockIdx.x, (int64_t)blockIdx.y);
+}
+
+// ---------------------------------------------------------------------------
+// K1 + K2 for the columns of B in one pass: a block takes one column, copies
+// its components into shared memory with one bulk copy each (the whole column
+// in flight at once, no registers held), reduces the column exponent there and
+// writes the column's digits from shared memory, so B is read once.
+// ---------------------------------------------------------------------------
+namespace colbulk {
+constexpr long long WAIT_POLLS = 1ll << 24;   // try_wait polls before giving up
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void bar_init(uint64_t* b) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(saddr(b)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(saddr(b)), "r"(bytes) : "memory");
+}
+// bytes (a multiple of 16) from a 16-byte aligned global address
+__device__ __forceinline__ void copy(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     saddr(dst)),
+                 "l"(src), "r"(bytes), "r"(saddr(b))
+                 : "memory");
+}
+__device__ __forceinline__ bool wait(uint64_t* b) {
+    for (long long it = 0; it < WAIT_POLLS; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(saddr(b))
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+}  // namespace colbulk
+
+template <typename T, int FORM, int NW, int Q>
+__global__ void __launch_bounds__(256, 3) k_split_cols_fused(Operand<T> b, int64_t k, int64_t n, int32_t* F,
+                                                          uint32_t* status, uint8_t* dig, int64_t np, int64_t kp,
+                                                          int s) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
+    const T* col = reinterpret_cast<const T*>(smraw + 16);   // [Q][k]
+    __shared__ int red[8];
+    __shared__ int bad_any;
+    const int64_t j = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const bool live = j < n;   // padding columns get zero digits
+    int Ecol = OZMP_EXP_ZERO;
+    if (live) {
+        if (tid == 0) {
+            bad_any = 0;
+            colbulk::bar_init(bar);
+            const uint32_t bytes = (uint32_t)(k * (int64_t)sizeof(T));
+            colbulk::expect_tx(bar, bytes * Q);
+#pragma unroll
+            for (int c = 0; c < Q; ++c)
+                colbulk::copy(smraw + 16 + (size_t)c * bytes, b.c[c] + j * b.ld, bytes, bar);
+        }
+        __syncthreads();
+        // every thread sees the copies complete (bounded); the verdict is uniform
+        const bool arrived = colbulk::wait(bar);
+        if (!__syncthreads_and(arrived)) {
+            if (tid == 0) atomicOr(status, ST_TIMEOUT);
+            return;
+        }
+        int emax = OZMP_EXP_ZERO;
+        bool ok = true;
+        for (int64_t p = tid; p < k; p += 256) {
+            T v[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[c] = (c < Q) ? col[(size_t)c * k + p] : (T)0;
+            int e;
+            ok &= exponent_loaded<T>(v, Q, e);
+            emax = e > emax ? e : emax;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int x = __shfl_xor_sync(0xffffffffu, emax, o);
+            emax = x > emax ? x : emax;
+        }
+        if (lane == 0) red[wid] = emax;
+        if (!ok) bad_any = 1;
+        __syncthreads();
+        Ecol = red[0];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) Ecol = red[w] > Ecol ? red[w] : Ecol;
+        if (tid == 0) {
+            F[j] = Ecol;
+            if (bad_any) atomicOr(status, ST_NONFINITE);
+        }
+    }
+    const int64_t quads = kp / 4;
+    uint8_t* const cbase = dig + (size_t)j * kp;
+    const size_t slice = (size_t)np * kp;
+    for (int64_t g = tid; g < quads; g += 256) {
+        const int64_t p0 = 4 * g;
+        T v[4][4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                v[e][c] = (live && c < Q && p0 + e < k) ? col[(size_t)c * k + p0 + e] : (T)0;
+        quad_digits<T, FORM, NW, Q>(v, Q, Ecol, s, [&](int t, uint32_t word) {
+            *reinterpret_cast<uint32_t*>(cbase + (size_t)(t - 1) * slice + p0) = word;
+        });
+    }
 }
 
 // binary64 digits, rows of A: 16 x 16 tile staged in shared memory
@@ -511,6 +667,22 @@ static inline Operand<T> make_op(const void* const* comps, int q, int64_t ld) {
 // words of the digit window: word 0 below every digit, sign bit on top
 static inline int digit_words(int beta, int s) { return (beta * s + 65 + 63) / 64; }
 
+// shared memory of the one-pass column kernel, or 0 where it does not apply:
+// e4m3 digits, whole columns of at most 112 KB (two blocks per SM), and
+// 16-byte aligned column starts and lengths for the bulk copies
+static inline size_t cols_fused_smem(const SplitArgs& g) {
+    if (g.big || !(g.form == OZMP_FORM_FP8 || g.form == OZMP_FORM_FP8_MMA)) return 0;
+    if (g.is_f32 ? g.q != 3 : (g.q < 2 || g.q > 4)) return 0;
+    if (g.n <= 0 || g.k <= 0) return 0;
+    const size_t es = g.is_f32 ? 4 : 8;
+    const size_t bytes = (size_t)g.k * es;
+    if (bytes % 16 != 0 || ((size_t)g.ldb * es) % 16 != 0) return 0;
+    for (int c = 0; c < g.q; ++c)
+        if ((uintptr_t)g.B[c] % 16 != 0) return 0;
+    const size_t total = 16 + bytes * (size_t)g.q;
+    return total <= 112 * 1024 + 16 ? total : 0;
+}
+
 template <typename T, int FORM, int NW, int Q>
 static cudaError_t digits_b1_q(const SplitArgs& g, cudaStream_t st) {
     Operand<T> a = make_op<T>(g.A, g.q, g.lda);
@@ -521,6 +693,16 @@ static cudaError_t digits_b1_q(const SplitArgs& g, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     kr<<<gr, 256, sm, st>>>(a, g.m, g.k, g.E, (uint8_t*)g.Adig, g.mp, g.kp, g.s);
+    if constexpr ((FORM == OZMP_FORM_FP8 || FORM == OZMP_FORM_FP8_BAL) && Q > 0) {
+        const size_t fsm = cols_fused_smem(g);
+        if (fsm) {
+            auto kf = k_split_cols_fused<T, FORM, NW, Q>;
+            e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+            if (e != cudaSuccess) return e;
+            kf<<<(unsigned)g.np, 256, fsm, st>>>(b, g.k, g.n, g.F, g.status, (uint8_t*)g.Bdig, g.np, g.kp, g.s);
+            return cudaGetLastError();
+        }
+    }
     int64_t tot = (g.kp / 4) * g.np;
     k_split_cols_b1<T, FORM, NW, Q><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(b, g.k, g.n, g.F,
                                                                                  (uint8_t*)g.Bdig, g.np, g.kp, g.s);

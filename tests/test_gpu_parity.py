@@ -77,6 +77,39 @@ def test_split_widest_register_windows(form, s):
     _split_check("dd", form, 70, 60, 50, phi=1.0, seed=7, nslices=s)
 
 
+@pytest.mark.parametrize("form", ["fp8", "fp8bal"])
+@pytest.mark.parametrize("prec", ["dd", "qd", "ts"])
+def test_column_digits_in_one_pass_and_in_two(prec, form):
+    # columns of B with 16-byte aligned starts and lengths are copied whole into
+    # shared memory and split there (one read of B); a leading dimension of
+    # k + 1 takes the separate exponent and digit kernels: both give the
+    # oracle's exponents and digits
+    m, n, k = 70, 90, 136
+    A, B = gen_problem(prec, m, n, k, phi=1.0, seed=11)
+    dt = torch.float32 if prec == "ts" else torch.float64
+    Eo = Fo = dA = dB = None
+    for pad in (0, 1):
+        p = oz.Plan(prec, m, n, k, form, 0)
+        Bd = []
+        for b in B:
+            buf = torch.zeros((n, k + pad), dtype=dt, device="cuda")
+            buf[:, :k] = torch.from_numpy(np.ascontiguousarray(b.T))
+            Bd.append(buf.T[:k, :])                   # k x n, column stride k + pad
+        p.split(to_dev(A), Bd)
+        torch.cuda.synchronize()
+        assert p.status() == oz.Status.OK
+        i = p.info
+        if dB is None:
+            Eo, dA = _osplit(A, form, i.beta, i.nslices)
+            Fo, dB = _osplit([np.asfortranarray(b.T) for b in B], form, i.beta, i.nslices)
+        E, F = [t.cpu().numpy() for t in p.exponents()]
+        ga, gb = [t.cpu().numpy() for t in p.digits()]
+        assert list(E) == Eo and list(F) == Fo, pad
+        np.testing.assert_array_equal(digits_to_int(gb[:, :n, :k], form), dB)
+        np.testing.assert_array_equal(digits_to_int(ga[:, :m, :k], form), dA)
+        assert not digits_to_int(gb[:, n:, :], form).any() and not digits_to_int(gb[:, :, k:], form).any()
+
+
 @pytest.mark.parametrize("form", ["fp8", "fp8bal", "fp8mma", "int8", "fp64"])
 def test_diagonals_bit_exact(form):
     s = {"fp8": 20, "fp8bal": 16, "fp8mma": 20, "int8": 12, "fp64": 5}[form]
