@@ -13,7 +13,8 @@ Printed: one JSON line (rank 0).  Besides the contract keys it carries
   roofline      -- the slice-product kernel: algorithmic tensor FLOPs
                    (pairs * 2 m n k) / its CUDA-event time, against the
                    e4m3 dense peak derived from the measured bf16 peak;
-  splitter      -- HBM bytes of K1 + K2 / their time, against measured HBM;
+  splitter      -- algorithmic HBM bytes of K1 + K2 (operands read once,
+                   digits written once) / their time, against measured HBM;
   e2e           -- the same metric through the C ABI with host buffers
                    (pinned H2D of A, B and D2H of C inside the timed region);
   cpu_baseline  -- the oracle (exact product rounded to 512 bits) on the
@@ -329,8 +330,10 @@ def batched_512_variant(oz, torch):
 
 
 def splitter_bytes(q, w, m, n, k, s, db):
-    # K1 reads both operands, K2 reads them again and writes the digits
-    return 2 * q * w * (m * k + k * n) + s * db * (m * k + k * n)
+    # algorithmic bytes of K1 + K2: both operands read once, every digit
+    # written once (the row exponents of A take a second read of A, which
+    # counts as time, not as algorithmic bytes)
+    return q * w * (m * k + k * n) + s * db * (m * k + k * n)
 
 
 def main():

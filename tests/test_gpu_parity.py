@@ -82,8 +82,9 @@ def test_split_widest_register_windows(form, s):
 def test_column_digits_in_one_pass_and_in_two(prec, form):
     # columns of B with 16-byte aligned starts and lengths are copied whole into
     # shared memory and split there (one read of B); a leading dimension of
-    # k + 1 takes the separate exponent and digit kernels: both give the
-    # oracle's exponents and digits
+    # k + 1 takes the separate exponent and digit kernels (and m + 1 gives A
+    # an unaligned leading dimension too): both give the oracle's exponents
+    # and digits
     m, n, k = 70, 90, 136
     A, B = gen_problem(prec, m, n, k, phi=1.0, seed=11)
     dt = torch.float32 if prec == "ts" else torch.float64
@@ -95,7 +96,12 @@ def test_column_digits_in_one_pass_and_in_two(prec, form):
             buf = torch.zeros((n, k + pad), dtype=dt, device="cuda")
             buf[:, :k] = torch.from_numpy(np.ascontiguousarray(b.T))
             Bd.append(buf.T[:k, :])                   # k x n, column stride k + pad
-        p.split(to_dev(A), Bd)
+        Ad = []
+        for a in A:
+            buf = torch.zeros((k, m + pad), dtype=dt, device="cuda")
+            buf[:, :m] = torch.from_numpy(np.ascontiguousarray(a.T))
+            Ad.append(buf.T[:m, :])                   # m x k, column stride m + pad
+        p.split(Ad, Bd)
         torch.cuda.synchronize()
         assert p.status() == oz.Status.OK
         i = p.info
