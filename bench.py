@@ -329,6 +329,20 @@ def batched_512_variant(oz, torch):
             "loop_gflops": flops / (ms_l * 1e-3) / 1e9, "status": st.name}
 
 
+def launches_per_step(oz, info, Bd, k, w):
+    """Kernels of one plan execution: exponent init, row exponents, row digits,
+    then for B either one pass (e4m3 forms, 16-byte aligned column starts and
+    lengths, at most 112 KB a column) or column exponents + column digits;
+    then the slice-product kernel and, for the tcgen05 forms, its rounding
+    pass."""
+    e4m3 = oz.Form(info.form) in (oz.Form.FP8, oz.Form.FP8_BAL, oz.Form.FP8_MMA)
+    ldb = Bd[0].stride(1)
+    one_pass = (e4m3 and (k * w) % 16 == 0 and (ldb * w) % 16 == 0 and len(Bd) * k * w <= 112 * 1024
+                and all(b.data_ptr() % 16 == 0 for b in Bd))
+    tc = oz.Form(info.form) in (oz.Form.FP8, oz.Form.FP8_BAL)
+    return 3 + (1 if one_pass else 2) + 1 + (1 if tc else 0)
+
+
 def splitter_bytes(q, w, m, n, k, s, db):
     # algorithmic bytes of K1 + K2: both operands read once, every digit
     # written once (the row exponents of A take a second read of A, which
@@ -565,9 +579,7 @@ def main():
                 "ms_per_step": e2e_ms, "steps": e2e_steps,
                 "pipelined": "operands of step i+1 copied in and the result of step i-1 copied out on two copy "
                              "streams during step i's product (double-buffered device operands)"},
-        # per step: 5 split kernels (exponent init, row and column exponents, row and
-        # column digits) + the slice-product kernel + (tcgen05 form) its rounding pass
-        "gpu_launches": (7 if oz.Form(info.form) in (oz.Form.FP8, oz.Form.FP8_BAL) else 6) * args.steps,
+        "gpu_launches": launches_per_step(oz, info, Bd, k, w) * args.steps,
         "clocks": clk,
         "device_status": status.name,
     }

@@ -23,6 +23,8 @@ struct SplitArgs {
     int s, beta;
     int big;               // the many-component / wide-window splitter (split_big.cu)
     int bal;               // balanced radix-32 e4m3 digits (beta = 5)
+    long long wait_limit;  // one-pass column kernel: polls before its wait gives up (0: the default)
+    int inject_stall;      // one-pass column kernel, test hook: copies never issued
 };
 
 struct GemmArgs {

@@ -33,6 +33,9 @@ struct ozmp_plan_s {
     // tcgen05 form, for tests of the bounded waits (OZMP_TC_WAIT_LIMIT, OZMP_TC_INJECT_STALL)
     long long tc_wait_limit;
     int tc_inject_stall;
+    // one-pass column splitter, the same test hooks (OZMP_SPLIT_WAIT_LIMIT, OZMP_SPLIT_INJECT_STALL)
+    long long split_wait_limit;
+    int split_inject_stall;
     // kernel timing ring (ozmp_plan_set_timing): tev[2 x] / tev[2 x + 1] around call x mod tev_n
     cudaEvent_t* tev;
     int tev_n;
@@ -198,6 +201,8 @@ inline SplitArgs split_args(ozmp_plan_s* p, const void* const* A, int64_t lda, c
     a.E = (int32_t*)(w + p->off_E);
     a.F = (int32_t*)(w + p->off_F);
     a.status = (uint32_t*)(w + p->off_status);
+    a.wait_limit = p->split_wait_limit;
+    a.inject_stall = p->split_inject_stall;
     a.Adig = w + p->off_Adig;
     a.Bdig = w + p->off_Bdig;
     a.s = p->s;
@@ -333,6 +338,14 @@ inline ozmp_status zero_c(ozmp_plan_s* p, void* const* C, int64_t ldc) {
 inline ozmp_status plan_init(ozmp_plan_s* p, int prec, int64_t m, int64_t n, int64_t k, int form, int nslices,
                              ozmp_stream stream) {
     memset(p, 0, sizeof(*p));
+    {
+        // test hooks of the splitter's bounded wait: a smaller poll limit, and
+        // columns whose copies are never issued so that the wait runs out
+        const char* wl = getenv("OZMP_SPLIT_WAIT_LIMIT");
+        p->split_wait_limit = wl ? atoll(wl) : 0;
+        const char* inj = getenv("OZMP_SPLIT_INJECT_STALL");
+        p->split_inject_stall = (inj && inj[0] == '1') ? 1 : 0;
+    }
     int q = prec_q(prec);
     if (!q || m < 0 || n < 0 || k < 0 || nslices < 0 || nslices > OZMP_MAX_SLICES) return OZMP_ERR_INVALID_ARG;
     if (form < OZMP_FORM_AUTO || form > OZMP_FORM_FP8_BAL) return OZMP_ERR_INVALID_ARG;

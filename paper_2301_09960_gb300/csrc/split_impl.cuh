@@ -525,8 +525,8 @@ __device__ __forceinline__ void copy(void* dst, const void* src, uint32_t bytes,
                  "l"(src), "r"(bytes), "r"(saddr(b))
                  : "memory");
 }
-__device__ __forceinline__ bool wait(uint64_t* b) {
-    for (long long it = 0; it < WAIT_POLLS; ++it) {
+__device__ __forceinline__ bool wait(uint64_t* b, long long polls) {
+    for (long long it = 0; it < polls; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -542,7 +542,7 @@ __device__ __forceinline__ bool wait(uint64_t* b) {
 template <typename T, int FORM, int NW, int Q>
 __global__ void __launch_bounds__(256, 3) k_split_cols_fused(Operand<T> b, int64_t k, int64_t n, int32_t* F,
                                                           uint32_t* status, uint8_t* dig, int64_t np, int64_t kp,
-                                                          int s) {
+                                                          int s, long long polls, int stall) {
     extern __shared__ __align__(16) unsigned char smraw[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
     const T* col = reinterpret_cast<const T*>(smraw + 16);   // [Q][k]
@@ -557,14 +557,16 @@ __global__ void __launch_bounds__(256, 3) k_split_cols_fused(Operand<T> b, int64
             bad_any = 0;
             colbulk::bar_init(bar);
             const uint32_t bytes = (uint32_t)(k * (int64_t)sizeof(T));
-            colbulk::expect_tx(bar, bytes * Q);
+            if (!stall) {   // (the test hook leaves the barrier incomplete, nothing in flight)
+                colbulk::expect_tx(bar, bytes * Q);
 #pragma unroll
-            for (int c = 0; c < Q; ++c)
-                colbulk::copy(smraw + 16 + (size_t)c * bytes, b.c[c] + j * b.ld, bytes, bar);
+                for (int c = 0; c < Q; ++c)
+                    colbulk::copy(smraw + 16 + (size_t)c * bytes, b.c[c] + j * b.ld, bytes, bar);
+            }
         }
         __syncthreads();
         // every thread sees the copies complete (bounded); the verdict is uniform
-        const bool arrived = colbulk::wait(bar);
+        const bool arrived = colbulk::wait(bar, polls);
         if (!__syncthreads_and(arrived)) {
             if (tid == 0) atomicOr(status, ST_TIMEOUT);
             return;
@@ -699,7 +701,9 @@ static cudaError_t digits_b1_q(const SplitArgs& g, cudaStream_t st) {
             auto kf = k_split_cols_fused<T, FORM, NW, Q>;
             e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
             if (e != cudaSuccess) return e;
-            kf<<<(unsigned)g.np, 256, fsm, st>>>(b, g.k, g.n, g.F, g.status, (uint8_t*)g.Bdig, g.np, g.kp, g.s);
+            const long long polls = g.wait_limit > 0 ? g.wait_limit : colbulk::WAIT_POLLS;
+            kf<<<(unsigned)g.np, 256, fsm, st>>>(b, g.k, g.n, g.F, g.status, (uint8_t*)g.Bdig, g.np, g.kp, g.s,
+                                                 polls, g.inject_stall);
             return cudaGetLastError();
         }
     }

@@ -16,7 +16,7 @@ from oracle import exact as X
 from oracle import ozaki as O
 from ozmp_inputs import gen_problem
 
-from _util import from_dev, to_dev
+from _util import digits_to_int, from_dev, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -49,3 +49,30 @@ def test_wait_runs_out_and_context_stays_usable(pair, monkeypatch):
     for a_i, i in enumerate(rows):
         for b_j, j in enumerate(cols):
             assert [float(c[i, j]) for c in Cg] == X.to_components(r["S"][a_i][b_j], 2)
+
+
+def test_column_split_wait_runs_out_and_context_stays_usable(monkeypatch):
+    # the one-pass column splitter waits (bounded) on the bulk copies of its
+    # column; OZMP_SPLIT_INJECT_STALL=1 issues none, so the wait runs out and
+    # the split reports OZMP_ERR_TIMEOUT; a following split is the oracle's
+    m, n, k = 256, 64, 256          # 16-byte aligned columns: the one-pass kernel
+    A, B = gen_problem("dd", m, n, k, seed=3)
+    Ad, Bd = to_dev(A), to_dev(B)
+    monkeypatch.setenv("OZMP_SPLIT_INJECT_STALL", "1")
+    monkeypatch.setenv("OZMP_SPLIT_WAIT_LIMIT", "20000")
+    p = oz.Plan("dd", m, n, k, "fp8bal", 0)
+    monkeypatch.delenv("OZMP_SPLIT_INJECT_STALL")
+    monkeypatch.delenv("OZMP_SPLIT_WAIT_LIMIT")
+    p.split(Ad, Bd)
+    torch.cuda.synchronize()
+    assert p.status() == oz.Status.ERR_TIMEOUT
+    del p
+    p2 = oz.Plan("dd", m, n, k, "fp8bal", 0)
+    p2.split(Ad, Bd)
+    torch.cuda.synchronize()
+    assert p2.status() == oz.Status.OK
+    i = p2.info
+    Fo, dB = O.split_balanced([np.asfortranarray(b.T) for b in B], i.nslices)
+    assert list(p2.exponents()[1].cpu().numpy()) == Fo
+    gb = p2.digits()[1].cpu().numpy()
+    np.testing.assert_array_equal(digits_to_int(gb[:, :n, :k], "fp8bal"), dB)
