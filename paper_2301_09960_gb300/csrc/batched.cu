@@ -18,6 +18,7 @@
 #include <queue>
 #include <vector>
 #include "gemm_tc_impl.cuh"
+#include "batched_split.cuh"
 #include "plan.h"
 #include "split_impl.cuh"
 
@@ -26,111 +27,6 @@ using namespace ozmp_plan_detail;
 
 namespace ozmp {
 
-// per problem split descriptor (device memory)
-struct BSplit {
-    const void* A[4];
-    const void* B[4];
-    int64_t lda, ldb, m, n, k, mp, np, kp;
-    int32_t* E;
-    int32_t* F;
-    uint8_t* Adig;
-    uint8_t* Bdig;
-    int q, s;
-};
-
-// problem of batched block b: the last p with pre[p] <= b
-__device__ __forceinline__ int find_prob(const int* pre, int count, int b) {
-    int lo = 0, hi = count - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (pre[mid] <= b) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-template <typename T>
-__device__ __forceinline__ Operand<T> opA(const BSplit& s) {
-    Operand<T> o;
-    for (int i = 0; i < 4; ++i) o.c[i] = (const T*)s.A[i];
-    o.ld = s.lda;
-    o.q = s.q;
-    return o;
-}
-template <typename T>
-__device__ __forceinline__ Operand<T> opB(const BSplit& s) {
-    Operand<T> o;
-    for (int i = 0; i < 4; ++i) o.c[i] = (const T*)s.B[i];
-    o.ld = s.ldb;
-    o.q = s.q;
-    return o;
-}
-
-__global__ void k_b_init(const BSplit* P, const int* pre, int count) {
-    const int p = find_prob(pre, count, blockIdx.x);
-    const BSplit& s = P[p];
-    const int64_t i = (int64_t)(blockIdx.x - pre[p]) * blockDim.x + threadIdx.x;
-    if (i < s.mp) s.E[i] = OZMP_EXP_ZERO;
-    if (i < s.np) s.F[i] = OZMP_EXP_ZERO;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_b_exp_rows(const BSplit* P, const int* pre, int count, uint32_t* status) {
-    const int p = find_prob(pre, count, blockIdx.x);
-    const BSplit& s = P[p];
-    const int lb = blockIdx.x - pre[p];
-    const int nbx = (int)((s.m + 255) / 256);
-    exp_rows_body(opA<T>(s), s.m, s.k, 256, s.E, status, (int64_t)(lb % nbx), (int64_t)(lb / nbx));
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_b_exp_cols(const BSplit* P, const int* pre, int count, uint32_t* status) {
-    const int p = find_prob(pre, count, blockIdx.x);
-    const BSplit& s = P[p];
-    exp_cols_body(opB<T>(s), s.k, s.n, s.F, status, (int64_t)(blockIdx.x - pre[p]), (int64_t)0);
-}
-
-// FORM: OZMP_FORM_FP8 (4-bit digits) or OZMP_FORM_FP8_BAL (balanced radix-32 digits)
-// The digit launches cover only the tiles that hold values: rows i < m
-// (tiles of 32) and values p < k (chunks of 64) of A, columns j < n and
-// values p < k (quads) of B.  The batched workspace is zeroed when the plan
-// is built, so the rest of the padding keeps zero digits without being
-// written.
-template <typename T, int NW, int FORM>
-__global__ void __launch_bounds__(256) k_b_split_rows(const BSplit* P, const int* pre, int count) {
-    const int p = find_prob(pre, count, blockIdx.x);
-    const BSplit& s = P[p];
-    const int lb = blockIdx.x - pre[p];
-    const int nbx = (int)((s.m + 31) / 32);
-    split_rows_b1_body<T, FORM, NW>(opA<T>(s), s.m, s.k, s.E, s.Adig, s.mp, s.kp, s.s,
-                                    (int64_t)(lb % nbx), (int64_t)(lb / nbx));
-}
-
-template <typename T, int NW, int FORM>
-__global__ void __launch_bounds__(256) k_b_split_cols(const BSplit* P, const int* pre, int count) {
-    const int p = find_prob(pre, count, blockIdx.x);
-    const BSplit& s = P[p];
-    split_cols_b1_body<T, FORM, NW>(opB<T>(s), s.k, s.n, s.F, s.Bdig, s.np, s.kp, s.s,
-                                    (int64_t)(blockIdx.x - pre[p]), (int64_t)0, (s.k + 3) / 4);
-}
-
-template <typename T, int FORM>
-static void set_split_smem(size_t sm) {
-    cudaFuncSetAttribute(k_b_split_rows<T, 4, FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k_b_split_rows<T, 6, FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-}
-
-// the digit launches of one group (rows of A into shared-memory tiles, columns of B direct)
-template <typename T, int FORM>
-static void split_group(int nw, const int (&blocks)[5], const BSplit* sp, const int* const (&pre)[5], int cnt,
-                        size_t sm, cudaStream_t cs) {
-    if (nw == 4) {
-        k_b_split_rows<T, 4, FORM><<<blocks[3], 256, sm, cs>>>(sp, pre[3], cnt);
-        k_b_split_cols<T, 4, FORM><<<blocks[4], 256, 0, cs>>>(sp, pre[4], cnt);
-    } else {
-        k_b_split_rows<T, 6, FORM><<<blocks[3], 256, sm, cs>>>(sp, pre[3], cnt);
-        k_b_split_cols<T, 6, FORM><<<blocks[4], 256, 0, cs>>>(sp, pre[4], cnt);
-    }
-}
 
 }  // namespace ozmp
 
@@ -194,9 +90,10 @@ static void launch_b_finish(int nw, int blocks, const tc::Prob* probs, const int
 // ----------------------------------------------------------------------------
 namespace {
 
-struct Group {              // problems sharing a component type (batched split launches)
+struct Group {              // problems sharing a component type and count (batched split launches)
     std::vector<int> ids;
     int is_f32 = 0;
+    int q = 2;
     int nw = 4;
     int s_max = 1;
     // device offsets (bytes into meta) of BSplit[] and prefix arrays; block totals
@@ -512,18 +409,21 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
             destroy_batch(b);
             return OZMP_ERR_CUDA;
         }
-        // groups by component type
-        for (int t = 0; t < 2; ++t) {
+        // groups by component type and count
+        for (int t = 0; t < 2; ++t)
+            for (int qq = 2; qq <= 4; ++qq) {
             Group g;
             g.is_f32 = t;
+            g.q = qq;
             for (int i = 0; i < count; ++i)
-                if (b->subs[i].is_f32 == t && b->subs[i].m > 0 && b->subs[i].n > 0 && b->subs[i].k > 0) {
+                if (b->subs[i].is_f32 == t && b->subs[i].q == qq && b->subs[i].m > 0 && b->subs[i].n > 0 &&
+                    b->subs[i].k > 0) {
                     g.ids.push_back(i);
                     g.s_max = std::max(g.s_max, b->subs[i].s);
                     if ((b->subs[i].beta * b->subs[i].s + 65 + 63) / 64 > 4) g.nw = 6;
                 }
             if (!g.ids.empty()) b->groups.push_back(g);
-        }
+            }
         // device meta layout
         size_t mo = 0;
         std::vector<std::vector<int>> pre_host;
@@ -591,10 +491,8 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
             for (int kx = 0; kx < 5; ++kx) pre[kx].assign(cnt + 1, 0);
             for (int x = 0; x < cnt; ++x) {
                 const ozmp_plan_s& s = b->subs[g.ids[x]];
-                const int nb[5] = {(int)((std::max(s.mp, s.np) + 255) / 256),
-                                   (int)(((s.m + 255) / 256) * ((s.k + 255) / 256)), (int)((s.n + 7) / 8),
-                                   (int)(((s.m + 31) / 32) * ((s.k + 63) / 64)),
-                                   (int)((((s.k + 3) / 4) * s.n + 255) / 256)};
+                int nb[5];
+                bsplit_blocks(s.m, s.n, s.k, s.mp, s.np, nb);
                 for (int kx = 0; kx < 5; ++kx) pre[kx][x + 1] = pre[kx][x] + nb[kx];
             }
             for (int kx = 0; kx < 5; ++kx) {
@@ -705,12 +603,10 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
     }
     if (!b->gexec && b->form == OZMP_FORM_FP8) {
         for (Group& g : b->groups) {
-            const size_t sm = (size_t)g.s_max * 32 * 16 * 4;
-            if (g.is_f32) {
-                if (b->bal) set_split_smem<float, OZMP_FORM_FP8_BAL>(sm); else set_split_smem<float, OZMP_FORM_FP8>(sm);
-            } else {
-                if (b->bal) set_split_smem<double, OZMP_FORM_FP8_BAL>(sm); else set_split_smem<double, OZMP_FORM_FP8>(sm);
-            }
+            BSplitGroup L = {};
+            L.is_f32 = g.is_f32; L.q = g.q; L.nw = g.nw; L.bal = b->bal ? 1 : 0;
+            L.smem = (size_t)g.s_max * 32 * 16 * 4;
+            if (bsplit_set_smem(L) != cudaSuccess) return OZMP_ERR_CUDA;
         }
         tc_set_smem();
     }
@@ -729,20 +625,14 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
                     const BSplit* sp = (const BSplit*)((char*)b->meta + g.off_split);
                     const int* pre[5];
                     for (int kx = 0; kx < 5; ++kx) pre[kx] = (const int*)((char*)b->meta + g.off_pre[kx]);
-                    const int cnt = (int)g.ids.size();
-                    k_b_init<<<g.blocks[0], 256, 0, cs>>>(sp, pre[0], cnt);
-                    const size_t sm = (size_t)g.s_max * 32 * 16 * 4;
-                    if (g.is_f32) {
-                        k_b_exp_rows<float><<<g.blocks[1], 256, 0, cs>>>(sp, pre[1], cnt, status);
-                        k_b_exp_cols<float><<<g.blocks[2], 256, 0, cs>>>(sp, pre[2], cnt, status);
-                        if (b->bal) split_group<float, OZMP_FORM_FP8_BAL>(g.nw, g.blocks, sp, pre, cnt, sm, cs);
-                        else split_group<float, OZMP_FORM_FP8>(g.nw, g.blocks, sp, pre, cnt, sm, cs);
-                    } else {
-                        k_b_exp_rows<double><<<g.blocks[1], 256, 0, cs>>>(sp, pre[1], cnt, status);
-                        k_b_exp_cols<double><<<g.blocks[2], 256, 0, cs>>>(sp, pre[2], cnt, status);
-                        if (b->bal) split_group<double, OZMP_FORM_FP8_BAL>(g.nw, g.blocks, sp, pre, cnt, sm, cs);
-                        else split_group<double, OZMP_FORM_FP8>(g.nw, g.blocks, sp, pre, cnt, sm, cs);
-                    }
+                    BSplitGroup L = {};
+                    L.sp = sp;
+                    for (int kx = 0; kx < 5; ++kx) { L.pre[kx] = pre[kx]; L.blocks[kx] = g.blocks[kx]; }
+                    L.count = (int)g.ids.size();
+                    L.is_f32 = g.is_f32; L.q = g.q; L.nw = g.nw; L.bal = b->bal ? 1 : 0;
+                    L.smem = (size_t)g.s_max * 32 * 16 * 4;
+                    L.status = status;
+                    if (bsplit_launch(L, cs) != cudaSuccess) ok = false;
                 }
                 if (b->split_bytes)
                     cudaMemsetAsync((char*)b->ws + b->off_split, 0, b->split_bytes, cs);
