@@ -613,15 +613,40 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
     if (!b->gexec) {
         cudaStream_t cs = nullptr;
         if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return OZMP_ERR_CUDA;
+        // branch streams and events of the split: group g's rows of A on
+        // side[2 g] (cs for the first group), its columns of B on side[2 g + 1]
+        const size_t ng = b->groups.size();
+        std::vector<cudaStream_t> side(2 * ng, nullptr);
+        std::vector<cudaEvent_t> evs(2 * ng, nullptr), join_b(ng, nullptr);
+        cudaEvent_t fork = nullptr;
+        bool made = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
+        for (size_t x = 0; x < 2 * ng; ++x) {
+            if (x > 0) made = made && cudaStreamCreateWithFlags(&side[x], cudaStreamNonBlocking) == cudaSuccess;
+            made = made && cudaEventCreateWithFlags(&evs[x], cudaEventDisableTiming) == cudaSuccess;
+        }
+        for (size_t x = 0; x < ng; ++x) made = made && cudaEventCreateWithFlags(&join_b[x], cudaEventDisableTiming) == cudaSuccess;
+        auto release = [&]() {
+            for (cudaStream_t x : side) if (x) cudaStreamDestroy(x);
+            for (cudaEvent_t x : evs) if (x) cudaEventDestroy(x);
+            for (cudaEvent_t x : join_b) if (x) cudaEventDestroy(x);
+            if (fork) cudaEventDestroy(fork);
+        };
         cudaGraph_t graph = nullptr;
-        bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        bool ok = made && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
         uint32_t* status = (uint32_t*)((char*)b->meta + b->off_status);
         if (ok) {
             // 1. the caller's pointers (read from the pinned mirror at every replay)
             cudaMemcpyAsync(b->meta, b->pinned, b->pinned_bytes, cudaMemcpyHostToDevice, cs);
             cudaMemsetAsync(status, 0, 16, cs);
             if (b->form == OZMP_FORM_FP8) {
+                // split: a branch of the graph per group and operand (A's rows,
+                // B's columns), forked after the descriptor upload and joined
+                // before the product launch
+                if (cudaEventRecord(fork, cs) != cudaSuccess) ok = false;
+                size_t gi = 0;
                 for (Group& g : b->groups) {
+                    cudaStream_t sa = gi == 0 ? cs : side[2 * gi], sb = side[2 * gi + 1];
+                    if (gi > 0 && cudaStreamWaitEvent(sa, fork, 0) != cudaSuccess) ok = false;
                     const BSplit* sp = (const BSplit*)((char*)b->meta + g.off_split);
                     const int* pre[5];
                     for (int kx = 0; kx < 5; ++kx) pre[kx] = (const int*)((char*)b->meta + g.off_pre[kx]);
@@ -632,7 +657,15 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
                     L.is_f32 = g.is_f32; L.q = g.q; L.nw = g.nw; L.bal = b->bal ? 1 : 0;
                     L.smem = (size_t)g.s_max * 32 * 16 * 4;
                     L.status = status;
-                    if (bsplit_launch(L, cs) != cudaSuccess) ok = false;
+                    if (bsplit_launch(L, sa, sb, evs[2 * gi]) != cudaSuccess) ok = false;
+                    // join: the group's branches end in events the product launch waits for
+                    if (sa != cs && (cudaEventRecord(evs[2 * gi + 1], sa) != cudaSuccess ||
+                                     cudaStreamWaitEvent(cs, evs[2 * gi + 1], 0) != cudaSuccess))
+                        ok = false;
+                    if (cudaEventRecord(join_b[gi], sb) != cudaSuccess ||
+                        cudaStreamWaitEvent(cs, join_b[gi], 0) != cudaSuccess)
+                        ok = false;
+                    ++gi;
                 }
                 if (b->split_bytes)
                     cudaMemsetAsync((char*)b->ws + b->off_split, 0, b->split_bytes, cs);
@@ -681,6 +714,7 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
         ok = ok && ce == cudaSuccess && graph;
         if (ok && cudaGraphInstantiate(&b->gexec, graph, 0) != cudaSuccess) ok = false;
         if (graph) cudaGraphDestroy(graph);
+        release();
         cudaStreamDestroy(cs);
         if (!ok) {
             cudaGetLastError();

@@ -79,34 +79,49 @@ static cudaError_t set_smem_t(size_t sm) {
 }
 
 template <typename T, int NW, int FORM, int Q>
-static cudaError_t launch_t(const BSplitGroup& g, cudaStream_t cs) {
+static cudaError_t launch_t(const BSplitGroup& g, cudaStream_t cs, cudaStream_t cs_b, cudaEvent_t ev_init) {
     k_b_init<<<g.blocks[0], 256, 0, cs>>>(g.sp, g.pre[0], g.count);
+    if (cs_b != cs) {
+        cudaError_t e = cudaEventRecord(ev_init, cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs_b, ev_init, 0);
+        if (e != cudaSuccess) return e;
+    }
     k_b_exp_rows<T, Q><<<g.blocks[1], 256, 0, cs>>>(g.sp, g.pre[1], g.count, g.status);
-    k_b_exp_cols<T, Q><<<g.blocks[2], 256, 0, cs>>>(g.sp, g.pre[2], g.count, g.status);
     k_b_split_rows<T, NW, FORM, Q><<<g.blocks[3], 256, g.smem, cs>>>(g.sp, g.pre[3], g.count);
-    k_b_split_cols<T, NW, FORM, Q><<<g.blocks[4], 256, 0, cs>>>(g.sp, g.pre[4], g.count);
+    k_b_exp_cols<T, Q><<<g.blocks[2], 256, 0, cs_b>>>(g.sp, g.pre[2], g.count, g.status);
+    k_b_split_cols<T, NW, FORM, Q><<<g.blocks[4], 256, 0, cs_b>>>(g.sp, g.pre[4], g.count);
     return cudaGetLastError();
 }
 
 
+struct Streams {
+    cudaStream_t a, b;
+    cudaEvent_t ev;
+};
+
+template <typename T, int NW, int FORM, int Q>
+static cudaError_t one(const BSplitGroup& g, const Streams* st) {
+    return st ? launch_t<T, NW, FORM, Q>(g, st->a, st->b, st->ev) : set_smem_t<T, NW, FORM, Q>(g.smem);
+}
+
 template <typename T, int Q>
-static cudaError_t by_form(const BSplitGroup& g, cudaStream_t cs, bool smem_only) {
-    if (g.bal) {
-        if (g.nw == 4) return smem_only ? set_smem_t<T, 4, OZMP_FORM_FP8_BAL, Q>(g.smem) : launch_t<T, 4, OZMP_FORM_FP8_BAL, Q>(g, cs);
-        return smem_only ? set_smem_t<T, 6, OZMP_FORM_FP8_BAL, Q>(g.smem) : launch_t<T, 6, OZMP_FORM_FP8_BAL, Q>(g, cs);
-    }
-    if (g.nw == 4) return smem_only ? set_smem_t<T, 4, OZMP_FORM_FP8, Q>(g.smem) : launch_t<T, 4, OZMP_FORM_FP8, Q>(g, cs);
-    return smem_only ? set_smem_t<T, 6, OZMP_FORM_FP8, Q>(g.smem) : launch_t<T, 6, OZMP_FORM_FP8, Q>(g, cs);
+static cudaError_t by_form(const BSplitGroup& g, const Streams* st) {
+    if (g.bal) return g.nw == 4 ? one<T, 4, OZMP_FORM_FP8_BAL, Q>(g, st) : one<T, 6, OZMP_FORM_FP8_BAL, Q>(g, st);
+    return g.nw == 4 ? one<T, 4, OZMP_FORM_FP8, Q>(g, st) : one<T, 6, OZMP_FORM_FP8, Q>(g, st);
 }
 
-static cudaError_t dispatch(const BSplitGroup& g, cudaStream_t cs, bool smem_only) {
-    if (g.is_f32) return by_form<float, 3>(g, cs, smem_only);
-    if (g.q == 2) return by_form<double, 2>(g, cs, smem_only);
-    if (g.q == 3) return by_form<double, 3>(g, cs, smem_only);
-    return by_form<double, 4>(g, cs, smem_only);
+// st == nullptr: raise the shared-memory limit only
+static cudaError_t dispatch(const BSplitGroup& g, const Streams* st) {
+    if (g.is_f32) return by_form<float, 3>(g, st);
+    if (g.q == 2) return by_form<double, 2>(g, st);
+    if (g.q == 3) return by_form<double, 3>(g, st);
+    return by_form<double, 4>(g, st);
 }
 
-cudaError_t bsplit_set_smem(const BSplitGroup& g) { return dispatch(g, nullptr, true); }
-cudaError_t bsplit_launch(const BSplitGroup& g, cudaStream_t cs) { return dispatch(g, cs, false); }
+cudaError_t bsplit_set_smem(const BSplitGroup& g) { return dispatch(g, nullptr); }
+cudaError_t bsplit_launch(const BSplitGroup& g, cudaStream_t cs, cudaStream_t cs_b, cudaEvent_t ev_init) {
+    const Streams st = {cs, cs_b, ev_init};
+    return dispatch(g, &st);
+}
 
 }  // namespace ozmp

@@ -59,7 +59,9 @@ struct BSplitGroup {
 
 // raise the row digit kernel's shared-memory limit (before a graph capture)
 cudaError_t bsplit_set_smem(const BSplitGroup& g);
-// the five launches of one group on stream cs (capturable)
-cudaError_t bsplit_launch(const BSplitGroup& g, cudaStream_t cs);
+// the five launches of one group (capturable): the exponent init, then A's
+// row exponents and digits on cs and B's column exponents and digits on cs_b,
+// which waits for the init through ev_init (cs_b == cs: all on cs)
+cudaError_t bsplit_launch(const BSplitGroup& g, cudaStream_t cs, cudaStream_t cs_b, cudaEvent_t ev_init);
 
 }  // namespace ozmp
