@@ -116,6 +116,26 @@ def test_column_digits_in_one_pass_and_in_two(prec, form):
         assert not digits_to_int(gb[:, n:, :], form).any() and not digits_to_int(gb[:, :, k:], form).any()
 
 
+@pytest.mark.parametrize("prec,kmax", [("dd", 7168), ("td", 4778), ("qd", 3584)])
+def test_column_split_at_the_shared_memory_limit(prec, kmax):
+    # a column of B goes through shared memory in one pass while its q
+    # components hold at most 112 KB (k = kmax); two more values of k take the
+    # separate exponent and digit kernels: both give the oracle's digits
+    m, n = 8, 6
+    for k in (kmax, kmax + 2):
+        A, B = gen_problem(prec, m, n, k, phi=1.0, seed=12)
+        p = oz.Plan(prec, m, n, k, "fp8bal", 0)
+        p.split(to_dev(A), to_dev(B))
+        torch.cuda.synchronize()
+        assert p.status() == oz.Status.OK
+        i = p.info
+        Fo, dB = O.split_balanced([np.asfortranarray(b.T) for b in B], i.nslices)
+        assert list(p.exponents()[1].cpu().numpy()) == Fo, k
+        gb = p.digits()[1].cpu().numpy()
+        np.testing.assert_array_equal(digits_to_int(gb[:, :n, :k], "fp8bal"), dB)
+        assert not digits_to_int(gb[:, n:, :], "fp8bal").any() and not digits_to_int(gb[:, :, k:], "fp8bal").any()
+
+
 @pytest.mark.parametrize("form", ["fp8", "fp8bal", "fp8mma", "int8", "fp64"])
 def test_diagonals_bit_exact(form):
     s = {"fp8": 20, "fp8bal": 16, "fp8mma": 20, "int8": 12, "fp64": 5}[form]
