@@ -1,0 +1,53 @@
+"""Host logic of bench.py that the JSON line rests on: the splitter's
+algorithmic bytes and the count of kernel launches per step."""
+import os
+import sys
+import types
+
+import pytest
+
+torch = pytest.importorskip("torch")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+import paper_2301_09960_gb300 as oz  # noqa: E402
+
+
+def test_splitter_bytes_are_one_read_of_the_operands_and_one_write_of_the_digits():
+    # DD 4096^3 with 26 one-byte slices: 2 x 8 x (mk + kn) + 26 x (mk + kn)
+    n = 4096
+    assert bench.splitter_bytes(2, 8, n, n, n, 26, 1) == (2 * 8 + 26) * 2 * n * n == 1409286144
+    # binary64 digits (8 bytes each), rectangular
+    assert bench.splitter_bytes(3, 8, 100, 30, 70, 9, 8) == (3 * 8 + 9 * 8) * (100 * 70 + 70 * 30)
+
+
+class _Col:
+    """A stand-in for a column-major device tensor: stride(1) and data_ptr()."""
+
+    def __init__(self, ld, ptr):
+        self.ld, self.ptr = ld, ptr
+
+    def stride(self, i):
+        return self.ld if i == 1 else 1
+
+    def data_ptr(self):
+        return self.ptr
+
+
+@pytest.mark.parametrize("form,k,ld,ptr,q,want", [
+    (oz.Form.FP8_BAL, 4096, 4096, 256, 2, 6),   # aligned DD columns: one pass over B
+    (oz.Form.FP8_BAL, 4095, 4095, 256, 2, 7),   # k * 8 not a multiple of 16: two kernels
+    (oz.Form.FP8_BAL, 4096, 4097, 256, 2, 7),   # leading dimension unaligned
+    (oz.Form.FP8_BAL, 4096, 4096, 264, 2, 7),   # base not 16-byte aligned
+    (oz.Form.FP8_BAL, 7168, 7168, 256, 2, 6),   # 112 KB a column: still one pass
+    (oz.Form.FP8_BAL, 7170, 7170, 256, 2, 7),   # past 112 KB
+    (oz.Form.FP8, 4096, 4096, 256, 4, 7),       # QD: 128 KB a column
+    (oz.Form.FP8_MMA, 4096, 4096, 256, 2, 5),   # mma.sync engine: no rounding pass
+    (oz.Form.INT8, 4096, 4096, 256, 2, 6),      # int8 digits: two kernels for B, no rounding pass
+    (oz.Form.FP64, 4096, 4096, 256, 2, 6),
+])
+def test_launches_per_step_follow_the_library_rule(form, k, ld, ptr, q, want):
+    info = types.SimpleNamespace(form=form)
+    Bd = [_Col(ld, ptr + c * 1024 * 1024) for c in range(q)]
+    assert bench.launches_per_step(oz, info, Bd, k, 8) == want
