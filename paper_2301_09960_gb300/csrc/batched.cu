@@ -1,8 +1,9 @@
 // Batched products: many uneven problems, each at its own precision and
-// slice count, in one captured CUDA graph -- one batched exponent launch,
-// one batched digit launch per operand and one persistent tcgen05 product
-// launch whose CTAs each walk a precomputed, load-balanced list of
-// (problem, tile) items.
+// slice count, in one captured CUDA graph -- per group of problems with the
+// same component count, batched exponent and digit launches (A's rows and
+// B's columns on parallel branches of the graph; kernels in
+// batched_split.cu), then one persistent tcgen05 product launch whose CTAs
+// each walk a precomputed, load-balanced list of (problem, tile) items.
 //
 // The paper computes one product at a time (Sec. 3, Algorithm 1); batching is
 // this library's addition.  The autotuner picks each problem's tile width
