@@ -389,14 +389,14 @@ __device__ __forceinline__ int window_top3(const T (&v)[4], int Erow, uint64_t (
 
 // balanced digits of two binary64 components read a three-word window
 template <typename T, int FORM, int NW, int Q>
-constexpr bool kDigitsDD3 = FORM == OZMP_FORM_FP8_BAL && Q == 2 && sizeof(T) == 8 && NW == 4;
+constexpr bool DIGITS_DD3 = FORM == OZMP_FORM_FP8_BAL && Q == 2 && sizeof(T) == 8 && NW == 4;
 
 // the digits of four loaded elements (consecutive k) that share the exponent
 // Ex: put(t, word) for t = 1 .. s, byte e of word = digit t of element e
 template <typename T, int FORM, int NW, int Q, typename Put>
 __device__ __forceinline__ void quad_digits(const T (&v)[4][4], int q, int Ex, int s, Put&& put) {
     int sign[4];
-    if constexpr (kDigitsDD3<T, FORM, NW, Q>) {
+    if constexpr (DIGITS_DD3<T, FORM, NW, Q>) {
         uint64_t w3[4][3];
 #pragma unroll
         for (int e = 0; e < 4; ++e) sign[e] = window_top3<T>(v[e], Ex, w3[e]);
