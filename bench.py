@@ -229,7 +229,7 @@ def literal_variant(oz, torch, n=1024):
 
 
 def lu_variant(oz, torch):
-    """The LU application (Sec. 5): in-place LU without pivoting of a random
+    """The LU application (Sec. 4.6): in-place LU without pivoting of a random
     n x n matrix (a_ij = U[0,1), the paper's test matrix) in DD and TD, and
     the solve of A x = b with b_i = 1 / i; time of the second call (the first
     creates the product plans), (2/3) n^3 / time."""

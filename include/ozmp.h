@@ -180,16 +180,22 @@ ozmp_status ozmp_gemm_md(int q, int64_t m, int64_t n, int64_t k, const double* c
 /*
  * ozmp_gemm_dd_noalloc -- the double-double product (as ozmp_gemm_dd, form
  * AUTO) without any memory allocation, on `stream`.  The paper has no
- * counterpart: this entry point exists for callers that cannot call
- * cudaMalloc -- code running while its stream is captured into a CUDA graph,
- * programs whose device memory all belongs to a pool or caching allocator,
- * latency-critical serving loops.
+ * counterpart.  It serves callers that cannot call cudaMalloc: programs
+ * whose device memory is all handed out by their own pool or caching
+ * allocator (an allocation behind the pool's back can fail when the pool
+ * holds the memory, and cudaMalloc/cudaFree synchronise the device), and
+ * plug-ins or real-time loops that are not allowed to allocate after start-up.
  * Scratch: a file-scope device array of OZMP_NOALLOC_SCRATCH_BYTES (64 MiB)
  * inside the library, held by every GPU that loads the library until the
- * process exits.  The first call on a device looks up its address; make that
- * first call before any stream capture.
- * Limit: problems whose workspace (workspace_bytes of a DD, FORM_AUTO plan of
- * the same m, n, k, nslices) exceeds the scratch are rejected with
+ * process exits.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.
+ * Limit: the scratch holds the exponents, both operands' digits and the
+ * exact accumulator of the whole-tile walk, off_acc + (4 acc_words + 1)
+ * mp np 8 bytes of a DD FORM_AUTO plan of the same m, n, k, nslices
+ * (ozmp_plan_get_info; rounded up to 256).  That is less than the plan's
+ * workspace_bytes, which adds a tile schedule and split-tile buffers that
+ * this entry point does not use.  Larger problems are rejected with
  * OZMP_ERR_UNSUPPORTED: m = n = k = 512 fits, 1024^3 does not.
  * All calls share the scratch and it keeps the last call's contents: calls
  * whose work overlaps on the GPU race and must be serialised by the caller.
@@ -272,7 +278,7 @@ ozmp_status ozmp_plan_multiply(ozmp_plan plan, void* const* C, int64_t ldc);
 ozmp_status ozmp_plan_diagonal(ozmp_plan plan, int d, int64_t* T);
 
 /*
- * LU factorisation without pivoting (Sec. 5, "LU decomposition using
+ * LU factorisation without pivoting (Sec. 4.6, "LU decomposition using
  * matrix multiplication"): A = L U in place, L unit lower (its diagonal not
  * stored), U upper, for q binary64 components, 2 <= q <= 4 (DD, TD, QD).
  * A: q device pointers, n x n column-major, leading dimension lda >= n.

@@ -2,7 +2,7 @@
 CPU oracle of the LU application (test infrastructure; imported only by
 the tests).
 
-Paper, Sec. 5 ("LU decomposition using matrix multiplication"): factor
+Paper, Sec. 4.6 ("LU decomposition using matrix multiplication"): factor
 A11 = L11 U11, turn A12 into U12 = L11^-1 A12 and A21 into L21 = A21 U11^-1,
 update A22 := A22 - L21 U12 with the Ozaki product, and repeat on A22.
 

@@ -359,7 +359,8 @@ def ozmp_gemm_md(A, B, C, nslices=0):
 
 def ozmp_gemm_dd_noalloc(A, B, C, nslices=0, stream=None):
     """Double-double product that allocates nothing (a fixed 64 MiB scratch
-    inside the library); for callers that cannot call cudaMalloc."""
+    inside the library), for callers that cannot call cudaMalloc, such as
+    programs whose device memory is all held by their own pool allocator."""
     m, k = A[0].shape
     n = B[0].shape[1]
     pa, ka = _ptrs(A)

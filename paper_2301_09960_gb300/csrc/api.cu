@@ -198,6 +198,7 @@ static thread_local ozmp_plan tl_plan = nullptr;
 static thread_local cudaStream_t tl_stream = nullptr;
 static thread_local int tl_form = OZMP_FORM_AUTO;
 static thread_local int tl_nslices = -1;
+static thread_local int tl_plan_form = -1;   // the form tl_plan was created for (as requested)
 
 ozmp_status ozmp_set_stream(ozmp_stream stream) {
     tl_stream = (cudaStream_t)stream;
@@ -219,13 +220,16 @@ ozmp_status ozmp_last_status(ozmp_status* device_status) {
 
 static ozmp_status plain_gemm(ozmp_prec prec, int64_t m, int64_t n, int64_t k, const void* const* A, int64_t lda,
                               const void* const* B, int64_t ldb, void* const* C, int64_t ldc, int nslices) {
-    int want_form = (tl_form == OZMP_FORM_AUTO) ? OZMP_FORM_FP8 : tl_form;
+    // the cached plan is reused only for the form it was requested with: the
+    // plan's own form field is the engine (FP8 for both e4m3 digit forms)
     ozmp_plan p = tl_plan;
-    if (!p || p->prec != prec || p->m != m || p->n != n || p->k != k || p->form != want_form || tl_nslices != nslices) {
-        if (p) { ozmp_plan_destroy(p); tl_plan = nullptr; }
+    if (!p || p->prec != prec || p->m != m || p->n != n || p->k != k || tl_plan_form != tl_form ||
+        tl_nslices != nslices) {
+        if (p) { ozmp_plan_destroy(p); tl_plan = nullptr; tl_plan_form = -1; }
         ozmp_status st = ozmp_plan_create(&p, prec, m, n, k, (ozmp_form)tl_form, nslices, tl_stream);
         if (st != OZMP_OK) return st;
         tl_plan = p;
+        tl_plan_form = tl_form;
         tl_nslices = nslices;
     }
     p->stream = tl_stream;

@@ -1,5 +1,5 @@
 // LU factorisation without pivoting with the Ozaki-scheme product (paper,
-// Sec. 5 "LU decomposition using matrix multiplication"): A = L U for q
+// Sec. 4.6 "LU decomposition using matrix multiplication"): A = L U for q
 // binary64 components (2 <= q <= 4), L unit lower, both stored in place.
 //
 // The paper's step is: factor A11 = L11 U11, turn A12 into U12 and A21 into

@@ -1,11 +1,11 @@
 // Double-double product that allocates no memory (ozmp_gemm_dd_noalloc).
 //
-// Who needs it: callers that must not call cudaMalloc.  Examples are code
-// that runs while its stream is being captured into a CUDA graph (device
-// allocation is not permitted there), programs whose device memory is all
-// owned by a pool or caching allocator (a cudaMalloc/cudaFree behind its back
-// synchronises the device and fragments the pool), and latency-critical
-// serving loops that cannot pay for an allocation.  The regular entry points
+// Who needs it: callers that must not call cudaMalloc.  A program whose
+// device memory is all handed out by its own pool or caching allocator
+// cannot have a library allocate behind the pool's back: the allocation can
+// fail because the pool holds the memory, and cudaMalloc/cudaFree
+// synchronise the device.  Plug-ins and real-time loops are often not
+// allowed to allocate after start-up at all.  The regular entry points
 // allocate their workspace on first use; this one instead uses a scratch
 // area that is part of the library's device image.
 //
@@ -16,6 +16,11 @@
 // address up with cudaGetSymbolAddress, with that device current, and every
 // call passes that address to the kernels.  Make that first call before any
 // stream capture.
+//
+// The scratch holds the plan layout of the whole-tile walk (exponents, digit
+// slices of both operands, carry-save limbs): plan_init's workspace size,
+// without the tile schedule and split-tile limbs that a regular plan appends.
+// Larger problems are rejected.
 //
 // All calls share the one array and it keeps the last call's contents: the
 // exponent vectors and the status word are reset by the first kernel of every

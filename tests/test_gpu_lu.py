@@ -1,4 +1,4 @@
-"""GPU parity of the LU application (Sec. 5) against the CPU oracle.
+"""GPU parity of the LU application (Sec. 4.6) against the CPU oracle.
 
 * factors and solutions bit-exact against oracle.lu (the same operations,
   each an exact value rounded canonically, the Ozaki products the exact
