@@ -113,3 +113,52 @@ def test_few_large_problems_split_into_pair_ranges(split, defer, monkeypatch):
         for x, y in zip(C, ref):
             assert torch.equal(x, y), (prec, m, n, k)
     oz.ozmp_plan_destroy(plan)
+
+
+def test_batched_512_problems_sampled_against_the_oracle():
+    # the batch of the benchmark (512 DD/TD problems, m, n, k log-uniform in
+    # [32, 768], seed 1), run as one graph; 8 DD and 8 TD problems are
+    # checked on a block of up to 32 x 32 entries (full k): bit for bit
+    # against the canonical rounding of the oracle's exact Ozaki sum with the
+    # automatic slice count, and within the precision's target against the
+    # exact product rounded to 512 bits
+    from oracle import _clib
+    from oracle import exact as X
+    from oracle import ozaki as O
+
+    shapes = batched_problem_shapes(512, seed=1)
+    host, probs = [], []
+    for idx, (m, n, k, prec) in enumerate(shapes):
+        A, B = gen_problem(prec, m, n, k, phi=1.0, seed=1000 + idx)
+        host.append((A, B))
+        C = [torch.full((n, m), 7.0, dtype=torch.float64, device="cuda").T for _ in A]
+        probs.append((prec, to_dev(A), to_dev(B), C, 0))
+    plan = oz.ozmp_gemm_batched(probs)
+    torch.cuda.synchronize()
+    assert oz.ozmp_plan_get_status(plan) == oz.Status.OK
+    rng = np.random.default_rng(11)
+    picks = []
+    for want in ("dd", "td"):
+        idx = [i for i, s in enumerate(shapes) if s[3] == want]
+        picks += list(rng.choice(idx, 8, replace=False))
+    target = {"dd": 2.0 ** -100, "td": 2.0 ** -150}
+    for idx in picks:
+        m, n, k, prec = shapes[idx]
+        A, B = host[idx]
+        q = len(A)
+        rows = sorted(set(np.linspace(0, m - 1, min(m, 32)).astype(int).tolist()))
+        cols = sorted(set(np.linspace(0, n - 1, min(n, 32)).astype(int).tolist()))
+        info = oz.Plan(prec, m, n, k, "auto", 0, workspace=False).info
+        assert info.form == oz.Form.FP8_BAL
+        r = O.ozaki_product([a[rows] for a in A], [b[:, cols] for b in B], info.beta, info.nslices,
+                            balanced=True)
+        Cg = [c.cpu().numpy() for c in probs[idx][3]]
+        for a, i in enumerate(rows):
+            for b, j in enumerate(cols):
+                got = [float(c[i, j]) for c in Cg]
+                assert got == X.to_components(r["S"][a][b], q), (idx, prec, m, n, k, i, j)
+        ex = _clib.exact_block(A, B, rows, cols)
+        chat = [[[float(c[i, j]) for c in Cg] for j in cols] for i in rows]
+        err = X.error_metrics(chat, ex)["err_nw"]
+        assert err <= target[prec], (idx, prec, m, n, k, err)
+    oz.ozmp_plan_destroy(plan)
