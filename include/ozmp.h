@@ -39,7 +39,10 @@
  * exponents outside the representable window) are written to a device
  * status word, readable with ozmp_plan_get_status / ozmp_last_status after
  * the stream has been synchronised.  C is unspecified after a data error.
- * Calls are stream-ordered and asynchronous.
+ * Every product of a plan is followed by an a-posteriori check of its error
+ * bound (OZMP_ERR_ACCURACY when the bound does not certify the target).
+ * Calls are stream-ordered and asynchronous, except that a plan with a
+ * data-dependent slice count (nslices = 0) waits for its exponent pass.
  */
 #ifndef OZMP_H
 #define OZMP_H
@@ -59,7 +62,9 @@ typedef enum {
     OZMP_ERR_NOMEM = 4,        /* workspace allocation failed or supplied workspace too small */
     OZMP_ERR_CUDA = 5,         /* a CUDA runtime call failed */
     OZMP_ERR_UNSUPPORTED = 6,  /* shape/precision/form combination not provided */
-    OZMP_ERR_TIMEOUT = 7       /* device status: a bounded wait in the batched scheduler gave up */
+    OZMP_ERR_TIMEOUT = 7,      /* device status: a bounded wait in the batched scheduler gave up */
+    OZMP_ERR_ACCURACY = 8      /* device status: the result's error bound does not certify the
+                                  precision's target (more slices are needed); C holds the result */
 } ozmp_status;
 
 /* precision of the operands (component count and word type).  A value q
@@ -118,9 +123,24 @@ typedef struct {
  * ozmp_plan_create -- fix precision, shape, digit form and slice count.
  * Sec. 3, Algorithm 1 (the choice of D, here nslices) and Sec. 3's remark
  * that the needed slice count depends on the data.
- *   nslices = 0 chooses s from the precision's target (2^-100 DD, 2^-150 TD,
- *   2^-200 QD, 2^(-50 q) for q binary64 components, 2^-66 TS) with a guard
- *   of log2 k + 16 bits; 1..OZMP_MAX_SLICES forces s (see the form limits).
+ *   Truncation bound: with s slices the computed sum S satisfies
+ *   |S_ij - C*_ij| <= k c(s) 2^(E_i + F_j - W(s)) (W(s) = beta s, or 5 s - 1
+ *   for balanced digits; c(s) about s), so
+ *   ||S - C*||_F <= k c(s) 2^-W(s) ||2^E||_2 ||2^F||_2.
+ *   nslices = 0: s is chosen from the data at every execution (split): after
+ *   the exponent reduce, the smallest s whose bound is half of 2^-target
+ *   times an estimate of ||C||_F (from the column norms of A and the row
+ *   norms of B) -- target 2^-100 DD, 2^-150 TD, 2^-200 QD, 2^(-50 q) for q
+ *   binary64 components, 2^-66 TS.  That choice is read back to the host, so
+ *   the execution waits for the exponent pass.  The plan reserves the
+ *   workspace of the slice counts within about 50 bits of the count
+ *   ceil((target + log2 k + 16) / beta) (for s outside, the nearest end is
+ *   used); ozmp_plan_get_info reports the count of the last execution.
+ *   1..OZMP_MAX_SLICES forces s (see the form limits).
+ *   Every execution then checks the result: with N a lower bound of
+ *   ||S||_F, the device status becomes OZMP_ERR_ACCURACY when
+ *   (bound + u_q N) / (N - bound) exceeds 2^-target (u_q: the rounding into
+ *   q components), e.g. for a forced s that is too small.
  *   stream: stream used by later executions through this plan.
  * The plan allocates its workspace lazily on first execution unless one is
  * supplied with ozmp_plan_set_workspace.  Returns INVALID_ARG for bad
@@ -157,7 +177,8 @@ ozmp_status ozmp_plan_get_status(ozmp_plan plan, ozmp_status* device_status);
 /*
  * Plain entry points (Sec. 1 problem statement, C := AB), one per precision.
  * They use a per-thread cached plan on the stream set with ozmp_set_stream
- * (default: legacy stream), FORM_AUTO, and nslices as for ozmp_plan_create.
+ * (default: legacy stream), the form set with ozmp_set_form (default
+ * FORM_AUTO), and nslices as for ozmp_plan_create (0: chosen from the data).
  */
 ozmp_status ozmp_gemm_dd(int64_t m, int64_t n, int64_t k, const double* const A[2], int64_t lda,
                          const double* const B[2], int64_t ldb, double* const C[2], int64_t ldc,
@@ -197,6 +218,8 @@ ozmp_status ozmp_gemm_md(int q, int64_t m, int64_t n, int64_t k, const double* c
  * workspace_bytes, which adds a tile schedule and split-tile buffers that
  * this entry point does not use.  Larger problems are rejected with
  * OZMP_ERR_UNSUPPORTED: m = n = k = 512 fits, 1024^3 does not.
+ * nslices = 0 is the automatic count ceil((100 + log2 k + 16) / 5) (no
+ * data-dependent choice and no a-posteriori check: both would need more).
  * All calls share the scratch and it keeps the last call's contents: calls
  * whose work overlaps on the GPU race and must be serialised by the caller.
  * The device status word is not reported; C is unspecified for NaN/Inf input.
@@ -210,7 +233,9 @@ ozmp_status ozmp_gemm_dd_noalloc(int64_t m, int64_t n, int64_t k, const double* 
  * Batched products (the paper computes one product at a time, Sec. 3;
  * batching is this library's addition): count independent problems
  * C_i := A_i B_i, each with its own precision, shape, leading dimensions and
- * slice count (0 = automatic), run as one captured CUDA graph.  For
+ * slice count (0 = the precision's automatic count ceil((target + log2 k +
+ * 16) / beta): a graph holds no read-back, so there is no data-dependent
+ * choice and no a-posteriori check in a batch), run as one captured CUDA graph.  For
  * FORM_FP8 / FORM_FP8_BAL / FORM_AUTO the graph holds one batched exponent launch, one
  * batched digit launch per operand and ONE persistent tcgen05 product launch
  * whose CTAs walk a load-balanced list of (problem, tile) items; the tile

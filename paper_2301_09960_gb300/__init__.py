@@ -40,6 +40,7 @@ class Status(IntEnum):
     ERR_CUDA = 5
     ERR_UNSUPPORTED = 6
     ERR_TIMEOUT = 7
+    ERR_ACCURACY = 8
 
 
 class Prec(IntEnum):
@@ -434,7 +435,6 @@ class Plan:
         self.prec = prec_code(prec)
         self.form_req = FORM_BY_NAME[form] if isinstance(form, str) else Form(form)
         self.h = ozmp_plan_create(self.prec, m, n, k, self.form_req, nslices, stream)
-        self.info = ozmp_plan_get_info(self.h)
         self.ws = None
         if workspace:
             nb = max(256, int(self.info.workspace_bytes))
@@ -442,6 +442,12 @@ class Plan:
             base = self.ws.data_ptr()
             self.ws_off = (-base) % 256
             ozmp_plan_set_workspace(self.h, base + self.ws_off, nb)
+
+    @property
+    def info(self) -> PlanInfo:
+        """The plan's description; with nslices = 0 the slice count is the one
+        the last split chose from the data."""
+        return ozmp_plan_get_info(self.h)
 
     @property
     def q(self):

@@ -13,12 +13,66 @@ using namespace ozmp;
 
 using namespace ozmp_plan_detail;
 
-extern "C" {
+// ---------------------------------------------------------------------------
+// plan creation and the data-dependent slice count
+// ---------------------------------------------------------------------------
+// A plan descriptor for a forced slice count s, made like p (same precision,
+// shape, digit form, stream and environment knobs); no memory is allocated.
+static ozmp_status plan_make_like(const ozmp_plan_s* p, int s, ozmp_plan_s* t) {
+    const int form = p->bal ? (int)OZMP_FORM_FP8_BAL : p->form;
+    ozmp_status st = plan_init(t, p->prec, p->m, p->n, p->k, form, s, p->stream);
+    if (st != OZMP_OK) return st;
+    t->split_wait_limit = p->split_wait_limit;
+    t->split_inject_stall = p->split_inject_stall;
+    if (p->env_read) {
+        t->env_read = 1;
+        t->env_pair_off = p->env_pair_off;
+        t->env_static = p->env_static;
+        t->env_group = p->env_group;
+        t->env_maxc = p->env_maxc;
+        t->tc_wait_limit = p->tc_wait_limit;
+        t->tc_inject_stall = p->tc_inject_stall;
+    }
+    st = plan_schedule(t);
+    if (st != OZMP_OK) { delete[] t->sched_host; t->sched_host = nullptr; }
+    return st;
+}
 
-const char* ozmp_version(void) { return OZMP_VERSION_STR; }
+// Re-make p for s slices inside its workspace (every s in [s_lo, s_cap] fits
+// the workspace reserved at creation; E, F and the statistics keep their
+// offsets, which depend on m, n, k only).
+static ozmp_status plan_set_slices(ozmp_plan_s* p, int s) {
+    if (s == p->s) return OZMP_OK;
+    ozmp_plan_s t;
+    ozmp_status st = plan_make_like(p, s, &t);
+    if (st != OZMP_OK) return st;
+    if (t.ws_bytes > p->ws_bytes || t.off_stats != p->off_stats || t.off_E != p->off_E || t.off_F != p->off_F) {
+        delete[] t.sched_host;
+        return OZMP_ERR_UNSUPPORTED;
+    }
+    t.ws = p->ws;
+    t.ws_owned = p->ws_owned;
+    t.ws_cap = p->ws_cap;
+    t.ws_bytes = p->ws_bytes;
+    t.tev = p->tev;
+    t.tev_n = p->tev_n;
+    t.tev_calls = p->tev_calls;
+    t.adapt = p->adapt;
+    t.check = p->check;
+    t.s_lo = p->s_lo;
+    t.s_cap = p->s_cap;
+    t.sched_ws = nullptr;   // the new schedule is uploaded before the next product
+    delete[] p->sched_host;
+    *p = t;
+    return OZMP_OK;
+}
 
-ozmp_status ozmp_plan_create(ozmp_plan* plan, ozmp_prec prec, int64_t m, int64_t n, int64_t k,
-                             ozmp_form form, int nslices, ozmp_stream stream) {
+// adapt: nslices = 0 chooses s from the data at every execution, within
+// s0 -/+ about 50 bits of the automatic count s0 (the workspace holds the
+// largest of those layouts); check: the a-posteriori bound check runs after
+// every execution.
+ozmp_status plan_create_internal(ozmp_plan* plan, ozmp_prec prec, int64_t m, int64_t n, int64_t k, ozmp_form form,
+                                 int nslices, ozmp_stream stream, bool adapt, bool check) {
     if (!plan) return OZMP_ERR_INVALID_ARG;
     *plan = nullptr;
     ozmp_plan_s* p = new (std::nothrow) ozmp_plan_s();   // zeroed: a rejected plan frees nothing it has not set
@@ -26,8 +80,40 @@ ozmp_status ozmp_plan_create(ozmp_plan* plan, ozmp_prec prec, int64_t m, int64_t
     ozmp_status st = plan_init(p, prec, m, n, k, form, nslices, stream);
     if (st == OZMP_OK) st = plan_schedule(p);
     if (st != OZMP_OK) { delete[] p->sched_host; delete p; return st; }
+    p->check = check ? 1 : 0;
+    p->s_lo = p->s_cap = p->s;
+    if (adapt && nslices == 0 && m > 0 && n > 0 && k > 0) {
+        p->adapt = 1;
+        const int span = (50 + p->beta - 1) / p->beta;
+        const int s0 = p->s;
+        size_t most = p->ws_bytes;
+        for (int s = s0 + 1; s <= s0 + span; ++s) {
+            ozmp_plan_s t;
+            if (plan_make_like(p, s, &t) != OZMP_OK) break;
+            delete[] t.sched_host;
+            if (t.ws_bytes > most) most = t.ws_bytes;
+            p->s_cap = s;
+        }
+        for (int s = s0 - 1; s >= 1 && s >= s0 - span; --s) {
+            ozmp_plan_s t;
+            if (plan_make_like(p, s, &t) != OZMP_OK) break;
+            delete[] t.sched_host;
+            if (t.ws_bytes > most) most = t.ws_bytes;
+            p->s_lo = s;
+        }
+        p->ws_bytes = most;
+    }
     *plan = p;
     return OZMP_OK;
+}
+
+extern "C" {
+
+const char* ozmp_version(void) { return OZMP_VERSION_STR; }
+
+ozmp_status ozmp_plan_create(ozmp_plan* plan, ozmp_prec prec, int64_t m, int64_t n, int64_t k,
+                             ozmp_form form, int nslices, ozmp_stream stream) {
+    return plan_create_internal(plan, prec, m, n, k, form, nslices, stream, true, true);
 }
 
 static void free_timing(ozmp_plan p) {
@@ -80,12 +166,64 @@ ozmp_status ozmp_plan_set_workspace(ozmp_plan p, void* dev_ptr, size_t bytes) {
     if (p->ws && p->ws_owned) { cudaStreamSynchronize(p->stream); cudaFree(p->ws); }
     p->ws = dev_ptr;
     p->ws_owned = false;
+    p->ws_cap = bytes;
+    p->sched_ws = nullptr;
     return OZMP_OK;
 }
 
 ozmp_status ozmp_plan_set_stream(ozmp_plan p, ozmp_stream stream) {
     if (!p) return OZMP_ERR_INVALID_ARG;
     p->stream = (cudaStream_t)stream;
+    return OZMP_OK;
+}
+
+// Exponents and digits.  An adaptive plan reduces the exponents, chooses s
+// from the data (one 4-byte read-back: the call waits for that pass), re-makes
+// itself for that s and writes the digits; other plans split in one go and
+// take the exponent statistics of the a-posteriori check.
+static ozmp_status do_split(ozmp_plan p, const void* const* A, int64_t lda, const void* const* B, int64_t ldb) {
+    SplitArgs a = split_args(p, A, lda, B, ldb);
+    char* w = (char*)p->ws;
+    if (p->adapt) {
+        if (launch_split_exponents(a, p->stream) != cudaSuccess) return OZMP_ERR_CUDA;
+        BoundStats* bs = bound_stats(p);
+        if (launch_bound_scale(a.E, p->m, a.F, p->n, bs, (double*)(w + p->off_rowB), p->k, true, p->stream) !=
+                cudaSuccess ||
+            launch_bound_choose(A, lda, B, ldb, p->q, p->is_f32 != 0, p->m, p->n, p->k, bs,
+                                (double*)(w + p->off_colA), (double*)(w + p->off_rowB), bound_form(p), p->s_lo,
+                                p->s_cap, p->stream) != cudaSuccess)
+            return OZMP_ERR_CUDA;
+        int s = 0;
+        if (cudaMemcpyAsync(&s, &bs->s_needed, sizeof(int), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+            cudaStreamSynchronize(p->stream) != cudaSuccess)
+            return OZMP_ERR_CUDA;
+        if (s < p->s_lo) s = p->s_lo;
+        if (s > p->s_cap) s = p->s_cap;
+        ozmp_status st = plan_set_slices(p, s);
+        if (st != OZMP_OK) return st;
+        a = split_args(p, A, lda, B, ldb);
+        return launch_split_digits(a, p->stream) == cudaSuccess ? OZMP_OK : OZMP_ERR_CUDA;
+    }
+    if (launch_split(a, p->stream) != cudaSuccess) return OZMP_ERR_CUDA;
+    if (p->check && launch_bound_scale(a.E, p->m, a.F, p->n, bound_stats(p), nullptr, p->k, false, p->stream) !=
+                        cudaSuccess)
+        return OZMP_ERR_CUDA;
+    return OZMP_OK;
+}
+
+// Slice products, exact accumulation and rounding into C; then the
+// a-posteriori check of the result.
+static ozmp_status do_multiply(ozmp_plan p, void* const* C, int64_t ldc) {
+    if (plan_upload_schedule(p) != OZMP_OK) return OZMP_ERR_CUDA;
+    GemmArgs g = gemm_args(p);
+    for (int c = 0; c < OZMP_MAX_COMPONENTS; ++c) g.C[c] = (c < p->q) ? C[c] : nullptr;
+    g.ldc = ldc;
+    take_timing(p, g);
+    if (launch_gemm(g, p->stream) != cudaSuccess) return OZMP_ERR_CUDA;
+    if (p->check &&
+        launch_bound_check(C[0], p->is_f32 != 0, p->m, p->n, ldc, bound_stats(p), bound_form(p), p->s,
+                           (uint32_t*)((char*)p->ws + p->off_status), ST_ACCURACY, p->stream) != cudaSuccess)
+        return OZMP_ERR_CUDA;
     return OZMP_OK;
 }
 
@@ -96,8 +234,7 @@ ozmp_status ozmp_plan_split(ozmp_plan p, const void* const* A, int64_t lda, cons
         return OZMP_ERR_INVALID_ARG;
     ozmp_status st = ensure_ws(p);
     if (st != OZMP_OK) return st;
-    SplitArgs a = split_args(p, A, lda, B, ldb);
-    return launch_split(a, p->stream) == cudaSuccess ? OZMP_OK : OZMP_ERR_CUDA;
+    return do_split(p, A, lda, B, ldb);
 }
 
 ozmp_status ozmp_plan_execute(ozmp_plan p, const void* const* A, int64_t lda, const void* const* B, int64_t ldb,
@@ -110,14 +247,9 @@ ozmp_status ozmp_plan_execute(ozmp_plan p, const void* const* A, int64_t lda, co
     ozmp_status st = ensure_ws(p);
     if (st != OZMP_OK) return st;
     if (p->k == 0) return zero_c(p, C, ldc);
-    SplitArgs a = split_args(p, A, lda, B, ldb);
-    if (launch_split(a, p->stream) != cudaSuccess) return OZMP_ERR_CUDA;
-    if (plan_upload_schedule(p) != OZMP_OK) return OZMP_ERR_CUDA;
-    GemmArgs g = gemm_args(p);
-    for (int c = 0; c < OZMP_MAX_COMPONENTS; ++c) g.C[c] = (c < p->q) ? C[c] : nullptr;
-    g.ldc = ldc;
-    take_timing(p, g);
-    return launch_gemm(g, p->stream) == cudaSuccess ? OZMP_OK : OZMP_ERR_CUDA;
+    st = do_split(p, A, lda, B, ldb);
+    if (st != OZMP_OK) return st;
+    return do_multiply(p, C, ldc);
 }
 
 ozmp_status ozmp_plan_multiply(ozmp_plan p, void* const* C, int64_t ldc) {
@@ -127,12 +259,7 @@ ozmp_status ozmp_plan_multiply(ozmp_plan p, void* const* C, int64_t ldc) {
     if (p->m == 0 || p->n == 0) return OZMP_OK;
     if (!ptrs_ok(C, p->q)) return OZMP_ERR_INVALID_ARG;
     if (p->k == 0) return zero_c(p, C, ldc);
-    if (plan_upload_schedule(p) != OZMP_OK) return OZMP_ERR_CUDA;
-    GemmArgs g = gemm_args(p);
-    for (int c = 0; c < OZMP_MAX_COMPONENTS; ++c) g.C[c] = (c < p->q) ? C[c] : nullptr;
-    g.ldc = ldc;
-    take_timing(p, g);
-    return launch_gemm(g, p->stream) == cudaSuccess ? OZMP_OK : OZMP_ERR_CUDA;
+    return do_multiply(p, C, ldc);
 }
 
 ozmp_status ozmp_plan_diagonal(ozmp_plan p, int d, int64_t* T) {
@@ -188,6 +315,7 @@ ozmp_status ozmp_plan_get_status(ozmp_plan p, ozmp_status* device_status) {
     if (w & ST_NONFINITE) *device_status = OZMP_ERR_NONFINITE;
     else if (w & ST_RANGE) *device_status = OZMP_ERR_RANGE;
     else if (w & ST_TIMEOUT) *device_status = OZMP_ERR_TIMEOUT;
+    else if (w & ST_ACCURACY) *device_status = OZMP_ERR_ACCURACY;
     return OZMP_OK;
 }
 

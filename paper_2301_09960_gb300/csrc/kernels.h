@@ -79,6 +79,10 @@ int tc_num_sms();
 int tc_num_pair_slots();   // co-resident clusters of two CTAs of the tcgen05 pair form
 
 cudaError_t launch_split(const SplitArgs& a, cudaStream_t st);
+// the two passes of launch_split: exponents E, F (all column exponents
+// included), then the digits for the plan's slice count
+cudaError_t launch_split_exponents(const SplitArgs& a, cudaStream_t st);
+cudaError_t launch_split_digits(const SplitArgs& a, cudaStream_t st);
 cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t st);
 
 }  // namespace ozmp

@@ -359,7 +359,12 @@ static void gemm_sub(Ctx& x, const Mat& C, const Mat& A, const Mat& B, int64_t m
     ozmp_plan p;
     auto it = x.plans.find(key);
     if (it == x.plans.end()) {
-        if (ozmp_plan_create(&p, OZMP_PREC_Q(x.q), m, n, k, OZMP_FORM_FP8_BAL, 0, x.st) != OZMP_OK) { x.failed = true; return; }
+        // the automatic slice count of the precision (no data-dependent choice, no check):
+        // the factorisation is defined with it
+        if (plan_create_internal(&p, OZMP_PREC_Q(x.q), m, n, k, OZMP_FORM_FP8_BAL, 0, x.st, false, false) != OZMP_OK) {
+            x.failed = true;
+            return;
+        }
         x.plans[key] = p;
     } else {
         p = it->second;

@@ -14,7 +14,7 @@ namespace ozmp {
 // ----------------------------------------------------------------------------
 // status word bits (device) -> ozmp_status (host picks the first set bit)
 // ----------------------------------------------------------------------------
-enum : uint32_t { ST_NONFINITE = 1u, ST_RANGE = 2u, ST_TIMEOUT = 4u };
+enum : uint32_t { ST_NONFINITE = 1u, ST_RANGE = 2u, ST_TIMEOUT = 4u, ST_ACCURACY = 8u };
 
 // ----------------------------------------------------------------------------
 // 64-bit shifts that are defined for every count (0 for counts >= 64)

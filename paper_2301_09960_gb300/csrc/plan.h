@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include "bound.cuh"
 #include "kernels.h"
 #include "ozmp_internal.cuh"
 
@@ -43,6 +44,17 @@ struct ozmp_plan_s {
     size_t off_items, off_soff, off_tslot, off_sacc, split_bytes;
     int sched_ntiles;
     void* sched_ws;
+    // error bound (bound.cu): statistics region, per-column norms of A and
+    // per-row norms of B (both k doubles), at offsets that depend on m, n, k only
+    size_t off_stats, off_colA, off_rowB;
+    int target_bits;   // the precision's normwise target 2^-target_bits
+    int adapt;         // s chosen from the data at every execution (nslices = 0 at creation)
+    int check;         // a-posteriori bound check after every execution
+    int s_lo, s_cap;   // adaptive plans: the slice counts the reserved workspace holds
+    size_t ws_cap;     // bytes of the current workspace
+    // schedule knobs, read from the environment once (OZMP_TC_PAIR, OZMP_TC_DYNAMIC,
+    // OZMP_TC_GROUP, OZMP_TC_MAX_CHUNKS) and kept when the plan is re-made for another s
+    int env_read, env_pair_off, env_static, env_group, env_maxc;
 };
 
 namespace ozmp_batch {
@@ -154,6 +166,10 @@ inline void fill_layout(ozmp_plan_s* p) {
     p->off_E = off; off = align256(off + (size_t)p->mp * 4);
     p->off_F = off; off = align256(off + (size_t)p->np * 4);
     p->off_status = off; off = align256(off + 16);
+    const size_t kk = p->k > 0 ? (size_t)p->k : 1;
+    p->off_stats = off; off = align256(off + 256);
+    p->off_colA = off; off = align256(off + kk * 8);
+    p->off_rowB = off; off = align256(off + kk * 8);
     p->off_Adig = off; off = align256(off + (size_t)p->s * p->mp * p->kp * p->db);
     p->off_Bdig = off; off = align256(off + (size_t)p->s * p->np * p->kp * p->db);
     p->off_acc = off;
@@ -171,8 +187,24 @@ inline ozmp_status ensure_ws(ozmp_plan_s* p) {
     }
     p->ws = ptr;
     p->ws_owned = true;
+    p->ws_cap = p->ws_bytes;
     return OZMP_OK;
 }
+
+// the digit form of the truncation bound (bound.cuh) of a plan
+inline BoundForm bound_form(const ozmp_plan_s* p) {
+    BoundForm f;
+    f.beta = p->beta;
+    f.eo = p->bal ? 1 : 0;
+    const bool e4m3 = (p->form == OZMP_FORM_FP8 || p->form == OZMP_FORM_FP8_MMA);
+    f.dmax = p->bal ? 16 : (e4m3 ? 15 : (1 << p->beta) - 1);
+    f.target = p->target_bits;
+    f.uq = ldexp(1.0, 1 - (p->is_f32 ? 24 : 53) * p->q);
+    f.k = p->k;
+    return f;
+}
+
+inline BoundStats* bound_stats(ozmp_plan_s* p) { return (BoundStats*)((char*)p->ws + p->off_stats); }
 
 inline bool ptrs_ok(const void* const* v, int q) {
     if (!v) return false;
@@ -264,8 +296,24 @@ inline void take_timing(ozmp_plan_s* p, GemmArgs& g) {
 // per-CTA lists).
 inline ozmp_status plan_schedule(ozmp_plan_s* p) {
     if (p->form != OZMP_FORM_FP8 || p->m == 0 || p->n == 0 || p->k == 0) return OZMP_OK;
-    const char* env = getenv("OZMP_TC_PAIR");
-    p->tc_cg = (p->mp % 256 == 0 && !(env && env[0] == '0')) ? 2 : 1;
+    if (!p->env_read) {
+        const char* env = getenv("OZMP_TC_PAIR");
+        p->env_pair_off = (env && env[0] == '0') ? 1 : 0;
+        const char* dyn = getenv("OZMP_TC_DYNAMIC");
+        p->env_static = (dyn && dyn[0] == '0') ? 1 : 0;
+        const char* grp = getenv("OZMP_TC_GROUP");
+        p->env_group = grp ? atoi(grp) : 0;
+        const char* mxc = getenv("OZMP_TC_MAX_CHUNKS");
+        p->env_maxc = mxc ? atoi(mxc) : 0;
+        // test hooks of the bounded waits: a smaller poll limit, and a stage
+        // whose copies are never issued so that the waits on it run out
+        const char* wl = getenv("OZMP_TC_WAIT_LIMIT");
+        p->tc_wait_limit = wl ? atoll(wl) : 0;
+        const char* inj = getenv("OZMP_TC_INJECT_STALL");
+        p->tc_inject_stall = (inj && inj[0] == '1') ? 1 : 0;
+        p->env_read = 1;
+    }
+    p->tc_cg = (p->mp % 256 == 0 && !p->env_pair_off) ? 2 : 1;
     const int ntiles = (int)((p->mp / (128 * p->tc_cg)) * (p->np / 256));
     const int pairs = p->s * (p->s + 1) / 2;
     const int sms = p->tc_cg == 2 ? tc_num_pair_slots() : tc_num_sms();
@@ -274,19 +322,10 @@ inline ozmp_status plan_schedule(ozmp_plan_s* p) {
     if (!p->sched_host) return OZMP_ERR_NOMEM;
     int* items = p->sched_host;
     int* off = p->sched_host + (size_t)6 * ntiles * TC_MAX_CHUNKS;
-    // test hooks of the bounded waits: a smaller poll limit, and a stage whose
-    // copies are never issued so that the waits on it run out
-    const char* wl = getenv("OZMP_TC_WAIT_LIMIT");
-    p->tc_wait_limit = wl ? atoll(wl) : 0;
-    const char* inj = getenv("OZMP_TC_INJECT_STALL");
-    p->tc_inject_stall = (inj && inj[0] == '1') ? 1 : 0;
-    const char* dyn = getenv("OZMP_TC_DYNAMIC");
-    p->tc_dyn = !(dyn && dyn[0] == '0');
-    const char* grp = getenv("OZMP_TC_GROUP");
-    const char* mxc = getenv("OZMP_TC_MAX_CHUNKS");
+    p->tc_dyn = !p->env_static;
     const int tm = (int)(p->mp / (128 * p->tc_cg));
     p->sched_grid = tc_schedule(ntiles, pairs, sms, items, off, &p->sched_items, &p->sched_slots, !p->tc_dyn, tm,
-                                grp ? atoi(grp) : 0, mxc ? atoi(mxc) : 0);
+                                p->env_group, p->env_maxc);
     p->sched_slots *= p->tc_cg;
     // CTA offsets right after the items in the host copy
     int* off2 = items + 6 * p->sched_items;
@@ -379,6 +418,7 @@ inline ozmp_status plan_init(ozmp_plan_s* p, int prec, int64_t m, int64_t n, int
     }
     if (nslices > maxs || nslices * p->beta > maxbits) return OZMP_ERR_UNSUPPORTED;
     p->s = nslices;
+    p->target_bits = prec_target_bits(prec);
     p->big = (q > 4 || nslices > (p->bal ? 63 : 64)) ? 1 : 0;
     if (p->big && p->is_f32) return OZMP_ERR_UNSUPPORTED;   // the many-component splitter reads binary64
     p->mp = roundup(m, 128);
@@ -393,3 +433,8 @@ inline ozmp_status plan_init(ozmp_plan_s* p, int prec, int64_t m, int64_t n, int
 
 }  // namespace ozmp_plan_detail
 
+// plan creation with the data-dependent slice count (adapt, nslices = 0) and
+// the a-posteriori bound check (check) switched on or off; ozmp_plan_create
+// has both on (api.cu)
+ozmp_status plan_create_internal(ozmp_plan* plan, ozmp_prec prec, int64_t m, int64_t n, int64_t k, ozmp_form form,
+                                 int nslices, ozmp_stream stream, bool adapt, bool check);

@@ -16,8 +16,10 @@ static void init_exponents(const SplitArgs& g, cudaStream_t st) {
     k_init_exponents<<<(unsigned)((mx + 255) / 256), 256, 0, st>>>(g.E, g.mp, g.F, g.np, g.status);
 }
 
+// all_cols: reduce the column exponents here even where the one-pass column
+// digit kernel would (the slice count is then chosen between the two passes)
 template <typename T, int Q>
-static cudaError_t exponents_impl(const SplitArgs& g, cudaStream_t st) {
+static cudaError_t exponents_impl(const SplitArgs& g, cudaStream_t st, bool all_cols) {
     Operand<T> a = make_op<T>(g.A, g.q, g.lda);
     Operand<T> b = make_op<T>(g.B, g.q, g.ldb);
     init_exponents(g, st);
@@ -28,30 +30,39 @@ static cudaError_t exponents_impl(const SplitArgs& g, cudaStream_t st) {
         dim3 gr((unsigned)((g.m + 255) / 256), (unsigned)((g.k + kchunk - 1) / kchunk));
         k_exp_rows<T, Q><<<gr, 256, 0, st>>>(a, g.m, g.k, kchunk, g.E, g.status);
     }
-    if (g.n > 0 && g.k > 0 && cols_fused_smem(g) == 0) {   // else the column digit pass reduces them
+    if (g.n > 0 && g.k > 0 && (all_cols || cols_fused_smem(g) == 0)) {   // else the column digit pass reduces them
         const int split = (int)((g.k + 1023) / 1024 < 8 ? (g.k + 1023) / 1024 : 8);
         k_exp_cols<T, Q><<<(unsigned)((g.n * split + 7) / 8), 256, 0, st>>>(b, g.k, g.n, g.F, g.status, split);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_split(const SplitArgs& g, cudaStream_t st) {
+static cudaError_t exponents(const SplitArgs& g, cudaStream_t st, bool all_cols) {
     if (g.big) {
         // more than 4 components or a window wider than the register splitter's (split_big.cu)
         init_exponents(g, st);
-        cudaError_t e = launch_exponents_big(g, st);
-        if (e != cudaSuccess) return e;
-        return launch_digits_big(g, st);
+        return launch_exponents_big(g, st);
     }
-    cudaError_t e = g.is_f32     ? exponents_impl<float, 3>(g, st)
-                    : g.q == 2   ? exponents_impl<double, 2>(g, st)
-                    : g.q == 3   ? exponents_impl<double, 3>(g, st)
-                                 : exponents_impl<double, 4>(g, st);
-    if (e != cudaSuccess) return e;
+    return g.is_f32     ? exponents_impl<float, 3>(g, st, all_cols)
+           : g.q == 2   ? exponents_impl<double, 2>(g, st, all_cols)
+           : g.q == 3   ? exponents_impl<double, 3>(g, st, all_cols)
+                        : exponents_impl<double, 4>(g, st, all_cols);
+}
+
+cudaError_t launch_split_digits(const SplitArgs& g, cudaStream_t st) {
+    if (g.big) return launch_digits_big(g, st);
     if (g.form == OZMP_FORM_FP64) return launch_digits_fp64(g, st);
     if (g.form == OZMP_FORM_INT8) return launch_digits_int8(g, st);
     if (g.bal) return launch_digits_fp8bal(g, st);
     return launch_digits_fp8(g, st);   // FORM_FP8 and FORM_FP8_MMA share the e4m3 digits
+}
+
+cudaError_t launch_split_exponents(const SplitArgs& g, cudaStream_t st) { return exponents(g, st, true); }
+
+cudaError_t launch_split(const SplitArgs& g, cudaStream_t st) {
+    cudaError_t e = exponents(g, st, false);
+    if (e != cudaSuccess) return e;
+    return launch_split_digits(g, st);
 }
 
 }  // namespace ozmp

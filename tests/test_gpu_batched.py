@@ -33,7 +33,12 @@ def _make(shapes, seed0):
 
 
 def _single(prec, A, B, form):
-    C, p = oz.gemm(A, B, prec, form, 0)
+    # a batch takes the precision's automatic count (no data-dependent choice
+    # inside a graph): the single product with that count forced
+    m, k = A[0].shape
+    n = B[0].shape[1]
+    s0 = oz.Plan(prec, m, n, k, form, 0, workspace=False).info.nslices
+    C, p = oz.gemm(A, B, prec, form, s0)
     return C
 
 

@@ -64,26 +64,26 @@ def _sampled(prec, form, m, n, k, phi, seed, rows, cols, err_rows, err_cols, nsl
 
 
 def test_dd_4096_headline():
-    # the bench workload: DD 4096^3, phi = 1, s = 32 e4m3 slices
+    # the bench workload: DD 4096^3, phi = 1, in 4-bit e4m3 digits
     rows = [0, 1, 255, 256, 2047, 2048, 4094, 4095]
     cols = [0, 255, 256, 1000, 3071, 4095]
     i = _sampled("dd", "fp8", 4096, 4096, 4096, 1.0, 0, rows, cols, [0, 3, 7], [0, 5])
-    assert i.nslices == 32
+    assert i.nslices <= 32      # chosen from the data; the fixed rule ceil((100 + 12 + 16) / 4) is 32
 
 
 def test_dd_4096_balanced_digits():
-    # the same workload in balanced radix-32 e4m3 digits: s = 26 slices
+    # the same workload in balanced radix-32 e4m3 digits
     rows = [0, 1, 255, 256, 2047, 2048, 4094, 4095]
     cols = [0, 255, 256, 1000, 3071, 4095]
     i = _sampled("dd", "fp8bal", 4096, 4096, 4096, 1.0, 0, rows, cols, [0, 3, 7], [0, 5])
-    assert i.nslices == 26 and i.beta == 5
+    assert i.nslices <= 26 and i.beta == 5      # the fixed rule gives 26
 
 
 def test_qd_4096_balanced_digits():
     rows = [0, 300, 2048, 4095]
     cols = [1, 2049, 4095]
     i = _sampled("qd", "fp8bal", 4096, 4096, 4096, 1.0, 0, rows, cols, [0, 3], [0, 2])
-    assert i.nslices == 46
+    assert i.nslices <= 46      # the fixed rule gives 46
 
 
 def test_qd_4096():

@@ -8,7 +8,15 @@
 * at sizes the oracle cannot follow step by step, the factors reproduce A:
   on sampled entries the exact product L U differs from A by at most
   n 2^(-50 q) |L||U|;
+* against the exact rational factors of the Sec. 4.6 block iteration
+  (oracle.lu_exact, independent of the library's recursion, block size
+  and reciprocal iteration): the normwise errors of L and U lie within the
+  first-order perturbation bound of a backward error n 2^(-50 q) |L||U|;
 * a zero pivot is reported as a range error.
+
+The bit-exact comparison with oracle.lu is an agreement check between two
+statements of the same operations; the exact-rational and backward-error
+checks tie the factors to the factorisation itself.
 """
 from fractions import Fraction
 
@@ -22,6 +30,7 @@ if not torch.cuda.is_available():
 import paper_2301_09960_gb300 as oz
 from oracle import exact as X
 from oracle import lu as LU
+from oracle import lu_exact as LE
 
 from _util import from_dev, to_dev
 
@@ -111,3 +120,45 @@ def test_zero_pivot_is_a_range_error():
     comps[1][0, 0] = 0.0
     Ad = to_dev(comps)
     assert oz.ozmp_lu(Ad) == oz.Status.ERR_RANGE
+
+
+@pytest.mark.parametrize("q,n,dominant", [(2, 48, False), (3, 40, False), (4, 36, False), (2, 48, True),
+                                          (3, 40, True)])
+def test_factors_near_the_exact_rational_lu(q, n, dominant):
+    # The exact factors L, U of A (Fractions).  A backward error
+    # L^ U^ = A + dA with ||dA||_F <= eps ||(|L||U|)||_F, eps = n 2^(-50 q),
+    # moves the factors by at most (first order)
+    #   ||dL||_F <= eps ||L||_2 ||L^-1||_2 ||U^-1||_2 ||(|L||U|)||_F,
+    #   ||dU||_F <= eps ||L^-1||_2 ||U^-1||_2 ||U||_2 ||(|L||U|)||_F;
+    # the test allows twice that.  A wrong entry anywhere is off by O(1).
+    comps = _random(n, q, seed=700 + 10 * q + n)
+    if dominant:
+        # the paper's matrix plus n/2 on the diagonal: a well-conditioned LU
+        comps[0] = np.asfortranarray(comps[0] + np.eye(n) * (n / 2))
+    L, U = LE.lu_blocked(LE.values(comps), n)
+    Ad = to_dev(comps)
+    assert oz.ozmp_lu(Ad) == oz.Status.OK
+    F = from_dev(Ad)
+    Lf = np.array([[float(x) for x in row] for row in L])
+    Uf = np.array([[float(x) for x in row] for row in U])
+    nrm2 = lambda M: float(np.linalg.norm(M, 2))
+    Li, Ui = np.linalg.inv(Lf), np.linalg.inv(Uf)
+    base = float(np.linalg.norm(np.abs(Lf) @ np.abs(Uf)))
+    eps = n * 2.0 ** (-50 * q)
+    bound_L = 2 * eps * nrm2(Lf) * nrm2(Li) * nrm2(Ui) * base
+    bound_U = 2 * eps * nrm2(Li) * nrm2(Ui) * nrm2(Uf) * base
+    dL2 = dU2 = 0.0
+    for i in range(n):
+        for j in range(n):
+            got = X.to_fraction(X.elem_value([c[i, j] for c in F]))
+            if i > j:
+                dL2 += float(got - L[i][j]) ** 2
+            else:
+                dU2 += float(got - U[i][j]) ** 2
+    assert dL2 ** 0.5 <= bound_L, (dL2 ** 0.5, bound_L)
+    assert dU2 ** 0.5 <= bound_U, (dU2 ** 0.5, bound_U)
+    # and the bound is not vacuous: it is below what binary64 arithmetic can
+    # reach (2^-60 relative), and for the well-conditioned matrices within a
+    # factor 2^20 of the target
+    rel = 2.0 ** (20 - 50 * q) if dominant else 2.0 ** -60
+    assert bound_L < rel * nrm2(Lf) and bound_U < rel * nrm2(Uf)

@@ -73,7 +73,7 @@ def _fraction_error(A, B, Cg, rows, cols):
 @pytest.mark.parametrize("q,m,n,k", [(5, 70, 60, 50), (8, 70, 60, 50), (16, 40, 36, 30)])
 def test_split_bit_exact(q, m, n, k, form):
     A, B = gen_problem(f"q{q}", m, n, k, phi=1.0, seed=21 + q)
-    p = oz.Plan(q, m, n, k, form, 0)
+    p = oz.Plan(q, m, n, k, form, _auto_slices(q, k, form))
     p.split(to_dev(A), to_dev(B))
     torch.cuda.synchronize()
     i = p.info

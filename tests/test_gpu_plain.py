@@ -40,7 +40,8 @@ def test_thread_plan_follows_the_requested_form():
             C = _zeros(m, n)
             oz.ozmp_gemm_dd(Ad, Bd, C, s)
             torch.cuda.synchronize()
-            assert oz.ozmp_last_status() == oz.Status.OK
+            # 8 slices are far from the 2^-100 target: the check says so
+            assert oz.ozmp_last_status() == oz.Status.ERR_ACCURACY
             for g, r in zip(C, ref[want]):
                 assert torch.equal(g, r), (form, want)
     finally:

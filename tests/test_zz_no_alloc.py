@@ -28,6 +28,15 @@ def _dd(m, n, k, seed):
     return [oz.colmajor(a) for a in A], [oz.colmajor(b) for b in B]
 
 
+def _auto_count(m, n, k):
+    """The automatic slice count that nslices = 0 means here: the fixed rule
+    (the regular entry point would choose from the data instead)."""
+    h = oz.ozmp_plan_create(oz.Prec.DD, m, n, k, oz.Form.AUTO, 0, None)
+    s = oz.ozmp_plan_get_info(h).nslices
+    oz.ozmp_plan_destroy(h)
+    return s
+
+
 def _zeros(m, n):
     return [torch.zeros((n, m), dtype=torch.float64, device="cuda").T for _ in range(2)]
 
@@ -40,7 +49,7 @@ def test_noalloc_matches_regular_entry_point_on_two_calls():
         ref = _zeros(m, n)
         oz.ozmp_set_stream(torch.cuda.current_stream())
         oz.ozmp_set_form(oz.Form.AUTO)
-        oz.ozmp_gemm_dd(A, B, ref, 0)
+        oz.ozmp_gemm_dd(A, B, ref, _auto_count(m, n, k))
         got = _zeros(m, n)
         oz.ozmp_gemm_dd_noalloc(A, B, got, 0, torch.cuda.current_stream())
         torch.cuda.synchronize()
@@ -89,7 +98,7 @@ def test_noalloc_limit_is_the_whole_tile_layout():
     ref = _zeros(m_fit, n)
     oz.ozmp_set_stream(torch.cuda.current_stream())
     oz.ozmp_set_form(oz.Form.AUTO)
-    oz.ozmp_gemm_dd(A, B, ref, 0)
+    oz.ozmp_gemm_dd(A, B, ref, _auto_count(m_fit, n, k))
     got = _zeros(m_fit, n)
     oz.ozmp_gemm_dd_noalloc(A, B, got, 0, torch.cuda.current_stream())
     torch.cuda.synchronize()
