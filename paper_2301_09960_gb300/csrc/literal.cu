@@ -12,10 +12,11 @@
 //         c with 2^(2c - 53) >= l, l the inner dimension);
 //   slice_alpha = (V_s + tau) - tau in binary64 round-to-nearest;
 // and slice_D = RN64(V).  The products A_alpha B_beta (alpha + beta <= D+1)
-// are binary64 GEMMs (cuBLAS DGEMM, as the paper's GPU path); they are
+// are binary64 GEMMs (the paper's GPU path called cuBLAS DGEMM; here they run
+// on this library's own binary64 tensor-core kernel, DMMA m8n8k4); they are
 // error-free except those of the rounded remainders.  The products are
 // summed exactly and rounded canonically into the q output components.
-#include <cublas_v2.h>
+#include <cstring>
 #include <vector>
 #include "exact_acc.cuh"
 #include "kernels.h"
@@ -90,8 +91,73 @@ __global__ void __launch_bounds__(256) k_sum(const double* P, int npairs, int64_
     if (bad) atomicOr(status, ST_RANGE);
 }
 
+// P = X Y for column-major X (m x k, ld ldx), Y (k x n, ld ldy), P (m x n,
+// ld m) in binary64 on the tensor cores (mma.sync m8n8k4 f64, fp64
+// accumulation).  A 64 x 64 tile of P per block of four warps (32 x 32 each),
+// k in steps of 16 through shared memory; ragged edges are zero-filled.
+namespace dg {
+constexpr int BM = 64, BN = 64, BK = 16, NT = 128;
+constexpr int LDA = BM + 8;   // sA[kk][row]: the four k columns of a fragment fall in two bank halves
+constexpr int LDB = BK + 4;   // sB[col][kk]
+}
+
+__device__ __forceinline__ void dmma(double (&c)[2], double a, double b) {
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+                 : "+d"(c[0]), "+d"(c[1])
+                 : "d"(a), "d"(b));
+}
+
+__global__ void __launch_bounds__(128) k_dgemm(const double* X, int64_t ldx, const double* Y, int64_t ldy, double* P,
+                                               int64_t m, int64_t n, int64_t k) {
+    using namespace dg;
+    __shared__ double sA[BK * LDA];
+    __shared__ double sB[BN * LDB];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 1, wn = warp >> 1;
+    const int gq = lane >> 2, tq = lane & 3;
+    const int64_t i0 = (int64_t)blockIdx.x * BM, j0 = (int64_t)blockIdx.y * BN;
+    double acc[16][2];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) acc[e][0] = acc[e][1] = 0.0;
+    for (int64_t p0 = 0; p0 < k; p0 += BK) {
+#pragma unroll
+        for (int r = 0; r < BM * BK / NT; ++r) {
+            const int x = tid + NT * r;
+            const int row = x % BM, kk = x / BM;            // along the columns of X: coalesced
+            const int64_t i = i0 + row, p = p0 + kk;
+            sA[kk * LDA + row] = (i < m && p < k) ? X[i + p * ldx] : 0.0;
+            const int kb = x % BK, col = x / BK;            // along the columns of Y
+            const int64_t pb = p0 + kb, j = j0 + col;
+            sB[col * LDB + kb] = (pb < k && j < n) ? Y[pb + j * ldy] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k4 = 0; k4 < BK / 4; ++k4) {
+            double af[4], bf[4];
+#pragma unroll
+            for (int mt = 0; mt < 4; ++mt) af[mt] = sA[(k4 * 4 + tq) * LDA + wm * 32 + mt * 8 + gq];
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) bf[nt] = sB[(wn * 32 + nt * 8 + gq) * LDB + k4 * 4 + tq];
+#pragma unroll
+            for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) dmma(acc[mt * 4 + nt], af[mt], bf[nt]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+                const int64_t i = i0 + wm * 32 + mt * 8 + gq;
+                const int64_t j = j0 + wn * 32 + nt * 8 + 2 * tq + v;
+                if (i < m && j < n) P[i + j * m] = acc[mt * 4 + nt][v];
+            }
+}
+
 struct State {
-    cublasHandle_t h = nullptr;
     void* buf = nullptr;
     size_t bytes = 0;
     double* cptr_dev = nullptr;   // device copy of the output pointers
@@ -131,10 +197,6 @@ extern "C" ozmp_status ozmp_gemm_literal(int q, int D, int64_t m, int64_t n, int
         if (cudaMalloc(&lit::tl.buf, need) != cudaSuccess) { cudaGetLastError(); return OZMP_ERR_NOMEM; }
         lit::tl.bytes = need;
     }
-    if (!lit::tl.h) {
-        if (cublasCreate(&lit::tl.h) != CUBLAS_STATUS_SUCCESS) return OZMP_ERR_CUDA;
-    }
-    if (cublasSetStream(lit::tl.h, st) != CUBLAS_STATUS_SUCCESS) return OZMP_ERR_CUDA;
     char* w = (char*)lit::tl.buf;
     double* SA = slices_A ? slices_A : (double*)(w + o_sa);
     double* SB = slices_B ? slices_B : (double*)(w + o_sb);
@@ -171,14 +233,14 @@ extern "C" ozmp_status ozmp_gemm_literal(int q, int D, int64_t m, int64_t n, int
             }
         }
         // binary64 slice products, pairs alpha + beta <= D + 1 (alpha outer)
-        const double one = 1.0, zero = 0.0;
+        const dim3 grid((unsigned)((m + lit::dg::BM - 1) / lit::dg::BM), (unsigned)((n + lit::dg::BN - 1) / lit::dg::BN));
         int t = 0;
         for (int al = 1; al <= D; ++al)
             for (int be = 1; be <= D + 1 - al; ++be, ++t)
-                if (cublasDgemm(lit::tl.h, CUBLAS_OP_N, CUBLAS_OP_N, (int)m, (int)n, (int)k, &one,
-                                SA + (size_t)(al - 1) * m * k, (int)m, SB + (size_t)(be - 1) * k * n, (int)k, &zero,
-                                P + (size_t)t * m * n, (int)m) != CUBLAS_STATUS_SUCCESS)
-                    return OZMP_ERR_CUDA;
+                lit::k_dgemm<<<grid, lit::dg::NT, 0, st>>>(SA + (size_t)(al - 1) * m * k, m,
+                                                           SB + (size_t)(be - 1) * k * n, k, P + (size_t)t * m * n,
+                                                           m, n, k);
+        if (cudaGetLastError() != cudaSuccess) return OZMP_ERR_CUDA;
     } else {
         if (cudaMemsetAsync(P, 0, pr * 8, st) != cudaSuccess) return OZMP_ERR_CUDA;
     }
