@@ -143,8 +143,48 @@ def _host_operands(prec, m, n, k, phi, seed):
     return gen_problem(prec, m, n, k, phi=phi, seed=seed)
 
 
-def run_variant(oz, torch, prec, form, n, phi, steps, warmup, nslices=0):
-    """Device-resident timing of one (precision, form): returns a dict."""
+def target_bits(prec) -> int:
+    """Normwise target of a precision: 2^-(50 q) for q binary64 components, 2^-66 for TS."""
+    if prec == "ts":
+        return 66
+    q = {"dd": 2, "td": 3, "qd": 4}.get(prec)
+    if q is None:
+        q = int(str(prec)[1:])      # "q5" .. "q16"
+    return 50 * q
+
+
+def sample_idx(m, n, b):
+    """b evenly spaced rows and columns (first and last included)."""
+    import numpy as np
+    rows = sorted(set(np.linspace(0, m - 1, min(m, b)).astype(int).tolist()))
+    cols = sorted(set(np.linspace(0, n - 1, min(n, b)).astype(int).tolist()))
+    return rows, cols
+
+
+def sampled_error(torch, C, A, B, rows, cols, prec, ex=None):
+    """Normwise and largest elementwise relative error of the device result C
+    on a block of entries (full k), against the exact product rounded to 512
+    bits (the oracle); only that block is read back."""
+    from oracle import _clib
+    from oracle import exact as X
+    if ex is None:
+        ex = _clib.exact_block(A, B, rows, cols)
+    ri = torch.tensor(rows, device=C[0].device)
+    ci = torch.tensor(cols, device=C[0].device)
+    blk = [c.index_select(0, ri).index_select(1, ci).cpu().numpy() for c in C]
+    chat = [[[float(b[a, c]) for b in blk] for c in range(len(cols))] for a in range(len(rows))]
+    em = X.error_metrics(chat, ex)
+    out = {"err_nw": em["err_nw"], "err_max_rel": em["err_max"], "err_block": f"{len(rows)}x{len(cols)}, full k",
+           "target": 2.0 ** -target_bits(prec)}
+    if target_bits(prec) > 480:
+        # the oracle's 512-bit rounding limits what can be resolved
+        out["resolution"] = 2.0 ** -510
+    return out
+
+
+def run_variant(oz, torch, prec, form, n, phi, steps, warmup, nslices=0, err=True):
+    """Device-resident timing of one (precision, form), with the error of the
+    result on a 64 x 64 block against the oracle: returns a dict."""
     import numpy as np
     A, B = _host_operands(prec, n, n, n, phi, 0)
     Ad = [oz.colmajor(a) for a in A]
@@ -175,6 +215,9 @@ def run_variant(oz, torch, prec, form, n, phi, steps, warmup, nslices=0):
            "pairs": i.npairs, "ms_per_step": tot, "gflops": flops / (tot * 1e-3) / 1e9,
            "split_ms": sum(split_ms) / steps, "gemm_ms": sum(gemm_ms) / steps,
            "slice_tflops": i.npairs * flops / (sum(gemm_ms) / steps * 1e-3) / 1e12, "status": st.name}
+    if err:
+        rows, cols = sample_idx(n, n, 64)
+        out.update(sampled_error(torch, C, A, B, rows, cols, prec))
     del p, Ad, Bd, C
     torch.cuda.empty_cache()
     return out
@@ -182,23 +225,16 @@ def run_variant(oz, torch, prec, form, n, phi, steps, warmup, nslices=0):
 
 def literal_variant(oz, torch, n=1024):
     """Accuracy and time against the division count D: Algorithm 1 as printed
-    (binary64 round-to-nearest slices, DGEMM products) and the truncating
-    binary64-digit form with s = D, both against the e4m3 form at its
-    automatic slice count (error near 2^-106) as the reference; DD, n^3,
-    phi = 1.  err = ||C_D - C_ref||_F / ||C_ref||_F over the whole C."""
-    import numpy as np
+    (binary64 round-to-nearest slices, binary64 tensor-core products) and the
+    truncating binary64-digit form with s = D, both against the exact
+    product rounded to 512 bits (the oracle) on a 64 x 64 block (full k); DD,
+    n^3, phi = 1."""
+    from oracle import _clib
     A, B = _host_operands("dd", n, n, n, 1.0, 0)
     Ad = [oz.colmajor(a) for a in A]
     Bd = [oz.colmajor(b) for b in B]
-    ref, _ = oz.gemm(Ad, Bd, "dd", "fp8", 0)
-    R = [t.cpu().numpy() for t in ref]
-    rn = float(np.sqrt(np.sum(R[0] ** 2)))
-
-    def err(C):
-        Cn = [t.cpu().numpy() for t in C]
-        d = (Cn[0] - R[0]) + (Cn[1] - R[1])
-        return float(np.sqrt(np.sum(d ** 2))) / rn
-
+    rows, cols = sample_idx(n, n, 64)
+    ex = _clib.exact_block(A, B, rows, cols)
     out = []
     for D in (3, 4, 5, 6, 7, 8):
         row = {"D": D}
@@ -208,7 +244,7 @@ def literal_variant(oz, torch, n=1024):
             t0 = time.time()
             st = oz.ozmp_gemm_literal(Ad, Bd, C, D)
             row["literal_ms"] = (time.time() - t0) * 1e3
-            row["literal_err"] = err(C)
+            row["literal_err"] = sampled_error(torch, C, A, B, rows, cols, "dd", ex)["err_nw"]
             row["literal_status"] = st.name
             p = oz.Plan("dd", n, n, n, "fp64", D)
             C2 = [torch.empty((n, n), dtype=torch.float64, device="cuda").T for _ in range(2)]
@@ -220,12 +256,13 @@ def literal_variant(oz, torch, n=1024):
             e1.record()
             torch.cuda.synchronize()
             row["truncating_fp64_ms"] = e0.elapsed_time(e1)
-            row["truncating_fp64_err"] = err(C2)
+            row["truncating_fp64_err"] = sampled_error(torch, C2, A, B, rows, cols, "dd", ex)["err_nw"]
+            row["truncating_status"] = p.status().name
             del p
-        except Exception as ex:
-            row["error"] = repr(ex)[:200]
+        except Exception as ex_:
+            row["error"] = repr(ex_)[:200]
         out.append(row)
-    return out
+    return {"vs": "exact product rounded to 512 bits, 64 x 64 block, full k", "rows": out}
 
 
 def lu_variant(oz, torch):
@@ -285,8 +322,11 @@ def td_qd_1024_variant(oz, torch):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        out.append({"prec": prec, "form": "naive (multi-component triple loop)", "ms_per_step": ms,
-                    "gflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e9})
+        row = {"prec": prec, "form": "naive (multi-component triple loop)", "ms_per_step": ms,
+               "gflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e9}
+        rows, cols = sample_idx(n, n, 64)
+        row.update(sampled_error(torch, C, A, B, rows, cols, prec))
+        out.append(row)
     return out
 
 
@@ -314,7 +354,25 @@ def batched_512_variant(oz, torch):
     ms_b = e0.elapsed_time(e1) / reps
     st = oz.ozmp_plan_get_status(plan)
     oz.ozmp_plan_destroy(plan)
-    plans = [oz.Plan(p[0], p[1][0].shape[0], p[2][0].shape[1], p[1][0].shape[1], "auto", 0) for p in probs]
+    # error of 8 DD and 8 TD problems on up to 32 x 32 entries, against the oracle
+    import numpy as np
+    rng = np.random.default_rng(11)
+    picks = []
+    for want in ("dd", "td"):
+        idx = [i for i, sh in enumerate(shapes) if sh[3] == want]
+        picks += [int(x) for x in rng.choice(idx, 8, replace=False)]
+    errs = {"dd": [], "td": []}
+    for idx in picks:
+        m, n, k, prec = shapes[idx]
+        A, B = gen_problem(prec, m, n, k, phi=1.0, seed=1000 + idx)
+        rows, cols = sample_idx(m, n, 32)
+        errs[prec].append(sampled_error(torch, probs[idx][3], A, B, rows, cols, prec)["err_nw"])
+    # the loop of single calls does the same work: the automatic (fixed-rule) counts of the batch
+    def rule_count(p):
+        return oz.Plan(p[0], p[1][0].shape[0], p[2][0].shape[1], p[1][0].shape[1], "auto", 0,
+                       workspace=False).info.nslices
+    plans = [oz.Plan(p[0], p[1][0].shape[0], p[2][0].shape[1], p[1][0].shape[1], "auto", rule_count(p))
+             for p in probs]
     for pl, p in zip(plans, probs):
         pl.execute(p[1], p[2], p[3])
     torch.cuda.synchronize()
@@ -326,21 +384,200 @@ def batched_512_variant(oz, torch):
     ms_l = e0.elapsed_time(e1)
     return {"problems": len(probs), "gflops_total": flops / 1e9, "batched_ms": ms_b,
             "batched_gflops": flops / (ms_b * 1e-3) / 1e9, "loop_ms": ms_l,
-            "loop_gflops": flops / (ms_l * 1e-3) / 1e9, "status": st.name}
+            "loop_gflops": flops / (ms_l * 1e-3) / 1e9, "status": st.name,
+            "err_nw_max": {p: max(v) for p, v in errs.items()},
+            "err_sample": "8 DD and 8 TD problems (seed 11), up to 32 x 32 entries each, full k, against the exact "
+                          "product rounded to 512 bits",
+            "target": {"dd": 2.0 ** -100, "td": 2.0 ** -150}}
 
 
-def launches_per_step(oz, info, Bd, k, w):
-    """Kernels of one plan execution: exponent init, row exponents, row digits,
-    then for B either one pass (e4m3 forms, 16-byte aligned column starts and
-    lengths, at most 112 KB a column) or column exponents + column digits;
-    then the slice-product kernel and, for the tcgen05 forms, its rounding
-    pass."""
-    e4m3 = oz.Form(info.form) in (oz.Form.FP8, oz.Form.FP8_BAL, oz.Form.FP8_MMA)
-    ldb = Bd[0].stride(1)
-    one_pass = (e4m3 and (k * w) % 16 == 0 and (ldb * w) % 16 == 0 and len(Bd) * k * w <= 112 * 1024
-                and all(b.data_ptr() % 16 == 0 for b in Bd))
-    tc = oz.Form(info.form) in (oz.Form.FP8, oz.Form.FP8_BAL)
-    return 3 + (1 if one_pass else 2) + 1 + (1 if tc else 0)
+# peak of the slice-product engine of a form (TFLOP/s or TOPS) and its source
+def engine_peak(form, bf16, bf16_sus, src, burst):
+    if form in ("fp8", "fp8_bal", "fp8bal", "fp8_mma", "fp8mma"):
+        if burst:
+            return bf16 * 2.0, f"e4m3 dense = bf16 {src} burst x 2 (nominal ratio)"
+        return bf16_sus * 2.0, f"e4m3 dense = bf16 {src} sustained x 2 (nominal ratio)"
+    if form == "fp16":
+        # kind::f16 runs at the bf16 rate
+        if burst:
+            return bf16, f"f16 dense = bf16 {src} burst"
+        return bf16_sus, f"f16 dense = bf16 {src} sustained"
+    if form == "int8":
+        return 151.3, "IMMA mma.sync s8 microbenchmark on this GB300 (no MEASURED_PEAKS entry)"
+    return 1.05, "DMMA mma.sync f64 microbenchmark on this GB300 (no MEASURED_PEAKS entry)"
+
+
+def timed_product(oz, torch, prec, form, m, n, k, Ad, Bd, warm, nslices=0):
+    """One timed product through a plan (split, then multiply, CUDA events on
+    the current stream; the product kernel alone from the plan's timing
+    ring).  Returns (row, C, plan)."""
+    dt = torch.float32 if prec == "ts" else torch.float64
+    C = [torch.empty((n, m), dtype=dt, device="cuda").T for _ in Ad]
+    p = oz.Plan(prec, m, n, k, form, nslices)
+    for _ in range(warm):
+        p.split(Ad, Bd)
+        p.multiply(C)
+    torch.cuda.synchronize()
+    p.set_timing(1)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    p.split(Ad, Bd)
+    ev[1].record()
+    p.multiply(C)
+    ev[2].record()
+    torch.cuda.synchronize()
+    kern = p.read_timing(1)
+    p.set_timing(0)
+    i = p.info
+    flops = 2.0 * m * n * k
+    tot = ev[0].elapsed_time(ev[2])
+    split_ms = ev[0].elapsed_time(ev[1])
+    kms = kern[0] if kern else ev[1].elapsed_time(ev[2])
+    q = len(Ad)
+    w = 4 if prec == "ts" else 8
+    sb = splitter_bytes(q, w, m, n, k, i.nslices, i.digit_bytes)
+    row = {"prec": prec, "form": oz.Form(i.form).name.lower(), "beta": i.beta, "nslices": i.nslices,
+           "pairs": i.npairs, "ms": tot, "gflops": flops / (tot * 1e-3) / 1e9, "split_ms": split_ms,
+           "product_kernel_ms": kms, "slice_tflops": i.npairs * flops / (kms * 1e-3) / 1e12,
+           "splitter_gbs": sb / (split_ms * 1e-3) / 1e9, "status": p.status().name}
+    return row, C, p
+
+
+def min_slices(oz, torch, prec, form, As, Bs, ex, k, start):
+    """The smallest forced slice count whose result meets the precision's
+    target on the sampled block, found on the sampled rows and columns alone
+    (full k): their exponents, digits and sums equal those of the whole
+    product, so the block's error is the same."""
+    from oracle import exact as X
+    ms, ns = As[0].shape[0], Bs[0].shape[1]
+    tgt = 2.0 ** -target_bits(prec)
+    dt = torch.float32 if prec == "ts" else torch.float64
+
+    def err(s):
+        C = [torch.empty((ns, ms), dtype=dt, device="cuda").T for _ in As]
+        p = oz.Plan(prec, ms, ns, k, form, s)
+        p.execute(As, Bs, C)
+        torch.cuda.synchronize()
+        Cg = [c.cpu().numpy() for c in C]
+        chat = [[[float(c[a, b]) for c in Cg] for b in range(ns)] for a in range(ms)]
+        return X.error_metrics(chat, ex)["err_nw"]
+
+    s = start
+    if err(s) <= tgt:
+        while s > 1 and err(s - 1) <= tgt:
+            s -= 1
+        return s
+    while s < start + 16:
+        s += 1
+        if err(s) <= tgt:
+            return s
+    return None
+
+
+def config3_variant(oz, torch, n=4096):
+    """DD and QD n^3 with exponent spread phi in {0, 1, 4}: the balanced e4m3
+    (tcgen05), int8 (IMMA) and binary64 (DMMA) digit forms, each at the
+    slice count the library chooses from the data (nslices = 0): its time,
+    and its error on a 64 x 64 block against the oracle; beside it the
+    smallest slice count that still meets the target on that block."""
+    import numpy as np
+    from oracle import _clib
+    out = []
+    for prec in ("dd", "qd"):
+        for phi in (0.0, 1.0, 4.0):
+            A, B = _host_operands(prec, n, n, n, phi, 0)
+            rows, cols = sample_idx(n, n, 64)
+            ex = _clib.exact_block(A, B, rows, cols)
+            Ad = [oz.colmajor(a) for a in A]
+            Bd = [oz.colmajor(b) for b in B]
+            As = [oz.colmajor(np.ascontiguousarray(a[rows])) for a in A]
+            Bs = [oz.colmajor(np.ascontiguousarray(b[:, cols])) for b in B]
+            for form in ("fp8bal", "int8", "fp64"):
+                try:
+                    row, C, p = timed_product(oz, torch, prec, form, n, n, n, Ad, Bd, 0 if form == "fp64" else 1)
+                    row["phi"] = phi
+                    row.update(sampled_error(torch, C, A, B, rows, cols, prec, ex))
+                    row["s_min_on_block"] = min_slices(oz, torch, prec, form, As, Bs, ex, n, row["nslices"])
+                    del C, p
+                except Exception as e:  # report, do not hide
+                    row = {"prec": prec, "phi": phi, "form": form, "error": repr(e)[:200]}
+                out.append(row)
+            del Ad, Bd, As, Bs
+            torch.cuda.empty_cache()
+    return out
+
+
+def config5_variant(oz, torch):
+    """QD m = n = 8192, k = 16384 and TS 8192^3 (phi = 1): the balanced e4m3
+    and int8 forms (and, for TS, the binary32-slice form in binary16 digits
+    and binary64 digits), each with the fraction of its engine's peak, the
+    splitter's HBM rate and the error on a 32 x 32 block."""
+    from oracle import _clib
+    hbm, bf16, bf16_sus, src = measured_peaks()
+    out = []
+    for prec, m, n, k, forms in (("qd", 8192, 8192, 16384, ("fp8bal", "int8")),
+                                 ("ts", 8192, 8192, 8192, ("fp8bal", "fp16", "int8", "fp64"))):
+        A, B = _host_operands(prec, m, n, k, 1.0, 0)
+        rows, cols = sample_idx(m, n, 32)
+        ex = _clib.exact_block(A, B, rows, cols)
+        Ad = [oz.colmajor(a) for a in A]
+        Bd = [oz.colmajor(b) for b in B]
+        for form in forms:
+            try:
+                row, C, p = timed_product(oz, torch, prec, form, m, n, k, Ad, Bd, 1 if form == "fp8bal" else 0)
+                row.update({"m": m, "n": n, "k": k})
+                peak, note = engine_peak(form, bf16, bf16_sus, src, burst=True)
+                row["slice_frac_of_peak"] = row["slice_tflops"] / peak
+                row["peak"] = peak
+                row["peak_source"] = note
+                row["splitter_frac_of_hbm"] = row["splitter_gbs"] / hbm
+                row.update(sampled_error(torch, C, A, B, rows, cols, prec, ex))
+                del C, p
+            except Exception as e:
+                row = {"prec": prec, "form": form, "error": repr(e)[:200]}
+            out.append(row)
+        del Ad, Bd
+        torch.cuda.empty_cache()
+    out.append({"not_timed": "QD 8192^2 x 16384 in binary64 digits: about 80 DMMA slice products of 2.2 TFLOP each, "
+                             "near 3 minutes at the measured 1.05 TFLOP/s (bench.py --side config5_qd_fp64)"})
+    return out
+
+
+def config5_qd_fp64(oz, torch):
+    from oracle import _clib
+    prec, m, n, k = "qd", 8192, 8192, 16384
+    A, B = _host_operands(prec, m, n, k, 1.0, 0)
+    rows, cols = sample_idx(m, n, 32)
+    Ad = [oz.colmajor(a) for a in A]
+    Bd = [oz.colmajor(b) for b in B]
+    row, C, p = timed_product(oz, torch, prec, "fp64", m, n, k, Ad, Bd, 0)
+    row.update(sampled_error(torch, C, A, B, rows, cols, prec))
+    return row
+
+
+def launches_per_step(oz, info, Bd, k, w, adaptive=True, check=True):
+    """Kernels of one plan execution (the register splitter, q <= 4).
+
+    Slice count chosen from the data (adaptive): exponent init, the row and
+    the column exponent passes with the norms folded in, the choice, then
+    the row and the column digit kernels.  Fixed slice count: exponent init,
+    row exponents, then for B either one pass (e4m3 forms, 16-byte aligned
+    column starts and lengths, at most 112 KB a column) or column exponents
+    + column digits, the row digits, and the exponent statistics of the
+    check.  Then the slice-product kernel and, for the tcgen05 forms, its
+    rounding pass (which runs the check); the other engines take a check
+    pass over C.  (Exponents beyond +-230 add the scaled norm launches.)"""
+    form = oz.Form(info.form)
+    e4m3 = form in (oz.Form.FP8, oz.Form.FP8_BAL, oz.Form.FP8_MMA)
+    tc = form in (oz.Form.FP8, oz.Form.FP8_BAL, oz.Form.FP16)
+    if adaptive:
+        split = 4 + 2
+    else:
+        ldb = Bd[0].stride(1)
+        one_pass = (e4m3 and (k * w) % 16 == 0 and (ldb * w) % 16 == 0 and len(Bd) * k * w <= 112 * 1024
+                    and all(b.data_ptr() % 16 == 0 for b in Bd))
+        split = 3 + (1 if one_pass else 2) + (1 if check else 0)
+    return split + 1 + (1 if tc else (1 if check else 0))
 
 
 def splitter_bytes(q, w, m, n, k, s, db):
@@ -429,7 +666,6 @@ def main():
     Bd = [oz.colmajor(b) for b in B]
     C = [torch.empty((n, m), dtype=dt, device="cuda").T for _ in range(q)]
     plan = oz.Plan(prec, m, n, k, form, args.nslices)
-    info = plan.info
 
     for _ in range(args.warmup):
         plan.split(Ad, Bd)
@@ -463,6 +699,7 @@ def main():
     split_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
     gemm_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / args.steps
     status = plan.status()
+    info = plan.info          # the slice count the splits chose from the data
     if ws > 1:
         total_ms = _max_over_ranks(total_ms, "cuda")
     ms_per_step = total_ms / args.steps
@@ -530,19 +767,20 @@ def main():
 
     # ---- roofline of the dominant kernel (slice products) ----
     hbm, bf16, bf16_sus, src = measured_peaks()
-    peak_fp8 = bf16 * 2.0        # e4m3 dense / bf16 dense nominal ratio (4.5 / 2.25)
     alg_flops = info.npairs * flops
     achieved = alg_flops / (kernel_ms * 1e-3) / 1e12
-    peak_burst = None
-    if info.form in (oz.Form.FP8, oz.Form.FP8_BAL, oz.Form.FP8_MMA):
-        # the kernel is timed inside back-to-back steps that hold the GPU at its
-        # power cap: the sustained bf16 figure x 2 is the matching denominator
-        peak, peak_note = bf16_sus * 2.0, f"e4m3 dense = bf16 {src} sustained x 2 (nominal ratio)"
-        peak_burst = peak_fp8
-    elif info.form == oz.Form.INT8:
-        peak, peak_note = 151.3, "IMMA mma.sync s8 microbenchmark on this GB300 (no MEASURED_PEAKS entry)"
-    else:
-        peak, peak_note = 1.05, "DMMA mma.sync f64 microbenchmark on this GB300 (no MEASURED_PEAKS entry)"
+    # the burst peak matches a kernel timed in a short region at full clock;
+    # the sustained one (a seconds-long loop under the power cap) matches a
+    # region of seconds or one whose SM clock sat below its maximum
+    region_s = total_ms * 1e-3
+    capped = (clk.get("sm_mhz") is not None and clk.get("sm_max_mhz")
+              and clk["sm_mhz"] < 0.95 * clk["sm_max_mhz"])
+    burst = region_s < 2.0 and not capped
+    fname = oz.Form(info.form).name.lower()
+    peak, peak_note = engine_peak(fname, bf16, bf16_sus, src, burst)
+    peak_note += (f"; timed region {region_s:.2f} s at median SM {clk.get('sm_mhz')} of {clk.get('sm_max_mhz')} MHz"
+                  f" -> {'burst' if burst else 'sustained'}")
+    peak_other = engine_peak(fname, bf16, bf16_sus, src, not burst)[0]
     sbytes = splitter_bytes(q, w, m, n, k, info.nslices, info.digit_bytes)
     # DRAM bytes (read + write) of one launch of the product kernel, from the
     # one-pass ncu capture of this workload's launch in
@@ -555,9 +793,9 @@ def main():
         "metric": metric, "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "e4m3" if info.form in (oz.Form.FP8, oz.Form.FP8_BAL, oz.Form.FP8_MMA) else
-        ("s8" if info.form == oz.Form.INT8 else "f64"),
+        ({oz.Form.INT8: "s8", oz.Form.FP16: "f16"}.get(oz.Form(info.form), "f64")),
         "acc_dtype": "f32 (integers below 2^24, exact) -> int64 carry-save limbs"
-        if info.form in (oz.Form.FP8, oz.Form.FP8_BAL) else
+        if info.form in (oz.Form.FP8, oz.Form.FP8_BAL, oz.Form.FP16) else
         ("f32 (exact integers) -> int64" if info.form == oz.Form.FP8_MMA else
          ("s32 -> int64" if info.form == oz.Form.INT8 else "f64 (exact integers) -> int64")),
         "data": "synthetic (Eq. 1, seeded)",
@@ -567,11 +805,12 @@ def main():
                    "l2": "inputs larger than L2 (A, B and the digit workspace each exceed 129 MB)"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": {oz.Form.FP8: "k_gemm_tc (tcgen05)",
-                                oz.Form.FP8_BAL: "k_gemm_tc (tcgen05)", oz.Form.FP8_MMA: "k_gemm_b1<FP8> (mma.sync)",
+                                oz.Form.FP8_BAL: "k_gemm_tc (tcgen05)", oz.Form.FP16: "k_gemm_tc (tcgen05 kind::f16)",
+                                oz.Form.FP8_MMA: "k_gemm_b1<FP8> (mma.sync)",
                                 oz.Form.INT8: "k_gemm_b1<INT8> (mma.sync)"}.get(oz.Form(info.form), "k_gemm_f64 (DMMA)"),
                      "peak_source": peak_note,
-                     # context: the burst figure (a kernel timed alone), bf16 burst x 2
-                     "peak_burst": peak_burst, "frac_burst": achieved / peak_burst if peak_burst else None},
+                     # context: the other figure of the pair
+                     "peak_other": peak_other, "frac_other": achieved / peak_other},
         "splitter": {"ms": split_ms, "bytes": sbytes, "achieved_gbs": sbytes / (split_ms * 1e-3) / 1e9,
                      "peak_gbs": hbm, "frac": sbytes / (split_ms * 1e-3) / 1e9 / hbm},
         "stage_ms": {"split": split_ms, "products": gemm_ms, "product_kernel": kernel_ms},
@@ -579,7 +818,7 @@ def main():
                 "ms_per_step": e2e_ms, "steps": e2e_steps,
                 "pipelined": "operands of step i+1 copied in and the result of step i-1 copied out on two copy "
                              "streams during step i's product (double-buffered device operands)"},
-        "gpu_launches": launches_per_step(oz, info, Bd, k, w) * args.steps,
+        "gpu_launches": launches_per_step(oz, info, Bd, k, w, adaptive=args.nslices == 0) * args.steps,
         "clocks": clk,
         "device_status": status.name,
     }
@@ -625,6 +864,9 @@ SIDE = {
     "lu_4096": lambda oz, torch: lu_variant(oz, torch),
     "literal_vs_truncating_1024": lambda oz, torch: literal_variant(oz, torch),
     "td_qd_1024": lambda oz, torch: td_qd_1024_variant(oz, torch),
+    "config3_phi_sweep_4096": lambda oz, torch: config3_variant(oz, torch),
+    "config5_large": lambda oz, torch: config5_variant(oz, torch),
+    "config5_qd_fp64": lambda oz, torch: config5_qd_fp64(oz, torch),
 }
 
 
@@ -633,8 +875,9 @@ def add_variants(line, oz, torch, args):
     forms and precisions, more components, LU, Algorithm 1 as printed, TD/QD
     at 1024 and the batched problems."""
     var = []
-    for vp, vf in [("dd", "fp8"), ("dd", "fp8mma"), ("dd", "int8"), ("dd", "fp64"), ("qd", "fp8bal"),
-                   ("qd", "fp8"), ("qd", "fp8mma"), ("qd", "int8"), ("qd", "fp64")]:
+    # (the int8 and binary64 forms at 4096^3 are in config3, per exponent spread)
+    for vp, vf in [("dd", "fp8"), ("dd", "fp8mma"), ("dd", "fp16"), ("qd", "fp8bal"), ("qd", "fp8"),
+                   ("qd", "fp8mma")]:
         try:
             var.append(run_variant(oz, torch, vp, vf, args.n, args.phi, 1, 1))
         except Exception as ex:  # report, do not hide
@@ -656,6 +899,8 @@ def add_variants(line, oz, torch, args):
     line["literal_vs_truncating_1024"] = literal_variant(oz, torch)
     line["td_qd_1024"] = td_qd_1024_variant(oz, torch)
     line["batched_512_problems"] = batched_512_variant(oz, torch)
+    line["config3_phi_sweep_4096"] = config3_variant(oz, torch)
+    line["config5_large"] = config5_variant(oz, torch)
 
 
 if __name__ == "__main__":

@@ -84,9 +84,13 @@ typedef enum {
     OZMP_FORM_INT8 = 2,     /* int8 digits, beta = 7, IMMA int32 accumulation */
     OZMP_FORM_FP8  = 3,     /* e4m3 digits, beta = 4, tcgen05 kind::f8f6f4, binary32 accumulation in TMEM */
     OZMP_FORM_FP8_MMA = 4,  /* the same e4m3 digits on the legacy mma.sync QMMA path */
-    OZMP_FORM_FP8_BAL = 5   /* e4m3 digits, beta = 5: the truncated value floor(|x| 2^(5s-1-E)) in
+    OZMP_FORM_FP8_BAL = 5,  /* e4m3 digits, beta = 5: the truncated value floor(|x| 2^(5s-1-E)) in
                                balanced radix-32 digits (|d| <= 16, signed like x), tcgen05
                                kind::f8f6f4; a third fewer slices than FORM_FP8 for one bound */
+    OZMP_FORM_FP16 = 6      /* the binary32-slice form (the paper's SGEMM slices, S = 24): digits
+                               of beta = max{b <= 11: k (2^b - 1)^2 <= 2^24} bits held exactly in
+                               binary16, tcgen05 kind::f16 with binary32 accumulation in TMEM;
+                               at most 4 components */
 } ozmp_form;
 
 /* all-zero row/column exponent */
@@ -251,7 +255,8 @@ ozmp_status ozmp_gemm_dd_noalloc(int64_t m, int64_t n, int64_t k, const double* 
  * The problem array and the component-pointer arrays it points to are read
  * during the call only.  Batched problems hold at most 4 components,
  * 64 four-bit or 63 balanced slices and m n < 2^31 elements of C (else
- * OZMP_ERR_UNSUPPORTED); larger ones go through single-problem plans.  form FP8_BAL runs every problem in balanced
+ * OZMP_ERR_UNSUPPORTED); larger ones go through single-problem plans, and
+ * so does FORM_FP16 (UNSUPPORTED in a batch).  form FP8_BAL runs every problem in balanced
  * radix-32 digits; a plan is reused only with the form it was made for.
  */
 typedef struct {

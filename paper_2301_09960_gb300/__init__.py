@@ -57,6 +57,7 @@ class Form(IntEnum):
     FP8 = 3
     FP8_MMA = 4
     FP8_BAL = 5
+    FP16 = 6
 
 
 MAX_COMPONENTS = 16
@@ -64,7 +65,7 @@ MAX_COMPONENTS = 16
 PREC_BY_NAME = {"dd": Prec.DD, "td": Prec.TD, "qd": Prec.QD, "ts": Prec.TS}
 PREC_BY_NAME.update({f"q{q}": q for q in range(2, MAX_COMPONENTS + 1)})
 FORM_BY_NAME = {"auto": Form.AUTO, "fp64": Form.FP64, "int8": Form.INT8, "fp8": Form.FP8,
-                "fp8mma": Form.FP8_MMA, "fp8bal": Form.FP8_BAL}
+                "fp8mma": Form.FP8_MMA, "fp8bal": Form.FP8_BAL, "fp16": Form.FP16}
 NCOMP = {Prec.DD: 2, Prec.TD: 3, Prec.QD: 4, Prec.TS: 3}
 NCOMP.update({q: q for q in range(5, MAX_COMPONENTS + 1)})
 
@@ -496,7 +497,7 @@ class Plan:
         """(A digits [s, mp, kp], B digits [s, np, kp]) in the stored encoding."""
         import torch
         i = self.info
-        dt = torch.float64 if i.digit_bytes == 8 else torch.uint8
+        dt = {8: torch.float64, 2: torch.float16}.get(i.digit_bytes, torch.uint8)
         a = self._region(i.off_Adig, i.nslices * i.mp * i.kp, dt).view(i.nslices, i.mp, i.kp)
         b = self._region(i.off_Bdig, i.nslices * i.np * i.kp, dt).view(i.nslices, i.np, i.kp)
         return a, b

@@ -30,6 +30,7 @@ static ozmp_status plan_make_like(const ozmp_plan_s* p, int s, ozmp_plan_s* t) {
         t->env_static = p->env_static;
         t->env_group = p->env_group;
         t->env_maxc = p->env_maxc;
+        t->env_lock = p->env_lock;
         t->tc_wait_limit = p->tc_wait_limit;
         t->tc_inject_stall = p->tc_inject_stall;
     }
@@ -61,6 +62,8 @@ static ozmp_status plan_set_slices(ozmp_plan_s* p, int s) {
     t.check = p->check;
     t.s_lo = p->s_lo;
     t.s_cap = p->s_cap;
+    t.host_s = p->host_s;
+    t.ev_s = p->ev_s;
     t.sched_ws = nullptr;   // the new schedule is uploaded before the next product
     delete[] p->sched_host;
     *p = t;
@@ -102,6 +105,15 @@ ozmp_status plan_create_internal(ozmp_plan* plan, ozmp_prec prec, int64_t m, int
             p->s_lo = s;
         }
         p->ws_bytes = most;
+        // the read-back of the chosen s: a pinned word and an event after its copy
+        if (cudaMallocHost((void**)&p->host_s, sizeof(int)) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p->ev_s, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            if (p->host_s) cudaFreeHost(p->host_s);
+            delete[] p->sched_host;
+            delete p;
+            return OZMP_ERR_NOMEM;
+        }
     }
     *plan = p;
     return OZMP_OK;
@@ -137,6 +149,11 @@ ozmp_status ozmp_plan_destroy(ozmp_plan p) {
         cudaFree(p->ws);
     }
     free_timing(p);
+    if (p->host_s) {
+        cudaStreamSynchronize(p->stream);
+        cudaFreeHost(p->host_s);
+        cudaEventDestroy(p->ev_s);
+    }
     delete[] p->sched_host;
     delete p;
     return OZMP_OK;
@@ -178,27 +195,58 @@ ozmp_status ozmp_plan_set_stream(ozmp_plan p, ozmp_stream stream) {
 }
 
 // Exponents and digits.  An adaptive plan reduces the exponents, chooses s
-// from the data (one 4-byte read-back: the call waits for that pass), re-makes
-// itself for that s and writes the digits; other plans split in one go and
+// from the data (one 4-byte read-back: the call waits for that pass; the
+// digits for the previous count are already queued behind it), re-makes
+// itself for a new s and writes its digits; other plans split in one go and
 // take the exponent statistics of the a-posteriori check.
 static ozmp_status do_split(ozmp_plan p, const void* const* A, int64_t lda, const void* const* B, int64_t ldb) {
     SplitArgs a = split_args(p, A, lda, B, ldb);
     char* w = (char*)p->ws;
     if (p->adapt) {
-        if (launch_split_exponents(a, p->stream) != cudaSuccess) return OZMP_ERR_CUDA;
         BoundStats* bs = bound_stats(p);
-        if (launch_bound_scale(a.E, p->m, a.F, p->n, bs, (double*)(w + p->off_rowB), p->k, true, p->stream) !=
-                cudaSuccess ||
-            launch_bound_choose(A, lda, B, ldb, p->q, p->is_f32 != 0, p->m, p->n, p->k, bs,
-                                (double*)(w + p->off_colA), (double*)(w + p->off_rowB), bound_form(p), p->s_lo,
-                                p->s_cap, p->stream) != cudaSuccess)
+        double* colA = (double*)(w + p->off_colA);
+        double* rowB = (double*)(w + p->off_rowB);
+        auto copy_s = [&]() {   // the chosen s into the pinned word, then the event
+            return cudaMemcpyAsync(p->host_s, &bs->s_needed, sizeof(int), cudaMemcpyDeviceToHost, p->stream) ==
+                       cudaSuccess &&
+                   cudaEventRecord(p->ev_s, p->stream) == cudaSuccess;
+        };
+        auto read_s = [&](int* s) {
+            if (!copy_s() || cudaEventSynchronize(p->ev_s) != cudaSuccess) return false;
+            *s = *p->host_s;
+            return true;
+        };
+        auto scaled_choice = [&]() {   // norms scaled by the largest exponents (any exponent range)
+            return launch_bound_scale(a.E, p->m, a.F, p->n, bs, rowB, p->k, true, p->stream) == cudaSuccess &&
+                   launch_bound_choose(A, lda, B, ldb, p->q, p->is_f32 != 0, p->m, p->n, p->k, bs, colA, rowB,
+                                       bound_form(p), p->s_lo, p->s_cap, p->stream) == cudaSuccess;
+        };
+        // the exponent pass with the unscaled norms folded in, and the choice
+        // in one launch; the scaled norms when the exponents leave their range
+        // (and for the many-component splitter)
+        if (cudaMemsetAsync(colA, 0, p->off_rowB - p->off_colA + (size_t)p->k * 8, p->stream) != cudaSuccess)
             return OZMP_ERR_CUDA;
-        int s = 0;
-        if (cudaMemcpyAsync(&s, &bs->s_needed, sizeof(int), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
-            cudaStreamSynchronize(p->stream) != cudaSuccess)
+        const cudaError_t en = launch_split_exponents_norm(a, colA, rowB, p->stream);
+        bool ok;
+        if (en == cudaErrorNotSupported) {
+            cudaGetLastError();
+            ok = launch_split_exponents(a, p->stream) == cudaSuccess && scaled_choice();
+        } else {
+            ok = en == cudaSuccess && launch_bound_choose_raw(a.E, p->m, a.F, p->n, colA, rowB, p->k, bs,
+                                                              bound_form(p), p->s_lo, p->s_cap,
+                                                              p->stream) == cudaSuccess;
+        }
+        if (!ok || !copy_s()) return OZMP_ERR_CUDA;
+        // the digits for the count of the last execution go into the stream
+        // before the host waits for the new choice, so that the GPU splits
+        // while the host reads; a different choice splits again
+        if (launch_split_digits(a, p->stream) != cudaSuccess || cudaEventSynchronize(p->ev_s) != cudaSuccess)
             return OZMP_ERR_CUDA;
+        int s = *p->host_s;
+        if (s < 0 && (!scaled_choice() || !read_s(&s))) return OZMP_ERR_CUDA;
         if (s < p->s_lo) s = p->s_lo;
         if (s > p->s_cap) s = p->s_cap;
+        if (s == p->s) return OZMP_OK;
         ozmp_status st = plan_set_slices(p, s);
         if (st != OZMP_OK) return st;
         a = split_args(p, A, lda, B, ldb);
@@ -219,8 +267,16 @@ static ozmp_status do_multiply(ozmp_plan p, void* const* C, int64_t ldc) {
     for (int c = 0; c < OZMP_MAX_COMPONENTS; ++c) g.C[c] = (c < p->q) ? C[c] : nullptr;
     g.ldc = ldc;
     take_timing(p, g);
+    // the tcgen05 rounding pass runs the check as it writes C; the other
+    // engines take a pass over C's first component
+    const bool in_pass = p->check && tc_engine(p->form);
+    if (in_pass) {
+        g.chk = bound_stats(p);
+        g.chk_form = bound_form(p);
+        g.chk_flag = ST_ACCURACY;
+    }
     if (launch_gemm(g, p->stream) != cudaSuccess) return OZMP_ERR_CUDA;
-    if (p->check &&
+    if (p->check && !in_pass &&
         launch_bound_check(C[0], p->is_f32 != 0, p->m, p->n, ldc, bound_stats(p), bound_form(p), p->s,
                            (uint32_t*)((char*)p->ws + p->off_status), ST_ACCURACY, p->stream) != cudaSuccess)
         return OZMP_ERR_CUDA;
@@ -335,7 +391,7 @@ ozmp_status ozmp_set_stream(ozmp_stream stream) {
 }
 
 ozmp_status ozmp_set_form(ozmp_form form) {
-    if (form < OZMP_FORM_AUTO || form > OZMP_FORM_FP8_BAL) return OZMP_ERR_INVALID_ARG;
+    if (form < OZMP_FORM_AUTO || form > OZMP_FORM_FP16) return OZMP_ERR_INVALID_ARG;
     tl_form = form;
     return OZMP_OK;
 }

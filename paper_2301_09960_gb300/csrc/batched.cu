@@ -234,7 +234,8 @@ void destroy(void* b) { destroy_batch((Batch*)b); }
 extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, ozmp_form form, ozmp_stream stream,
                                          ozmp_plan* plan) {
     if (!probs || count <= 0 || !plan) return OZMP_ERR_INVALID_ARG;
-    if (form < OZMP_FORM_AUTO || form > OZMP_FORM_FP8_BAL) return OZMP_ERR_INVALID_ARG;
+    if (form < OZMP_FORM_AUTO || form > OZMP_FORM_FP16) return OZMP_ERR_INVALID_ARG;
+    if (form == OZMP_FORM_FP16) return OZMP_ERR_UNSUPPORTED;   // single-problem plans only
     // balanced digits run on the tcgen05 engine of the e4m3 form (also the
     // automatic choice, unless a problem forces more slices than they allow)
     bool bal = (form == OZMP_FORM_FP8_BAL);
@@ -672,6 +673,7 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
                     cudaMemsetAsync((char*)b->ws + b->off_split, 0, b->split_bytes, cs);
                 if (b->grid > 0) {
                     tc::Sched sc;
+                    memset(&sc, 0, sizeof(sc));   // no lockstep, no dynamic feed
                     sc.probs = (const tc::Prob*)((char*)b->meta + b->off_probs);
                     sc.maps = (const CUtensorMap*)((char*)b->meta + b->off_maps);
                     sc.items = (const tc::WorkItem*)((char*)b->meta + b->off_items);

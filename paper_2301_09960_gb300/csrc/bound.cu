@@ -193,41 +193,86 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_bound_check(const T* C0, int64_t m, int64_t n, int64_t ldc, BoundStats* st,
                                                      BoundForm f, int s, uint32_t* status, uint32_t flag) {
     __shared__ double shd[32];
-    __shared__ bool last;
     const int ge = st->GE, gf = st->GF;
     const bool zero = (ge == OZMP_EXP_ZERO || gf == OZMP_EXP_ZERO);
     double acc = 0.0;
-    if (!zero) {
-        const int g = ge + gf;
-        const bool plain = g > -1000 && g < 1000;
-        const double sc = plain ? pow2(-g) : 1.0;
-        for (int64_t j = blockIdx.x; j < n; j += gridDim.x)
+    if (!zero)
+        for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
+            float col = 0.f;   // binary32 partial sums: one column part of at most m / 256 squares
             for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
-                const double x = scaled((double)C0[i + j * ldc], g, sc, plain);
-                acc += x * x;
+                const float y = bound_abs_scaled_f32((double)C0[i + j * ldc], ge + gf);
+                col += y * y;
             }
-    }
+            acc += (double)col;
+        }
     acc = block_sum(acc, shd);
+    if (threadIdx.x == 0) bound_finish_block(st, acc, gridDim.x, f, s, status, flag);
+}
+
+// GE, GF, SE, SF from the exponents, est from the unscaled norms of the
+// exponent pass, and the slice count (-1: an exponent beyond the raw range)
+__global__ void __launch_bounds__(1024) k_bound_choose_raw(const int32_t* E, int64_t m, const int32_t* F, int64_t n,
+                                                           const double* colA, const double* rowB, int64_t k,
+                                                           BoundStats* st, BoundForm f, int s_lo, int s_hi) {
+    __shared__ int shi[32];
+    __shared__ double shd[32];
+    int ge = OZMP_EXP_ZERO, gf = OZMP_EXP_ZERO;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) ge = max(ge, E[i]);
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) gf = max(gf, F[j]);
+    ge = block_max(ge, shi);
+    gf = block_max(gf, shi);
+    double se = 0.0, sf = 0.0, v = 0.0;
+    if (ge != OZMP_EXP_ZERO)
+        for (int64_t i = threadIdx.x; i < m; i += blockDim.x)
+            if (E[i] != OZMP_EXP_ZERO) se += pow2(2 * (E[i] - ge));
+    if (gf != OZMP_EXP_ZERO)
+        for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
+            if (F[j] != OZMP_EXP_ZERO) sf += pow2(2 * (F[j] - gf));
+    for (int64_t p0 = threadIdx.x; p0 < k; p0 += 4 * (int64_t)blockDim.x) {
+        double a4[4], b4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t p = p0 + (int64_t)u * blockDim.x;
+            a4[u] = p < k ? colA[p] : 0.0;
+            b4[u] = p < k ? rowB[p] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v += a4[u] * b4[u];
+    }
+    se = block_sum(se, shd);
+    __syncthreads();
+    sf = block_sum(sf, shd);
+    __syncthreads();
+    v = block_sum(v, shd);
+    __shared__ double bc[3];   // SE, SF, est to every thread
+    __shared__ int best;
     if (threadIdx.x == 0) {
-        atomicAdd(&st->normS2, acc);
-        __threadfence();
-        last = (atomicAdd(&st->done, 1u) == gridDim.x - 1);
+        bc[0] = se;
+        bc[1] = sf;
+        bc[2] = v;
+        best = s_hi;
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
-    __threadfence();
-    const double n2 = atomicAdd(&st->normS2, 0.0);
-    // ready for the check of another multiply of the same split
+    se = bc[0];
+    sf = bc[1];
+    v = bc[2];
+    const bool zero = (ge == OZMP_EXP_ZERO || gf == OZMP_EXP_ZERO || !(v > 0.0));
+    const bool raw = !(ge > BOUND_RAW_EXP || ge < -BOUND_RAW_EXP || gf > BOUND_RAW_EXP || gf < -BOUND_RAW_EXP);
+    const double lest = zero ? 0.0 : log2(v) - 2.0 * (double)(ge + gf);   // log2 of est scaled by 4^-(GE + GF)
+    // candidate s_lo + x in thread x (the binary64 logarithms are slow one after another)
+    const int t = s_lo + (int)threadIdx.x;
+    if (!zero && raw && t <= s_hi && bound_log2(f, t, se, sf) <= -(double)(f.target + 1) + 0.5 * lest)
+        atomicMin(&best, t);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    st->GE = ge;
+    st->GF = gf;
+    st->SE = se;
+    st->SF = sf;
     st->normS2 = 0.0;
     st->done = 0u;
-    if (zero) return;
-    // N: a lower bound of ||S||_F (the first components are within 2^-53 of
-    // S, the sum of squares within far less than 2^-20)
-    const double N = sqrt(n2) * (1.0 - ldexp(1.0, -20));
-    const double B = exp2(bound_log2(f, s, st->SE, st->SF));
-    bool ok = N > B;
-    if (ok) ok = (B + f.uq * N) / (N - B) <= ldexp(1.0, -f.target);
-    if (!ok) atomicOr(status, flag);
+    st->est = zero || !raw ? 0.0 : exp2(lest);
+    st->s_needed = zero ? s_lo : (!raw ? -1 : best);
 }
 
 Ptrs make_ptrs(const void* const* v, int q) {
@@ -251,18 +296,24 @@ cudaError_t launch_bound_choose(const void* const* A, int64_t lda, const void* c
         const Ptrs a = make_ptrs(A, q), b = make_ptrs(B, q);
         const unsigned gc = (unsigned)((k * 32 + 255) / 256);
         const dim3 gr((unsigned)((k + 255) / 256), (unsigned)((n + 63) / 64));
-        // the estimate reads the leading component only (an estimate: the
-        // a-posteriori check certifies the result whatever it gives)
-        (void)q;
+        // each element as the binary64 sum of its components: components
+        // that cancel would mislead an estimate from the leading one alone
         if (is_f32) {
-            k_bound_colnorm<float><<<gc, 256, 0, stream>>>(a, 1, lda, m, k, st, colA);
-            k_bound_rownorm<float><<<gr, 256, 0, stream>>>(b, 1, ldb, k, n, st, rowB);
+            k_bound_colnorm<float><<<gc, 256, 0, stream>>>(a, q, lda, m, k, st, colA);
+            k_bound_rownorm<float><<<gr, 256, 0, stream>>>(b, q, ldb, k, n, st, rowB);
         } else {
-            k_bound_colnorm<double><<<gc, 256, 0, stream>>>(a, 1, lda, m, k, st, colA);
-            k_bound_rownorm<double><<<gr, 256, 0, stream>>>(b, 1, ldb, k, n, st, rowB);
+            k_bound_colnorm<double><<<gc, 256, 0, stream>>>(a, q, lda, m, k, st, colA);
+            k_bound_rownorm<double><<<gr, 256, 0, stream>>>(b, q, ldb, k, n, st, rowB);
         }
     }
     k_bound_choose<<<1, 1024, 0, stream>>>(st, colA, rowB, (m > 0 && n > 0) ? k : 0, f, s_lo, s_hi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bound_choose_raw(const int32_t* E, int64_t m, const int32_t* F, int64_t n, const double* colA,
+                                    const double* rowB, int64_t k, BoundStats* st, const BoundForm& f, int s_lo,
+                                    int s_hi, cudaStream_t stream) {
+    k_bound_choose_raw<<<1, 1024, 0, stream>>>(E, m, F, n, colA, rowB, (m > 0 && n > 0) ? k : 0, st, f, s_lo, s_hi);
     return cudaGetLastError();
 }
 

@@ -8,7 +8,8 @@ cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t st);
 
 cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t st) {
     if (g.mp == 0 || g.np == 0) return cudaSuccess;
-    if (g.form == OZMP_FORM_FP8) return launch_gemm_tc(g, st);   // records the timing pair itself
+    if (g.form == OZMP_FORM_FP8 || g.form == OZMP_FORM_FP16)
+        return launch_gemm_tc(g, st);   // records the timing pair itself
     if (g.tev_start) cudaEventRecord(g.tev_start, st);
     cudaError_t e;
     if (g.form == OZMP_FORM_INT8) {

@@ -127,6 +127,10 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
         if (lane == 0) {
             long long n = 0;
             bool ok = true;
+            // lockstep (the leader's producer of each cluster): whole-tile pairs issued so far
+            const bool lock = sc.step_done != nullptr && rank == 0;
+            long long P = 0;
+            bool gone = false;
             for (int k = 0; ok; ++k) {
                 const int idx = take(k, rank == 0, false);
                 if (idx == -2) { ok = false; break; }
@@ -136,8 +140,16 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                 const Prob p = *it.p;
                 const unsigned tx = CG == 2 ? 2u * (STAGE_A + SB) : STAGE_A + (unsigned)it.bn * BK;
                 const int jb = (int)it.j0 + (CG == 2 ? (int)rank * (BN / 2) : 0);
+                const bool whole = it.pa == 0 && it.pb == p.s * (p.s + 1) / 2;
+                if (lock && !whole && !gone) { atomicAdd(sc.retired, 1); gone = true; }
                 Walk w = Walk::at(it.dhi, it.pa);
                 for (int pi = it.pa; ok && pi < it.pb; ++pi) {
+                    if (lock && whole && P >= sc.lock_w && P - sc.lock_w < sc.lock_n) {
+                        // soft: after LOCK_POLLS polls the walk goes on regardless
+                        const volatile int* dp = sc.step_done + (P - sc.lock_w);
+                        const volatile int* rp = sc.retired;
+                        for (int x = 0; x < LOCK_POLLS && *dp + *rp < ncl; ++x) __nanosleep(128);
+                    }
                     const int u = w.d - w.t;
                     const int ya = (w.t - 1) * (int)p.mp + (int)it.i0;
                     const int yb = (u - 1) * (int)p.np + jb;
@@ -157,9 +169,14 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                             tma_load_2d(sB + (size_t)st * SB, it.mb, &full[st], kc * BK, yb);
                         }
                     }
+                    if (lock && whole) {
+                        if (P < sc.lock_n) atomicAdd(sc.step_done + P, 1);
+                        ++P;
+                    }
                     w.next_pair();
                 }
             }
+            if (lock && !gone) atomicAdd(sc.retired, 1);
             if (!ok) {
                 raise_abort();
                 // let the copies already issued land before the CTA can exit (the
@@ -199,11 +216,16 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                         const uint64_t bd = desc_sw128(saddr(sB + (size_t)st * SB));
 #pragma unroll
                         for (int kk = 0; kk < BK / 32; ++kk) {
+                            // 32 bytes of K per MMA: 32 e4m3 or 16 binary16 digits
                             const uint32_t acc = (fresh && kk == 0) ? 0u : 1u;
-                            if (CG == 2)
-                                mma_e4m3_tc_pair(dcol, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, acc);
-                            else
-                                mma_e4m3_tc(dcol, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, acc);
+                            const uint64_t a2 = ad + (uint64_t)(2 * kk), b2 = bd + (uint64_t)(2 * kk);
+                            if (p.kind) {
+                                if (CG == 2) mma_f16_tc_pair(dcol, a2, b2, idesc, acc);
+                                else mma_f16_tc(dcol, a2, b2, idesc, acc);
+                            } else {
+                                if (CG == 2) mma_e4m3_tc_pair(dcol, a2, b2, idesc, acc);
+                                else mma_e4m3_tc(dcol, a2, b2, idesc, acc);
+                            }
                         }
                         fresh = false;
                         if (CG == 2) mma_commit_pair(&empty[st]);
@@ -535,12 +557,15 @@ int tc_num_pair_slots() {
 }
 
 cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t st) {
-    if (g.mp % tc::BM || g.np % tc::BN || g.kp % tc::BK) return cudaErrorInvalidValue;
+    // binary16 digits take two bytes: the maps and the K steps count bytes
+    const int kind = g.form == OZMP_FORM_FP16 ? 1 : 0;
+    const int64_t kpb = g.kp * (kind ? 2 : 1);
+    if (g.mp % tc::BM || g.np % tc::BN || kpb % tc::BK) return cudaErrorInvalidValue;
     const int cg = (g.tc_cg == 2 && g.mp % (2 * tc::BM) == 0) ? 2 : 1;
     if (g.tc_cg == 2 && cg != 2) return cudaErrorInvalidValue;   // the schedule counts pair tiles
     CUtensorMap ma, mb;
-    if (!tc_make_map(&ma, g.Adig, (uint64_t)g.s * g.mp, (uint64_t)g.kp, tc::BM)) return cudaErrorInvalidValue;
-    if (!tc_make_map(&mb, g.Bdig, (uint64_t)g.s * g.np, (uint64_t)g.kp, tc::BN / cg)) return cudaErrorInvalidValue;
+    if (!tc_make_map(&ma, g.Adig, (uint64_t)g.s * g.mp, (uint64_t)kpb, tc::BM)) return cudaErrorInvalidValue;
+    if (!tc_make_map(&mb, g.Bdig, (uint64_t)g.s * g.np, (uint64_t)kpb, tc::BN / cg)) return cudaErrorInvalidValue;
     cudaError_t e = tc_set_smem();
     if (e != cudaSuccess) return e;
     tc::Prob p;
@@ -548,7 +573,8 @@ cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t st) {
     p.E = g.E; p.F = g.F; p.acc = g.acc;
     for (int c = 0; c < OZMP_MAX_COMPONENTS; ++c) p.C[c] = g.C[c];
     p.T = g.T;
-    p.m = g.m; p.n = g.n; p.mp = g.mp; p.np = g.np; p.kp = g.kp; p.ldc = g.ldc;
+    p.m = g.m; p.n = g.n; p.mp = g.mp; p.np = g.np; p.kp = kpb; p.ldc = g.ldc;
+    p.kind = kind;
     p.q = g.q; p.is_f32 = g.is_f32; p.s = g.s; p.beta = g.beta; p.ppd = g.ppd; p.acc_words = g.acc_words;
     p.eoff = g.eoff;
     p.bn = tc::BN;
@@ -557,6 +583,7 @@ cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t st) {
     p.cnt = g.cnt;
     p.defer = 1;
     tc::Sched sc;
+    memset(&sc, 0, sizeof(sc));
     sc.probs = nullptr;
     sc.maps = nullptr;
     sc.items = (const tc::WorkItem*)g.sched_items;
@@ -566,6 +593,10 @@ cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t st) {
     sc.nitems = g.sched_nitems;
     sc.wait_limit = g.wait_limit;
     sc.inject_stall = g.inject_stall;
+    sc.step_done = (sc.counter && g.lock_w > 0) ? g.step_done : nullptr;
+    sc.retired = g.retired;
+    sc.lock_w = g.lock_w;
+    sc.lock_n = g.lock_n;
     if (sc.items && g.split_bytes) {
         // split limbs, chunk counters and the feed counter are one region
         e = cudaMemsetAsync(g.sacc ? (void*)g.sacc : (void*)g.cnt_region, 0, g.split_bytes, st);

@@ -171,6 +171,26 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                  : "memory");
 }
 
+// binary16 digits: one MMA of K = 16 reads the same 32 bytes of a row as an
+// e4m3 MMA of K = 32, and the instruction descriptor has the same bits
+// (D = f32, A = B = f16 are type code 0 of kind::f16)
+__device__ __forceinline__ void mma_f16_tc(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_f16_tc_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                                uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // pair form: M = 256 over the two CTAs (A rows 0..127 from the leader's
 // shared memory, 128..255 from the peer's; B columns split the same way),
 // each CTA's tensor memory holding its 128 rows of D
@@ -231,10 +251,10 @@ struct Walk {
 // `zero` skips the loads (first and last drain of a tile coincide).  The
 // limbs are streamed through one carry chain into a two's complement value
 // of 64 NW bits, rounded canonically into C(i, j) (or written to T in the
-// diagnostic mode).
+// diagnostic mode).  Returns the first component written (0 otherwise).
 template <int NW>
-__device__ __forceinline__ void finish_element(const GemmArgs& g, int nl, const int64_t* base, size_t lstride,
-                                               size_t idx, int64_t i, int64_t j, int64_t x, int li, bool zero) {
+__device__ __forceinline__ double finish_element(const GemmArgs& g, int nl, const int64_t* base, size_t lstride,
+                                                 size_t idx, int64_t i, int64_t j, int64_t x, int li, bool zero) {
     uint64_t w[NW];
 #pragma unroll
     for (int x2 = 0; x2 < NW; ++x2) w[x2] = 0;
@@ -247,24 +267,32 @@ __device__ __forceinline__ void finish_element(const GemmArgs& g, int nl, const 
         w[l >> 2] |= ((uint64_t)t & 0xffffull) << (16 * (l & 3));
         carry = t >> 16;                           // arithmetic shift: floor division
     }
-    if (i >= g.m || j >= g.n) return;
+    if (i >= g.m || j >= g.n) return 0.0;
     if (g.d_only) {
         g.T[i + j * g.m] = (int64_t)w[0];
-        return;
+        return 0.0;
     }
     const int Ei = g.E[i], Fj = g.F[j];
     const bool nz = (Ei != OZMP_EXP_ZERO && Fj != OZMP_EXP_ZERO);
     const int U = nz ? Ei + Fj + g.eoff - g.beta * (g.s + 1) : 0;
     const size_t at = (size_t)(i + j * g.ldc);
     bool ok = true;
+    double c0 = 0.0;
     if (g.is_f32) {
-        if (nz) ok = canonical_round_put<NW, float>(w, U, g.q, [&](int c, float v) { ((float*)g.C[c])[at] = v; });
+        if (nz) ok = canonical_round_put<NW, float>(w, U, g.q, [&](int c, float v) {
+            ((float*)g.C[c])[at] = v;
+            if (c == 0) c0 = (double)v;
+        });
         else for (int c = 0; c < g.q; ++c) ((float*)g.C[c])[at] = 0.f;
     } else {
-        if (nz) ok = canonical_round_put<NW, double>(w, U, g.q, [&](int c, double v) { ((double*)g.C[c])[at] = v; });
+        if (nz) ok = canonical_round_put<NW, double>(w, U, g.q, [&](int c, double v) {
+            ((double*)g.C[c])[at] = v;
+            if (c == 0) c0 = v;
+        });
         else for (int c = 0; c < g.q; ++c) ((double*)g.C[c])[at] = 0.0;
     }
     if (!ok) atomicOr(g.status, ST_RANGE);
+    return c0;
 }
 
 __device__ __forceinline__ void finish_dispatch(const GemmArgs& g, int nl, const int64_t* base, size_t lstride,
@@ -294,6 +322,7 @@ struct Prob {
     int64_t m, n, mp, np, kp, ldc;
     int q, is_f32, s, beta, ppd, acc_words, bn, d_only;
     int eoff;              // exponent offset of the digit weights (2: balanced digits)
+    int kind;              // 0: e4m3 digits (kind::f8f6f4); 1: binary16 digits (kind::f16); kp counts bytes
     int defer;             // 1: the limbs are rounded into C by a separate pass after the launch
 };
 
@@ -335,7 +364,17 @@ struct Sched {
     int nitems;                //   (zeroed before the launch) instead of the per-CTA lists
     long long wait_limit;      // polls before a wait gives up (0: WAIT_LIMIT)
     int inject_stall;          // test hook: never load the first stage of each CTA's first item
+    // loose lockstep of the clusters' pair walks (null: off): step_done[P]
+    // counts the clusters that issued their P-th whole-tile pair, retired the
+    // clusters without whole tiles left; before pair P a leader waits a
+    // bounded time until step_done[P - lock_w] + retired covers every cluster
+    int* step_done;
+    int* retired;
+    int lock_w, lock_n;
 };
+
+// polls of one lockstep wait before the producer goes on regardless
+constexpr int LOCK_POLLS = 160;
 
 // Dynamic item feed: the leader's producer takes the next item index from the
 // global counter and publishes it through a ring of RING slots (in both CTAs

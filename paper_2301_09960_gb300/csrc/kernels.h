@@ -3,6 +3,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include "../../include/ozmp.h"
+#include "bound.cuh"
 
 namespace ozmp {
 
@@ -63,6 +64,15 @@ struct GemmArgs {
     int sched_nitems;
     size_t split_bytes;        // bytes of sacc + cnt + counter
     int tc_cg;                 // 2: CTA-pair tiles (256 x 256, cta_group::2); else one CTA per tile
+    // loose lockstep of the clusters' pair walks (lock_w > 0, dynamic feed):
+    // step counters and the retired count, zeroed with the split region
+    int* step_done;
+    int* retired;
+    int lock_w, lock_n;
+    // the a-posteriori bound check run by the tcgen05 rounding pass (null: none)
+    BoundStats* chk;
+    BoundForm chk_form;
+    uint32_t chk_flag;
 };
 
 // Tile schedule of one tcgen05 problem (host): whole tiles in full waves over
@@ -82,6 +92,11 @@ cudaError_t launch_split(const SplitArgs& a, cudaStream_t st);
 // the two passes of launch_split: exponents E, F (all column exponents
 // included), then the digits for the plan's slice count
 cudaError_t launch_split_exponents(const SplitArgs& a, cudaStream_t st);
+// the exponent pass together with the unscaled squared norms, colA[p] =
+// sum_i a_ip^2 and rowB[p] = sum_j b_pj^2 (each element the binary64 sum of
+// its components; both zeroed by the caller); cudaErrorNotSupported for the
+// many-component splitter
+cudaError_t launch_split_exponents_norm(const SplitArgs& a, double* colA, double* rowB, cudaStream_t st);
 cudaError_t launch_split_digits(const SplitArgs& a, cudaStream_t st);
 cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t st);
 

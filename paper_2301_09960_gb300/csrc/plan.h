@@ -54,7 +54,10 @@ struct ozmp_plan_s {
     size_t ws_cap;     // bytes of the current workspace
     // schedule knobs, read from the environment once (OZMP_TC_PAIR, OZMP_TC_DYNAMIC,
     // OZMP_TC_GROUP, OZMP_TC_MAX_CHUNKS) and kept when the plan is re-made for another s
-    int env_read, env_pair_off, env_static, env_group, env_maxc;
+    int env_read, env_pair_off, env_static, env_group, env_maxc, env_lock;
+    // adaptive plans: pinned host word of the chosen s and the event after its copy
+    int* host_s;
+    cudaEvent_t ev_s;
 };
 
 namespace ozmp_batch {
@@ -102,6 +105,23 @@ inline int beta_fp64(int64_t k) {
     return b;
 }
 
+// Largest beta <= 11 with k (2^beta - 1)^2 <= 2^24: a binary32 sum of k
+// digit products never rounds, and the digits are exact in binary16
+// (integers up to 2048); 0 when even beta = 1 does not fit (k > 2^24).
+inline int beta_fp16(int64_t k) {
+    if (k <= 0) k = 1;
+    int b = 0;
+    while (b < 11) {
+        const int64_t d = ((int64_t)1 << (b + 1)) - 1;
+        if ((unsigned __int128)k * d * d <= ((unsigned __int128)1 << 24)) ++b;
+        else break;
+    }
+    return b;
+}
+
+// the tcgen05 engine (carry-save limbs, tile schedule): e4m3 and binary16 digits
+inline bool tc_engine(int form) { return form == OZMP_FORM_FP8 || form == OZMP_FORM_FP16; }
+
 inline int bitlen128(unsigned __int128 x) {
     int b = 0;
     while (x) { ++b; x >>= 1; }
@@ -112,7 +132,7 @@ inline ozmp_status fill_schedule(ozmp_plan_s* p) {
     // largest digit magnitude and the exact-accumulation limit of the engine
     const bool e4m3 = (p->form == OZMP_FORM_FP8 || p->form == OZMP_FORM_FP8_MMA);
     uint64_t dmax = p->bal ? 16u : e4m3 ? 15u : ((1u << p->beta) - 1u);
-    unsigned __int128 limit = e4m3 ? ((unsigned __int128)1 << 24)
+    unsigned __int128 limit = (e4m3 || p->form == OZMP_FORM_FP16) ? ((unsigned __int128)1 << 24)
                             : (p->form == OZMP_FORM_INT8) ? (unsigned __int128)2147483647u
                             : ((unsigned __int128)1 << 53);
     int64_t kk = p->k > 0 ? p->k : 1;
@@ -156,7 +176,7 @@ inline ozmp_status fill_schedule(ozmp_plan_s* p) {
     int bits = maxbits + ceil_log2(p->s + 1) + 2;   // sum of s terms, sign bit
     p->acc_words = (bits + 63) / 64;
     if (p->acc_words < 2) p->acc_words = 2;
-    if (p->acc_words > (p->form == OZMP_FORM_FP8 ? 16 : 7)) return OZMP_ERR_UNSUPPORTED;
+    if (p->acc_words > (tc_engine(p->form) ? 16 : 7)) return OZMP_ERR_UNSUPPORTED;
     p->nlimbs = 4 * p->acc_words + 1;
     return OZMP_OK;
 }
@@ -173,7 +193,7 @@ inline void fill_layout(ozmp_plan_s* p) {
     p->off_Adig = off; off = align256(off + (size_t)p->s * p->mp * p->kp * p->db);
     p->off_Bdig = off; off = align256(off + (size_t)p->s * p->np * p->kp * p->db);
     p->off_acc = off;
-    if (p->form == OZMP_FORM_FP8) off = align256(off + (size_t)p->nlimbs * p->mp * p->np * 8);
+    if (tc_engine(p->form)) off = align256(off + (size_t)p->nlimbs * p->mp * p->np * 8);
     else if (p->ngroups > 1) off = align256(off + (size_t)p->acc_words * p->mp * p->np * 8);
     p->ws_bytes = off;
 }
@@ -257,7 +277,7 @@ inline GemmArgs gemm_args(ozmp_plan_s* p) {
     g.s = p->s; g.beta = p->beta; g.ppd = p->ppd; g.group_start = p->group_start;
     g.eoff = p->bal ? 2 : 0;
     g.acc_words = p->acc_words; g.ngroups = p->ngroups;
-    g.acc = (p->ngroups > 1 || p->form == OZMP_FORM_FP8) ? (int64_t*)(w + p->off_acc) : nullptr;
+    g.acc = (p->ngroups > 1 || tc_engine(p->form)) ? (int64_t*)(w + p->off_acc) : nullptr;
     g.status = (uint32_t*)(w + p->off_status);
     if (p->sched_host) {
         g.sched_items = w + p->off_items;
@@ -267,6 +287,12 @@ inline GemmArgs gemm_args(ozmp_plan_s* p) {
         int* cnt = (int*)(w + p->off_sacc + (size_t)p->sched_slots * p->nlimbs * 256 * 128 * 8);
         g.cnt = p->sched_slots ? cnt : nullptr;
         g.counter = p->tc_dyn ? cnt + p->sched_slots : nullptr;
+        if (p->env_lock > 0 && p->tc_dyn) {
+            g.retired = cnt + p->sched_slots + 1;
+            g.step_done = g.retired + 1;
+            g.lock_w = p->env_lock;
+            g.lock_n = p->sched_ntiles * (p->s * (p->s + 1) / 2);
+        }
         g.cnt_region = cnt;
         g.tile_slot = (const int*)(w + p->off_tslot);
         g.sched_nitems = p->sched_items;
@@ -295,16 +321,21 @@ inline void take_timing(ozmp_plan_s* p, GemmArgs& g) {
 // The items are taken from a counter in list order (OZMP_TC_DYNAMIC=0: fixed
 // per-CTA lists).
 inline ozmp_status plan_schedule(ozmp_plan_s* p) {
-    if (p->form != OZMP_FORM_FP8 || p->m == 0 || p->n == 0 || p->k == 0) return OZMP_OK;
+    if (!tc_engine(p->form) || p->m == 0 || p->n == 0 || p->k == 0) return OZMP_OK;
     if (!p->env_read) {
         const char* env = getenv("OZMP_TC_PAIR");
         p->env_pair_off = (env && env[0] == '0') ? 1 : 0;
         const char* dyn = getenv("OZMP_TC_DYNAMIC");
         p->env_static = (dyn && dyn[0] == '0') ? 1 : 0;
+        // defaults: bands of 8 row tiles, walked in a loose lockstep of one pair
+        // (at QD 8192^2 x 16384, where the operand panels no longer stay in L2,
+        // 945 -> 831 ms; DD 4096^3 unchanged)
         const char* grp = getenv("OZMP_TC_GROUP");
-        p->env_group = grp ? atoi(grp) : 0;
+        p->env_group = grp ? atoi(grp) : 8;
         const char* mxc = getenv("OZMP_TC_MAX_CHUNKS");
         p->env_maxc = mxc ? atoi(mxc) : 0;
+        const char* lk = getenv("OZMP_TC_LOCKSTEP");
+        p->env_lock = lk ? atoi(lk) : 1;
         // test hooks of the bounded waits: a smaller poll limit, and a stage
         // whose copies are never issued so that the waits on it run out
         const char* wl = getenv("OZMP_TC_WAIT_LIMIT");
@@ -340,8 +371,12 @@ inline ozmp_status plan_schedule(ozmp_plan_s* p) {
     p->off_soff = o; o = align256(o + (size_t)(p->sched_grid + 1) * 4);
     p->off_tslot = o; o = align256(o + (size_t)ntiles * 4);
     p->off_sacc = o;
-    // split limbs, their chunk counters and the item-feed counter, zeroed before each launch
-    p->split_bytes = (size_t)p->sched_slots * p->nlimbs * 256 * 128 * 8 + (size_t)p->sched_slots * 4 + 4;
+    // split limbs, their chunk counters, the item-feed counter and (lockstep)
+    // the retired count and one step counter per whole-tile pair a cluster can
+    // walk, zeroed before each launch
+    const size_t lock_n = (p->env_lock > 0 && p->tc_dyn) ? (size_t)ntiles * pairs : 0;
+    p->split_bytes = (size_t)p->sched_slots * p->nlimbs * 256 * 128 * 8 + (size_t)p->sched_slots * 4 + 4 +
+                     (lock_n ? 4 + 4 * lock_n : 0);
     o = align256(o + p->split_bytes);
     p->ws_bytes = o;
     return OZMP_OK;
@@ -387,7 +422,7 @@ inline ozmp_status plan_init(ozmp_plan_s* p, int prec, int64_t m, int64_t n, int
     }
     int q = prec_q(prec);
     if (!q || m < 0 || n < 0 || k < 0 || nslices < 0 || nslices > OZMP_MAX_SLICES) return OZMP_ERR_INVALID_ARG;
-    if (form < OZMP_FORM_AUTO || form > OZMP_FORM_FP8_BAL) return OZMP_ERR_INVALID_ARG;
+    if (form < OZMP_FORM_AUTO || form > OZMP_FORM_FP16) return OZMP_ERR_INVALID_ARG;
     p->prec = prec;
     p->q = q;
     p->is_f32 = (prec == OZMP_TS);
@@ -398,8 +433,10 @@ inline ozmp_status plan_init(ozmp_plan_s* p, int prec, int64_t m, int64_t n, int
     p->form = (form == OZMP_FORM_AUTO || p->bal) ? OZMP_FORM_FP8 : form;
     p->m = m; p->n = n; p->k = k;
     p->beta = (p->form == OZMP_FORM_FP64) ? beta_fp64(k)
+            : (p->form == OZMP_FORM_FP16) ? beta_fp16(k)
             : (p->form == OZMP_FORM_INT8 ? 7 : (p->bal ? 5 : 4));
-    p->db = (p->form == OZMP_FORM_FP64) ? 8 : 1;
+    if (p->beta < 1) return OZMP_ERR_UNSUPPORTED;
+    p->db = (p->form == OZMP_FORM_FP64) ? 8 : (p->form == OZMP_FORM_FP16 ? 2 : 1);
     // slice limits: the register-resident splitters hold 4 components,
     // windows of beta s + 65 bits in 7 words (binary64 digits: beta s <= 376)
     // or 6 words (1-byte digits), and write at most 64 e4m3 slices (63
@@ -422,7 +459,7 @@ inline ozmp_status plan_init(ozmp_plan_s* p, int prec, int64_t m, int64_t n, int
     p->big = (q > 4 || nslices > (p->bal ? 63 : 64)) ? 1 : 0;
     if (p->big && p->is_f32) return OZMP_ERR_UNSUPPORTED;   // the many-component splitter reads binary64
     p->mp = roundup(m, 128);
-    p->np = roundup(n, p->form == OZMP_FORM_FP8 ? 256 : 128);
+    p->np = roundup(n, tc_engine(p->form) ? 256 : 128);
     p->kp = roundup(k, 128);
     ozmp_status st = fill_schedule(p);
     if (st != OZMP_OK) return st;

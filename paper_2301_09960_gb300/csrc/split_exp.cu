@@ -7,6 +7,7 @@ cudaError_t launch_digits_fp8(const SplitArgs& g, cudaStream_t st);
 cudaError_t launch_digits_fp8bal(const SplitArgs& g, cudaStream_t st);
 cudaError_t launch_digits_int8(const SplitArgs& g, cudaStream_t st);
 cudaError_t launch_digits_fp64(const SplitArgs& g, cudaStream_t st);
+cudaError_t launch_digits_fp16(const SplitArgs& g, cudaStream_t st);
 cudaError_t launch_exponents_big(const SplitArgs& g, cudaStream_t st);
 cudaError_t launch_digits_big(const SplitArgs& g, cudaStream_t st);
 
@@ -52,12 +53,37 @@ static cudaError_t exponents(const SplitArgs& g, cudaStream_t st, bool all_cols)
 cudaError_t launch_split_digits(const SplitArgs& g, cudaStream_t st) {
     if (g.big) return launch_digits_big(g, st);
     if (g.form == OZMP_FORM_FP64) return launch_digits_fp64(g, st);
+    if (g.form == OZMP_FORM_FP16) return launch_digits_fp16(g, st);
     if (g.form == OZMP_FORM_INT8) return launch_digits_int8(g, st);
     if (g.bal) return launch_digits_fp8bal(g, st);
     return launch_digits_fp8(g, st);   // FORM_FP8 and FORM_FP8_MMA share the e4m3 digits
 }
 
 cudaError_t launch_split_exponents(const SplitArgs& g, cudaStream_t st) { return exponents(g, st, true); }
+
+template <typename T, int Q>
+static cudaError_t exponents_norm_impl(const SplitArgs& g, double* colA, double* rowB, cudaStream_t st) {
+    Operand<T> a = make_op<T>(g.A, g.q, g.lda);
+    Operand<T> b = make_op<T>(g.B, g.q, g.ldb);
+    init_exponents(g, st);
+    if (g.m > 0 && g.k > 0) {
+        dim3 gr((unsigned)((g.m + 255) / 256), (unsigned)((g.k + 15) / 16));
+        k_exp_rows_norm<T, Q><<<gr, 256, 0, st>>>(a, g.m, g.k, g.E, g.status, colA);
+    }
+    if (g.n > 0 && g.k > 0) {
+        dim3 gr((unsigned)((g.k + 255) / 256), (unsigned)((g.n + 63) / 64));
+        k_exp_cols_norm<T, Q><<<gr, 256, 0, st>>>(b, g.k, g.n, g.F, g.status, rowB);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_exponents_norm(const SplitArgs& g, double* colA, double* rowB, cudaStream_t st) {
+    if (g.big) return cudaErrorNotSupported;   // the caller takes the exponents and the norms separately
+    return g.is_f32     ? exponents_norm_impl<float, 3>(g, colA, rowB, st)
+           : g.q == 2   ? exponents_norm_impl<double, 2>(g, colA, rowB, st)
+           : g.q == 3   ? exponents_norm_impl<double, 3>(g, colA, rowB, st)
+                        : exponents_norm_impl<double, 4>(g, colA, rowB, st);
+}
 
 cudaError_t launch_split(const SplitArgs& g, cudaStream_t st) {
     cudaError_t e = exponents(g, st, false);

@@ -147,6 +147,123 @@ __global__ void __launch_bounds__(256) k_exp_cols(Operand<T> b, int64_t k, int64
 }
 
 // ---------------------------------------------------------------------------
+// K1 with the statistics of the data-dependent slice count (bound.cuh): the
+// same exponents, and beside them the squared norms of the elements (their
+// components summed in binary64: an estimate, which unnormalised components
+// that cancel do not mislead), unscaled (the caller falls back to scaled
+// norms when the exponents leave the range where no square or product of
+// squares can overflow or vanish): colA[p] += sum_i a_ip^2 over the block's
+// rows, rowB[p] += sum_j b_pj^2 over the block's columns (both zeroed before).
+__device__ __forceinline__ int xmax_warp(int v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// 16 per-lane values v[c] (c = column) summed over the 32 lanes of a warp by
+// recursive halving: each step hands half of the columns to the partner lane;
+// at the end lanes 2c and 2c + 1 hold the sum of column c (16 shuffle steps
+// per warp instead of a 5-step reduction per column)
+__device__ __forceinline__ double xsum16_warp(double (&v)[16]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;   // this lane keeps the upper half of the columns
+#pragma unroll
+        for (int c = 0; c < h; ++c) {
+            const double give = up ? v[c] : v[c + h];
+            const double got = __shfl_xor_sync(0xffffffffu, give, o);
+            v[c] = (up ? v[c + h] : v[c]) + got;
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// rows of A: one thread per row, KC = 16 columns per block row (as
+// k_exp_rows); a thread keeps its 16 squares in registers, the warp sums them
+// by recursive halving, the block in shared memory, then one global atomic
+// per block and column
+template <typename T, int Q>
+__global__ void __launch_bounds__(256) k_exp_rows_norm(Operand<T> a, int64_t m, int64_t k, int32_t* E,
+                                                       uint32_t* status, double* colA) {
+    constexpr int KC = 16, U = 4;
+    __shared__ double sc[KC];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in = i < m;
+    const int64_t p0 = (int64_t)blockIdx.y * KC;
+    const int64_t p1 = p0 + KC < k ? p0 + KC : k;
+    if (threadIdx.x < KC) sc[threadIdx.x] = 0.0;
+    __syncthreads();
+    int emax = OZMP_EXP_ZERO;
+    bool ok = true;
+    double sq[KC];
+#pragma unroll
+    for (int g = 0; g < KC / U; ++g) {
+        const int64_t p = p0 + g * U;
+        T v[U][4];
+#pragma unroll
+        for (int u = 0; u < U; ++u) load_raw<T>(a, Q, in && p + u < p1, i + (p + u) * a.ld, v[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            int e;
+            ok &= exponent_loaded<T>(v[u], Q, e);   // zeros outside the matrix: no exponent
+            emax = e > emax ? e : emax;
+            double x = 0.0;
+#pragma unroll
+            for (int c = 0; c < Q; ++c) x += (double)v[u][c];
+            sq[g * U + u] = x * x;
+        }
+    }
+    const double w = xsum16_warp(sq);
+    const int lane = threadIdx.x & 31;
+    if ((lane & 1) == 0 && (lane >> 1) < p1 - p0) atomicAdd(&sc[lane >> 1], w);
+    __syncthreads();
+    if (threadIdx.x < p1 - p0) atomicAdd(&colA[p0 + threadIdx.x], sc[threadIdx.x]);
+    if (in && emax != OZMP_EXP_ZERO) atomicMax(&E[i], emax);
+    if (!ok) atomicOr(status, ST_NONFINITE);
+}
+
+// columns of B: one thread per row p (coalesced along the column), JB
+// columns per block; a column's exponent is reduced over the warp and the
+// block (one global atomicMax per block and column), a row's squares are
+// summed in the thread (one global atomicAdd per thread)
+template <typename T, int Q>
+__global__ void __launch_bounds__(256) k_exp_cols_norm(Operand<T> b, int64_t k, int64_t n, int32_t* F,
+                                                       uint32_t* status, double* rowB) {
+    constexpr int JB = 64, U = 4;
+    __shared__ int sf[JB];
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in = p < k;
+    const int64_t j0 = (int64_t)blockIdx.y * JB;
+    const int64_t j1 = j0 + JB < n ? j0 + JB : n;
+    if (threadIdx.x < JB) sf[threadIdx.x] = OZMP_EXP_ZERO;
+    __syncthreads();
+    double acc = 0.0;
+    bool ok = true;
+    for (int64_t j = j0; j < j1; j += U) {
+        T v[U][4];
+#pragma unroll
+        for (int u = 0; u < U; ++u) load_raw<T>(b, Q, in && j + u < j1, p + (j + u) * b.ld, v[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (j + u >= j1) break;   // uniform over the block
+            int e;
+            ok &= exponent_loaded<T>(v[u], Q, e);
+            const int w = xmax_warp(e);
+            if ((threadIdx.x & 31) == 0 && w != OZMP_EXP_ZERO) atomicMax(&sf[j + u - j0], w);
+            double x = 0.0;
+#pragma unroll
+            for (int c = 0; c < Q; ++c) x += (double)v[u][c];
+            acc += x * x;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < j1 - j0 && sf[threadIdx.x] != OZMP_EXP_ZERO) atomicMax(&F[j0 + threadIdx.x], sf[threadIdx.x]);
+    if (in && acc != 0.0) atomicAdd(&rowB[p], acc);
+    if (!ok) atomicOr(status, ST_NONFINITE);
+}
+
+// ---------------------------------------------------------------------------
 // K2: digits
 // ---------------------------------------------------------------------------
 // encodings: FORM_INT8 -> two's complement int8, FORM_FP8 -> e4m3,
@@ -615,11 +732,19 @@ __global__ void __launch_bounds__(256, 3) k_split_cols_fused(Operand<T> b, int64
 }
 
 // binary64 digits, rows of A: 16 x 16 tile staged in shared memory
-template <typename T, int NW>
+// a digit (an integer of at most 26 bits) in the stored type: binary64, or
+// binary16 for the binary16-digit form (|d| <= 2047 there: exact)
+template <typename DT>
+__device__ __forceinline__ DT digit_value(double d) { return (DT)d; }
+template <>
+__device__ __forceinline__ __half digit_value<__half>(double d) { return __double2half(d); }
+
+template <typename T, int NW, typename DT = double>
 __global__ void __launch_bounds__(256) k_split_rows_f64(Operand<T> a, int64_t m, int64_t k, const int32_t* E,
-                                                        double* dig, int64_t mp, int64_t kp, int s, int beta) {
+                                                        DT* dig, int64_t mp, int64_t kp, int s, int beta) {
     constexpr int TI = 16, TP = 16;
-    extern __shared__ __align__(16) double sd[];    // [s][TI][TP]
+    extern __shared__ __align__(16) unsigned char sd_raw[];
+    DT* sd = reinterpret_cast<DT*>(sd_raw);         // [s][TI][TP]
     const int64_t i0 = (int64_t)blockIdx.x * TI, p0 = (int64_t)blockIdx.y * TP;
     const int ri = threadIdx.x % TI, pi = threadIdx.x / TI;
     const int64_t i = i0 + ri, p = p0 + pi;
@@ -628,7 +753,7 @@ __global__ void __launch_bounds__(256) k_split_rows_f64(Operand<T> a, int64_t m,
     const int sign = window_of<T, NW>(a, i < m && p < k, i + p * a.ld, Erow, w);
     for (int t = 1; t <= s; ++t) {
         const double d = (double)digit_of_rt<NW>(w, t, beta);
-        sd[((t - 1) * TI + ri) * TP + pi] = sign < 0 ? -d : d;
+        sd[((t - 1) * TI + ri) * TP + pi] = digit_value<DT>(sign < 0 ? -d : d);
     }
     __syncthreads();
     const int total = s * TI * TP;
@@ -639,9 +764,9 @@ __global__ void __launch_bounds__(256) k_split_rows_f64(Operand<T> a, int64_t m,
 }
 
 // binary64 digits, columns of B: one element per thread
-template <typename T, int NW>
+template <typename T, int NW, typename DT = double>
 __global__ void __launch_bounds__(256) k_split_cols_f64(Operand<T> b, int64_t k, int64_t n, const int32_t* F,
-                                                        double* dig, int64_t np, int64_t kp, int s, int beta) {
+                                                        DT* dig, int64_t np, int64_t kp, int s, int beta) {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= kp * np) return;
     const int64_t j = g / kp, p = g % kp;
@@ -650,7 +775,7 @@ __global__ void __launch_bounds__(256) k_split_cols_f64(Operand<T> b, int64_t k,
     const int sign = window_of<T, NW>(b, j < n && p < k, p + j * b.ld, Ecol, w);
     for (int t = 1; t <= s; ++t) {
         const double d = (double)digit_of_rt<NW>(w, t, beta);
-        dig[((size_t)(t - 1) * np + j) * kp + p] = sign < 0 ? -d : d;
+        dig[((size_t)(t - 1) * np + j) * kp + p] = digit_value<DT>(sign < 0 ? -d : d);
     }
 }
 
@@ -729,19 +854,21 @@ static cudaError_t digits_b1(const SplitArgs& g, cudaStream_t st) {
     }
 }
 
-template <typename T, int NW>
+// general-beta digits as binary64 (DT = double) or binary16 (DT = __half)
+// values: the same exact windows, one element per thread
+template <typename T, int NW, typename DT = double>
 static cudaError_t digits_f64(const SplitArgs& g, cudaStream_t st) {
     Operand<T> a = make_op<T>(g.A, g.q, g.lda);
     Operand<T> b = make_op<T>(g.B, g.q, g.ldb);
     dim3 gr((unsigned)(g.mp / 16), (unsigned)(g.kp / 16));
-    size_t sm = (size_t)g.s * 16 * 16 * 8;
-    auto kr = k_split_rows_f64<T, NW>;
+    size_t sm = (size_t)g.s * 16 * 16 * sizeof(DT);
+    auto kr = k_split_rows_f64<T, NW, DT>;
     cudaError_t e = cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    kr<<<gr, 256, sm, st>>>(a, g.m, g.k, g.E, (double*)g.Adig, g.mp, g.kp, g.s, g.beta);
+    kr<<<gr, 256, sm, st>>>(a, g.m, g.k, g.E, (DT*)g.Adig, g.mp, g.kp, g.s, g.beta);
     int64_t tot = g.kp * g.np;
-    k_split_cols_f64<T, NW><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(b, g.k, g.n, g.F, (double*)g.Bdig,
-                                                                          g.np, g.kp, g.s, g.beta);
+    k_split_cols_f64<T, NW, DT><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(b, g.k, g.n, g.F, (DT*)g.Bdig,
+                                                                              g.np, g.kp, g.s, g.beta);
     return cudaGetLastError();
 }
 
@@ -752,6 +879,9 @@ static cudaError_t digits_impl(const SplitArgs& g, cudaStream_t st) {
     if constexpr (FORM == OZMP_FORM_FP64) {
         if (nw <= 4) return digits_f64<T, 4>(g, st);
         return digits_f64<T, 7>(g, st);
+    } else if constexpr (FORM == OZMP_FORM_FP16) {
+        if (nw <= 4) return digits_f64<T, 4, __half>(g, st);
+        return digits_f64<T, 7, __half>(g, st);
     } else {
         if (nw <= 4) return digits_b1<T, FORM, 4>(g, st);
         return digits_b1<T, FORM, 6>(g, st);

@@ -15,6 +15,10 @@ def digits_to_int(arr, form):
         v = arr.astype(np.float64)
         assert np.all(v == np.round(v))
         return v.astype(np.int64)
+    if form == "fp16":
+        v = arr.astype(np.float16).astype(np.float64)
+        assert np.all(v == np.round(v))
+        return v.astype(np.int64)
     if form == "int8":
         return arr.astype(np.uint8).view(np.int8).astype(np.int64)
     assert form in ("fp8", "fp8mma", "fp8bal")

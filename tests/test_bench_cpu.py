@@ -36,18 +36,32 @@ class _Col:
 
 
 @pytest.mark.parametrize("form,k,ld,ptr,q,want", [
-    (oz.Form.FP8_BAL, 4096, 4096, 256, 2, 6),   # aligned DD columns: one pass over B
-    (oz.Form.FP8_BAL, 4095, 4095, 256, 2, 7),   # k * 8 not a multiple of 16: two kernels
-    (oz.Form.FP8_BAL, 4096, 4097, 256, 2, 7),   # leading dimension unaligned
-    (oz.Form.FP8_BAL, 4096, 4096, 264, 2, 7),   # base not 16-byte aligned
-    (oz.Form.FP8_BAL, 7168, 7168, 256, 2, 6),   # 112 KB a column: still one pass
-    (oz.Form.FP8_BAL, 7170, 7170, 256, 2, 7),   # past 112 KB
-    (oz.Form.FP8, 4096, 4096, 256, 4, 7),       # QD: 128 KB a column
-    (oz.Form.FP8_MMA, 4096, 4096, 256, 2, 5),   # mma.sync engine: no rounding pass
-    (oz.Form.INT8, 4096, 4096, 256, 2, 6),      # int8 digits: two kernels for B, no rounding pass
-    (oz.Form.FP64, 4096, 4096, 256, 2, 6),
+    (oz.Form.FP8_BAL, 4096, 4096, 256, 2, 7),   # aligned DD columns: one pass over B
+    (oz.Form.FP8_BAL, 4095, 4095, 256, 2, 8),   # k * 8 not a multiple of 16: two kernels
+    (oz.Form.FP8_BAL, 4096, 4097, 256, 2, 8),   # leading dimension unaligned
+    (oz.Form.FP8_BAL, 4096, 4096, 264, 2, 8),   # base not 16-byte aligned
+    (oz.Form.FP8_BAL, 7168, 7168, 256, 2, 7),   # 112 KB a column: still one pass
+    (oz.Form.FP8_BAL, 7170, 7170, 256, 2, 8),   # past 112 KB
+    (oz.Form.FP8, 4096, 4096, 256, 4, 8),       # QD: 128 KB a column
+    (oz.Form.FP16, 4096, 4096, 256, 2, 8),      # binary16 digits: two kernels for B, rounding pass
+    (oz.Form.FP8_MMA, 4096, 4096, 256, 2, 7),   # mma.sync engine: no rounding pass, a check pass
+    (oz.Form.INT8, 4096, 4096, 256, 2, 8),      # int8 digits: two kernels for B, a check pass
+    (oz.Form.FP64, 4096, 4096, 256, 2, 8),
 ])
-def test_launches_per_step_follow_the_library_rule(form, k, ld, ptr, q, want):
+def test_launches_per_step_with_a_fixed_slice_count(form, k, ld, ptr, q, want):
+    # exponent init, row exponents, (column exponents,) row and column
+    # digits, the check's exponent statistics, the product, then the rounding
+    # pass (tcgen05, which runs the check) or the check pass
     info = types.SimpleNamespace(form=form)
     Bd = [_Col(ld, ptr + c * 1024 * 1024) for c in range(q)]
-    assert bench.launches_per_step(oz, info, Bd, k, 8) == want
+    assert bench.launches_per_step(oz, info, Bd, k, 8, adaptive=False) == want
+
+
+@pytest.mark.parametrize("form", [oz.Form.FP8_BAL, oz.Form.FP8, oz.Form.FP16, oz.Form.FP8_MMA, oz.Form.INT8,
+                                  oz.Form.FP64])
+def test_launches_per_step_with_the_data_dependent_count(form):
+    # exponent init, the two exponent passes with the norms, the choice, row
+    # and column digits, the product, the rounding or the check pass: 8
+    info = types.SimpleNamespace(form=form)
+    Bd = [_Col(4096, 256 + c * 1024 * 1024) for c in range(2)]
+    assert bench.launches_per_step(oz, info, Bd, 4096, 8) == 8

@@ -170,7 +170,7 @@ def test_balanced_digit_limits():
     h = oz.ozmp_plan_create(oz.Prec.DD, 8, 8, 65536, oz.Form.FP8_BAL, 0, None)
     oz.ozmp_plan_destroy(h)
     with pytest.raises(oz.OzmpError) as e:
-        oz.ozmp_plan_create(oz.Prec.DD, 8, 8, 8, 6, 0, None)
+        oz.ozmp_plan_create(oz.Prec.DD, 8, 8, 8, 7, 0, None)
     assert e.value.status == oz.Status.ERR_INVALID_ARG
 
 
@@ -196,3 +196,37 @@ def test_triple_single_slice_limits():
         with pytest.raises(oz.OzmpError) as e:
             oz.ozmp_plan_create(oz.Prec.TS, 10, 10, 10, form, s, None)
         assert e.value.status == oz.Status.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 128, 1000, 2048, 4096, 8192, 16384, 2 ** 24])
+@pytest.mark.parametrize("prec", [oz.Prec.DD, oz.Prec.QD, oz.Prec.TS])
+def test_binary16_digit_plans(prec, k):
+    # the binary32-slice form: beta is the largest width with k (2^beta - 1)^2
+    # <= 2^24 (the oracle's beta_fp32, the paper's S = 24), held in binary16,
+    # so at most 11 bits; two-byte digits; a drain holds 2^24 / (k (2^beta - 1)^2)
+    # pairs; the fixed slice count covers the target bits + log2 k + 16 where
+    # the splitter's limits allow
+    h = oz.ozmp_plan_create(prec, 300, 200, k, oz.Form.FP16, 0, None)
+    try:
+        i = oz.ozmp_plan_get_info(h)
+        beta = min(11, O.beta_fp32(k))
+        assert i.form == oz.Form.FP16 and i.beta == beta and i.digit_bytes == 2
+        assert i.pairs_per_drain == min(2 ** 24 // (k * (2 ** beta - 1) ** 2), 2 ** 20)
+        bits = (66 if prec == oz.Prec.TS else 50 * int(prec)) + max(0, (k - 1).bit_length()) + 16
+        # (at most 64 slices of at most 376 bits in all: the register splitter's limits)
+        assert beta * i.nslices >= min(bits, beta * min(64, 376 // beta)) and i.nslices * beta <= 376
+        assert i.np % 256 == 0     # the tcgen05 engine's tile width
+    finally:
+        oz.ozmp_plan_destroy(h)
+
+
+def test_binary16_digit_limits():
+    # no digit width fits beyond k = 2^24; the register splitter holds at
+    # most 4 components and windows of beta s <= 376 bits
+    for args in [(oz.Prec.DD, 8, 8, 2 ** 24 + 1, 0), (5, 8, 8, 64, 0), (oz.Prec.DD, 8, 8, 64, 377 // 9 + 1)]:
+        with pytest.raises(oz.OzmpError) as e:
+            oz.ozmp_plan_create(args[0], args[1], args[2], args[3], oz.Form.FP16, args[4], None)
+        assert e.value.status == oz.Status.ERR_UNSUPPORTED, args
+    h = oz.ozmp_plan_create(oz.Prec.DD, 8, 8, 64, oz.Form.FP16, 376 // 9, None)   # beta 9 at k = 64
+    assert oz.ozmp_plan_get_info(h).beta == 9
+    oz.ozmp_plan_destroy(h)

@@ -38,8 +38,8 @@ Q = {"dd": 2, "td": 3, "qd": 4, "ts": 3}
 def _rule(A, B, form, target):
     """The documented a-priori slice count, from exact exponents: the smallest
     s with log2(k c(s)) - W(s) + log2(||2^E|| ||2^F||) <= -(target + 1) +
-    log2(sqrt(sum_p ||A0(:,p)||^2 ||B0(p,:)||^2)) (A0, B0: the leading
-    components), and the margin of that s."""
+    log2(sqrt(sum_p ||A(:,p)||^2 ||B(p,:)||^2)) (each element the binary64
+    sum of its components), and the margin of that s."""
     beta, eo, D = {"fp8bal": (5, 1, 16), "fp8": (4, 0, 15), "int8": (7, 0, 127)}[form]
     m, k = A[0].shape
     Bt = [np.asfortranarray(b.T) for b in B]
@@ -48,8 +48,8 @@ def _rule(A, B, form, target):
     ge, gf = max(E), max(F)
     se = sum(2.0 ** (2 * (e - ge)) for e in E)
     sf = sum(2.0 ** (2 * (f - gf)) for f in F)
-    a = np.ldexp(A[0].astype(np.float64), -ge)      # leading components
-    b = np.ldexp(B[0].astype(np.float64), -gf)
+    a = np.ldexp(sum(c.astype(np.float64) for c in A), -ge)    # elements as binary64 sums
+    b = np.ldexp(sum(c.astype(np.float64) for c in B), -gf)
     est = float(np.sum(np.sum(a * a, axis=0) * np.sum(b * b, axis=1)))
     rhs = -(target + 1) + 0.5 * math.log2(est)
 

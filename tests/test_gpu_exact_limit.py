@@ -21,7 +21,7 @@ and that every diagonal T_d = sum_{t+u=d} A_t B_u^T of ozmp_plan_diagonal
 equals the oracle's exact int64 slice products, element by element, on
 the CTA-pair tile, the single-CTA tile and the mma.sync (QMMA) engine, at a
 k with many pairs per drain and at the form's largest k (one pair per
-drain).
+drain); and the same for binary16 digits of beta = 6 bits on kind::f16.
 """
 import os
 import zlib
@@ -49,31 +49,37 @@ for _b in range(128):
         ENC[32 - int(_v)] = _b | 0x80
 
 
-def _digits(rng, s, rows, k, balanced):
-    """Digits (s, rows, k) int8 at their largest magnitudes, one sign pattern.
+def _digits(rng, s, rows, k, balanced, beta=4):
+    """Digits (s, rows, k) int16 at their largest magnitudes, one sign pattern.
 
     Balanced radix-32: top digit 16 and the others in {-16, -15} (mostly -16;
     the negative rest keeps |x| below 2).  Products of two non-top digits are
-    then +256, +240 or +225.  4-bit: all digits in {14, 15} (mostly 15),
-    products 196 .. 225."""
-    d = np.empty((s, rows, k), np.int8)
+    then +256, +240 or +225.  beta-bit digits: all in {2^beta - 2,
+    2^beta - 1} (mostly the largest), products up to (2^beta - 1)^2."""
+    d = np.empty((s, rows, k), np.int16)
     if balanced:
         d[0] = 16
         for t in range(1, s):
             d[t] = np.where(rng.random((rows, k)) < 0.85, -16, -15)
     else:
+        top = (1 << beta) - 1
         for t in range(s):
-            d[t] = np.where(rng.random((rows, k)) < 0.75, 15, 14)
+            d[t] = np.where(rng.random((rows, k)) < 0.75, top, top - 1)
     return d
 
 
-def _components(d, balanced, q):
+def _group(balanced, beta):
+    """Digits per binary64 component."""
+    return 10 if balanced else 52 // beta
+
+
+def _components(d, balanced, q, beta=4):
     """Exact binary64 components (q arrays rows x k) of the values whose
     digits are d: groups of g digits, each group one component."""
     s = d.shape[0]
-    g = 10 if balanced else 12
+    g = _group(balanced, beta)
     assert s == g * q
-    radix, bits, e0 = (32, 5, 2) if balanced else (16, 4, 1)
+    radix, bits, e0 = (32, 5, 2) if balanced else (1 << beta, beta, 1)
     comps = []
     for c in range(q):
         acc = np.zeros(d.shape[1:], np.int64)
@@ -94,6 +100,10 @@ CASES = [
     ("fp8-single-kmax", 2, "fp8", 256, 72, 74565, True),
     ("qmma-k2048", 4, "fp8mma", 256, 200, 2048, False),
     ("qmma-kmax", 2, "fp8mma", 128, 72, 74565, False),
+    # binary16 digits on kind::f16: beta = 6 at k = 2048 (two pairs a drain)
+    # and at k = 4096 (one pair a drain, 4096 * 63^2 = 0.97 * 2^24)
+    ("fp16-pair-k2048", 4, "fp16", 256, 200, 2048, False),
+    ("fp16-single-k4096", 2, "fp16", 128, 72, 4096, False),
 ]
 
 
@@ -101,12 +111,13 @@ CASES = [
 def test_diagonals_exact_at_the_accumulator_limit(case):
     name, q, form, m, n, k, single = case
     balanced = form == "fp8bal"
-    s = (10 if balanced else 12) * q
+    beta = O.beta_fp32(k) if form == "fp16" else (5 if balanced else 4)
+    s = _group(balanced, beta) * q
     rng = np.random.default_rng(zlib.crc32(name.encode()))
-    dA = _digits(rng, s, m, k, balanced)
-    dB = _digits(rng, s, n, k, balanced)
-    A = _components(dA, balanced, q)
-    Bt = _components(dB, balanced, q)                 # rows of Bt = columns of B
+    dA = _digits(rng, s, m, k, balanced, beta)
+    dB = _digits(rng, s, n, k, balanced, beta)
+    A = _components(dA, balanced, q, beta)
+    Bt = _components(dB, balanced, q, beta)           # rows of Bt = columns of B
     old = os.environ.get("OZMP_TC_PAIR")
     if single:
         os.environ["OZMP_TC_PAIR"] = "0"
@@ -119,8 +130,8 @@ def test_diagonals_exact_at_the_accumulator_limit(case):
             else:
                 os.environ["OZMP_TC_PAIR"] = old
     i = p.info
-    dmax2 = 256 if balanced else 225
-    assert i.nslices == s and i.pairs_per_drain == (2 ** 24) // (k * dmax2)
+    dmax2 = 256 if balanced else ((1 << beta) - 1) ** 2
+    assert i.nslices == s and i.beta == beta and i.pairs_per_drain == (2 ** 24) // (k * dmax2)
     # the drains reach the binary32 limit: pairs_per_drain full pairs of the
     # largest products come to within 8 % of 2^24
     assert i.pairs_per_drain * k * dmax2 > 0.92 * 2 ** 24
@@ -131,16 +142,20 @@ def test_diagonals_exact_at_the_accumulator_limit(case):
     E, F = [t.cpu().numpy() for t in p.exponents()]
     assert (E == 1).all() and (F == 1).all()
     ga, gb = p.digits()
-    # the library's digits are the chosen ones (compared as e4m3 codes)
+    # the library's digits are the chosen ones (e4m3 codes, or binary16 values)
     for t in range(s):
-        np.testing.assert_array_equal(ga[t, :m, :k].cpu().numpy(), ENC[dA[t].astype(np.intp) + 32])
-        np.testing.assert_array_equal(gb[t, :n, :k].cpu().numpy(), ENC[dB[t].astype(np.intp) + 32])
+        if form == "fp16":
+            np.testing.assert_array_equal(ga[t, :m, :k].cpu().numpy().astype(np.int16), dA[t])
+            np.testing.assert_array_equal(gb[t, :n, :k].cpu().numpy().astype(np.int16), dB[t])
+        else:
+            np.testing.assert_array_equal(ga[t, :m, :k].cpu().numpy(), ENC[dA[t].astype(np.intp) + 32])
+            np.testing.assert_array_equal(gb[t, :n, :k].cpu().numpy(), ENC[dB[t].astype(np.intp) + 32])
     rows = sorted({0, 1, 127, m // 2 + 3, m - 1})
     cols = sorted({0, 1, n // 2, n - 1})
     # the oracle's splitter finds the chosen digits as well (a sample)
     pc = slice(0, 96)
     sub = [a[rows][:, pc] for a in A]
-    Eo, do = O.split_balanced(sub, s) if balanced else O.split(sub, 4, s)
+    Eo, do = O.split_balanced(sub, s) if balanced else O.split(sub, beta, s)
     assert Eo == [1] * len(rows)
     np.testing.assert_array_equal(do, dA[:, rows][:, :, pc])
     # every diagonal against the oracle's exact slice products on sampled

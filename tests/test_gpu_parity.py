@@ -64,10 +64,10 @@ def _split_check(prec, form, m, n, k, phi, seed, nslices=0):
     return p, A, B, Ad, Bd, dA, dB
 
 
-@pytest.mark.parametrize("form", ["fp8", "fp8bal", "int8", "fp64"])
+@pytest.mark.parametrize("form", ["fp8", "fp8bal", "int8", "fp64", "fp16"])
 @pytest.mark.parametrize("prec", ["dd", "td", "qd", "ts"])
 def test_split_bit_exact(prec, form):
-    _split_check(prec, form, 150, 140, 130, phi=1.0, seed=1, nslices=6 if form == "fp64" else 14)
+    _split_check(prec, form, 150, 140, 130, phi=1.0, seed=1, nslices={"fp64": 6, "fp16": 10}.get(form, 14))
 
 
 @pytest.mark.parametrize("form,s", [("fp8", 64), ("fp8", 65), ("fp8bal", 63), ("fp8bal", 1)])
@@ -136,9 +136,9 @@ def test_column_split_at_the_shared_memory_limit(prec, kmax):
         assert not digits_to_int(gb[:, n:, :], "fp8bal").any() and not digits_to_int(gb[:, :, k:], "fp8bal").any()
 
 
-@pytest.mark.parametrize("form", ["fp8", "fp8bal", "fp8mma", "int8", "fp64"])
+@pytest.mark.parametrize("form", ["fp8", "fp8bal", "fp8mma", "int8", "fp64", "fp16"])
 def test_diagonals_bit_exact(form):
-    s = {"fp8": 20, "fp8bal": 16, "fp8mma": 20, "int8": 12, "fp64": 5}[form]
+    s = {"fp8": 20, "fp8bal": 16, "fp8mma": 20, "int8": 12, "fp64": 5, "fp16": 11}[form]
     p, A, B, Ad, Bd, dA, dB = _split_check("dd", form, 200, 150, 130, phi=1.0, seed=2, nslices=s)
     T = O.slice_products(dA, dB)
     for d in sorted({2, 3, s // 2 + 1, s + 1}):
@@ -172,7 +172,9 @@ CASES = [("dd", "fp8", 130, 140, 150), ("dd", "fp8mma", 140, 130, 150), ("dd", "
          ("qd", "fp8", 70, 130, 64), ("qd", "int8", 130, 70, 90), ("qd", "fp64", 140, 70, 70),
          ("ts", "fp8", 150, 140, 130), ("ts", "int8", 140, 130, 150), ("ts", "fp64", 130, 150, 140),
          ("dd", "fp8bal", 130, 140, 150), ("dd", "fp8bal", 300, 520, 260), ("td", "fp8bal", 130, 70, 100),
-         ("qd", "fp8bal", 70, 130, 64), ("ts", "fp8bal", 150, 140, 130)]
+         ("qd", "fp8bal", 70, 130, 64), ("ts", "fp8bal", 150, 140, 130),
+         ("dd", "fp16", 300, 520, 260), ("td", "fp16", 130, 70, 100), ("qd", "fp16", 70, 130, 64),
+         ("ts", "fp16", 150, 140, 130)]
 
 
 @pytest.mark.parametrize("prec,form,m,n,k", CASES)
