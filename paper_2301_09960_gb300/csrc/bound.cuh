@@ -65,9 +65,10 @@ __host__ __device__ inline double bound_log2(const BoundForm& f, int s, double S
 }
 
 // The largest exponent magnitude for which the unscaled squared norms of the
-// exponent pass (launch_split_exponents_norm) and their products stay inside
-// the normal binary64 range: m 4^GE, and k m n 4^(GE + GF), below 2^1010.
-constexpr int BOUND_RAW_EXP = 230;
+// exponent pass (launch_split_exponents_norm), summed in binary32, stay
+// inside its normal range: squares below 2^80, their sums over up to 2^31
+// rows below 2^111, the row maxima's squares above 2^-80.
+constexpr int BOUND_RAW_EXP = 40;
 
 #ifdef __CUDACC__
 // (x 2^-g)^2, exact scaling where 2^-g is a normal number

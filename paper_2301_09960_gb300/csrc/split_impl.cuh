@@ -13,6 +13,7 @@
 #include <cuda_fp8.h>
 #include "ozmp_internal.cuh"
 #include "kernels.h"
+#include "bound.cuh"
 
 namespace ozmp {
 
@@ -148,31 +149,59 @@ __global__ void __launch_bounds__(256) k_exp_cols(Operand<T> b, int64_t k, int64
 
 // ---------------------------------------------------------------------------
 // K1 with the statistics of the data-dependent slice count (bound.cuh): the
-// same exponents, and beside them the squared norms of the elements (their
-// components summed in binary64: an estimate, which unnormalised components
-// that cancel do not mislead), unscaled (the caller falls back to scaled
-// norms when the exponents leave the range where no square or product of
-// squares can overflow or vanish): colA[p] += sum_i a_ip^2 over the block's
-// rows, rowB[p] += sum_j b_pj^2 over the block's columns (both zeroed before).
+// same exponents, and beside them the squared norms of the elements (each
+// magnitude estimated from its exact exponent and leading component, in
+// binary32: mag_est_f32), unscaled (the caller falls back to scaled norms
+// when the exponents leave +-BOUND_RAW_EXP, where no square or sum of squares
+// can overflow or vanish in binary32): colA[p] += sum_i a_ip^2 over the
+// block's rows, rowB[p] += sum_j b_pj^2 over the block's columns (both zeroed
+// before).
 __device__ __forceinline__ int xmax_warp(int v) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 
+// |x| of an element as a binary32 from bit operations only (the binary64
+// pipe is slow on this GPU): the leading component when its exponent is the
+// element's exact exponent e (2^(e-1) <= |x| < 2^e), else 2^(e-1), a lower
+// bound (components that cancel cannot inflate it).  0 for a zero element or
+// below the binary32 normal range; saturated above it (exponents beyond
+// +-BOUND_RAW_EXP send the caller to the scaled norms anyway).
+template <typename T>
+__device__ __forceinline__ float mag_est_f32(const T (&v)[4], int e) {
+    if (e == OZMP_EXP_ZERO) return 0.f;
+    int fe;            // binary32 exponent field of the estimate
+    unsigned man = 0;  // its mantissa bits
+    if constexpr (sizeof(T) == 8) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong((double)v[0]);
+        const int ef = (int)((b >> 52) & 0x7ff);
+        if (ef != 0 && ef - 1022 == e) { fe = ef - 1023 + 127; man = (unsigned)((b >> 29) & 0x7fffffu); }
+        else fe = e - 1 + 127;
+    } else {
+        const unsigned b = __float_as_uint((float)v[0]);
+        const int ef = (int)((b >> 23) & 0xff);
+        if (ef != 0 && ef - 126 == e) { fe = ef; man = b & 0x7fffffu; }
+        else fe = e - 1 + 127;
+    }
+    if (fe <= 0) return 0.f;
+    if (fe >= 255) { fe = 254; man = 0x7fffffu; }
+    return __uint_as_float(((unsigned)fe << 23) | man);
+}
+
 // 16 per-lane values v[c] (c = column) summed over the 32 lanes of a warp by
 // recursive halving: each step hands half of the columns to the partner lane;
 // at the end lanes 2c and 2c + 1 hold the sum of column c (16 shuffle steps
 // per warp instead of a 5-step reduction per column)
-__device__ __forceinline__ double xsum16_warp(double (&v)[16]) {
+__device__ __forceinline__ float xsum16_warp(float (&v)[16]) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
         const bool up = (lane & o) != 0;   // this lane keeps the upper half of the columns
 #pragma unroll
         for (int c = 0; c < h; ++c) {
-            const double give = up ? v[c] : v[c + h];
-            const double got = __shfl_xor_sync(0xffffffffu, give, o);
+            const float give = up ? v[c] : v[c + h];
+            const float got = __shfl_xor_sync(0xffffffffu, give, o);
             v[c] = (up ? v[c + h] : v[c]) + got;
         }
     }
@@ -196,7 +225,7 @@ __global__ void __launch_bounds__(256) k_exp_rows_norm(Operand<T> a, int64_t m, 
     __syncthreads();
     int emax = OZMP_EXP_ZERO;
     bool ok = true;
-    double sq[KC];
+    float sq[KC];
 #pragma unroll
     for (int g = 0; g < KC / U; ++g) {
         const int64_t p = p0 + g * U;
@@ -208,15 +237,13 @@ __global__ void __launch_bounds__(256) k_exp_rows_norm(Operand<T> a, int64_t m, 
             int e;
             ok &= exponent_loaded<T>(v[u], Q, e);   // zeros outside the matrix: no exponent
             emax = e > emax ? e : emax;
-            double x = 0.0;
-#pragma unroll
-            for (int c = 0; c < Q; ++c) x += (double)v[u][c];
+            const float x = mag_est_f32<T>(v[u], e);
             sq[g * U + u] = x * x;
         }
     }
-    const double w = xsum16_warp(sq);
+    const float w = xsum16_warp(sq);
     const int lane = threadIdx.x & 31;
-    if ((lane & 1) == 0 && (lane >> 1) < p1 - p0) atomicAdd(&sc[lane >> 1], w);
+    if ((lane & 1) == 0 && (lane >> 1) < p1 - p0) atomicAdd(&sc[lane >> 1], (double)w);
     __syncthreads();
     if (threadIdx.x < p1 - p0) atomicAdd(&colA[p0 + threadIdx.x], sc[threadIdx.x]);
     if (in && emax != OZMP_EXP_ZERO) atomicMax(&E[i], emax);
@@ -238,7 +265,7 @@ __global__ void __launch_bounds__(256) k_exp_cols_norm(Operand<T> b, int64_t k, 
     const int64_t j1 = j0 + JB < n ? j0 + JB : n;
     if (threadIdx.x < JB) sf[threadIdx.x] = OZMP_EXP_ZERO;
     __syncthreads();
-    double acc = 0.0;
+    float acc = 0.f;
     bool ok = true;
     for (int64_t j = j0; j < j1; j += U) {
         T v[U][4];
@@ -251,15 +278,13 @@ __global__ void __launch_bounds__(256) k_exp_cols_norm(Operand<T> b, int64_t k, 
             ok &= exponent_loaded<T>(v[u], Q, e);
             const int w = xmax_warp(e);
             if ((threadIdx.x & 31) == 0 && w != OZMP_EXP_ZERO) atomicMax(&sf[j + u - j0], w);
-            double x = 0.0;
-#pragma unroll
-            for (int c = 0; c < Q; ++c) x += (double)v[u][c];
+            const float x = mag_est_f32<T>(v[u], e);
             acc += x * x;
         }
     }
     __syncthreads();
     if (threadIdx.x < j1 - j0 && sf[threadIdx.x] != OZMP_EXP_ZERO) atomicMax(&F[j0 + threadIdx.x], sf[threadIdx.x]);
-    if (in && acc != 0.0) atomicAdd(&rowB[p], acc);
+    if (in && acc != 0.f) atomicAdd(&rowB[p], (double)acc);
     if (!ok) atomicOr(status, ST_NONFINITE);
 }
 

@@ -3,7 +3,7 @@
 * With nslices = 0 the library picks, after the exponent reduce, the
   smallest s whose truncation bound k c(s) 2^-W(s) ||2^E|| ||2^F|| is half
   of 2^-target times the estimate sqrt(sum_p ||A(:,p)||^2 ||B(p,:)||^2) of
-  ||C||_F.  The rule is restated here from exact exponents and the
+  ||C||_F (element magnitudes from their exponents and leading components).  The rule is restated here from exact exponents and the
   operands, and the library's choice must equal it; wider exponent spreads
   (phi = 0, 1, 4) need more slices.
 * The result with the chosen s is bit-exact against the oracle's Ozaki sum
@@ -35,11 +35,33 @@ TARGET = {"dd": 100, "td": 150, "qd": 200, "ts": 66}
 Q = {"dd": 2, "td": 3, "qd": 4, "ts": 3}
 
 
+def _mag(comps):
+    """The magnitude estimate of every element (rows x cols): its leading
+    component truncated to 24 bits when that component has the element's
+    exact exponent e (2^(e-1) <= |x| < 2^e), else 2^(e-1); 0 for zeros."""
+    vals = X.matrix_values(comps)
+    lead = comps[0].astype(np.float64)
+    out = np.zeros(lead.shape)
+    for i, row in enumerate(vals):
+        for j, v in enumerate(row):
+            e = X.exponent(v)
+            if e == X.EXP_ZERO:
+                continue
+            h = float(lead[i, j])
+            if h != 0.0 and X.exponent(X.decode(h)) == e:
+                m, ee = np.frexp(abs(h))
+                out[i, j] = np.ldexp(np.floor(m * 2.0 ** 24) / 2.0 ** 24, ee)
+            else:
+                out[i, j] = 2.0 ** (e - 1)
+    return out
+
+
 def _rule(A, B, form, target):
     """The documented a-priori slice count, from exact exponents: the smallest
     s with log2(k c(s)) - W(s) + log2(||2^E|| ||2^F||) <= -(target + 1) +
-    log2(sqrt(sum_p ||A(:,p)||^2 ||B(p,:)||^2)) (each element the binary64
-    sum of its components), and the margin of that s."""
+    log2(sqrt(sum_p ||A(:,p)||^2 ||B(p,:)||^2)) (each element's magnitude
+    estimated from its exponent and leading component), and the margin of
+    that s."""
     beta, eo, D = {"fp8bal": (5, 1, 16), "fp8": (4, 0, 15), "int8": (7, 0, 127)}[form]
     m, k = A[0].shape
     Bt = [np.asfortranarray(b.T) for b in B]
@@ -48,8 +70,8 @@ def _rule(A, B, form, target):
     ge, gf = max(E), max(F)
     se = sum(2.0 ** (2 * (e - ge)) for e in E)
     sf = sum(2.0 ** (2 * (f - gf)) for f in F)
-    a = np.ldexp(sum(c.astype(np.float64) for c in A), -ge)    # elements as binary64 sums
-    b = np.ldexp(sum(c.astype(np.float64) for c in B), -gf)
+    a = np.ldexp(_mag(A), -ge)
+    b = np.ldexp(_mag(B), -gf)
     est = float(np.sum(np.sum(a * a, axis=0) * np.sum(b * b, axis=1)))
     rhs = -(target + 1) + 0.5 * math.log2(est)
 
@@ -91,7 +113,7 @@ def test_chosen_count_follows_the_rule_and_meets_the_target(prec, form, m, n, k)
         assert p.status() == oz.Status.OK
         s = p.info.nslices
         want, margin = _rule(A, B, form, TARGET[prec])
-        if margin > 1e-6:      # away from a tie of the two sides' roundings
+        if margin > 1e-3:      # away from a tie (the library sums the squares in binary32)
             assert s == want, (phi, s, want)
         if last is not None:
             assert s >= last - 1, (phi, s, last)
