@@ -14,9 +14,12 @@
 //   ||S - C*||_F <= k c(s) 2^-W(s) ||2^E||_2 ||2^F||_2.
 //
 // A-priori choice: ||C*||_F is estimated by sqrt(sum_p ||A(:,p)||^2
-// ||B(p,:)||^2), each element taken as the binary64 sum of its components
-// (exact in expectation for independent signs); s is the smallest count
-// whose bound is 2^-(target + 1) of that estimate.
+// ||B(p,:)||^2) (exact in expectation for independent signs); s is the
+// smallest count whose bound is 2^-(target + 1) of that estimate.  The
+// exponent passes take each element's magnitude as its leading component
+// when that component carries the element's exponent, else 2^(e-1), and sum
+// the squares in binary32; the scaled fallback launches take the binary64
+// sum of the components.
 // A-posteriori check: with the result's first components c0,
 // ||C*||_F >= ||S||_F - bound, and the canonical rounding into q components
 // adds at most u_q ||S||_F; the check flags the result when
