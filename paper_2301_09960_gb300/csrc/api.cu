@@ -105,15 +105,6 @@ ozmp_status plan_create_internal(ozmp_plan* plan, ozmp_prec prec, int64_t m, int
             p->s_lo = s;
         }
         p->ws_bytes = most;
-        // the read-back of the chosen s: a pinned word and an event after its copy
-        if (cudaMallocHost((void**)&p->host_s, sizeof(int)) != cudaSuccess ||
-            cudaEventCreateWithFlags(&p->ev_s, cudaEventDisableTiming) != cudaSuccess) {
-            cudaGetLastError();
-            if (p->host_s) cudaFreeHost(p->host_s);
-            delete[] p->sched_host;
-            delete p;
-            return OZMP_ERR_NOMEM;
-        }
     }
     *plan = p;
     return OZMP_OK;
@@ -203,6 +194,21 @@ static ozmp_status do_split(ozmp_plan p, const void* const* A, int64_t lda, cons
     SplitArgs a = split_args(p, A, lda, B, ldb);
     char* w = (char*)p->ws;
     if (p->adapt) {
+        // the read-back of the chosen s: a pinned word and an event after its
+        // copy, made at the plan's first split (like its workspace)
+        if (!p->host_s) {
+            if (cudaMallocHost((void**)&p->host_s, sizeof(int)) != cudaSuccess) {
+                cudaGetLastError();
+                p->host_s = nullptr;
+                return OZMP_ERR_NOMEM;
+            }
+            if (cudaEventCreateWithFlags(&p->ev_s, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                cudaFreeHost(p->host_s);
+                p->host_s = nullptr;
+                return OZMP_ERR_CUDA;
+            }
+        }
         BoundStats* bs = bound_stats(p);
         double* colA = (double*)(w + p->off_colA);
         double* rowB = (double*)(w + p->off_rowB);
