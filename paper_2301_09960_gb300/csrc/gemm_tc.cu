@@ -1,5 +1,6 @@
 // Single-problem launch of the tcgen05 e4m3 slice-product kernel (the
 // kernel itself is in gemm_tc_impl.cuh) and the tensor-map helpers.
+#include <type_traits>
 #include <vector>
 #include "gemm_tc_impl.cuh"
 
@@ -191,72 +192,79 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer (the leader's)
         if (lane == 0 && rank == 0) {
-            long long n = 0;
-            int buf = 0, uses[2] = {0, 0};
-            bool ok = mbar_wait<CG == 2>(&acce[0], 1u, abort_flag, WL);     // first use of buffer 0
-            for (int k = 0; ok; ++k) {
-                const int idx = take(k, false, false);
-                if (idx == -2) { ok = false; break; }
-                if (idx < 0) break;
-                Item it;
-                item_at<CG>(sc, &single, &tmA, &tmB, idx, it, rank);
-                const Prob p = *it.p;
-                const uint32_t idesc = idesc_e4m3(BM * CG, it.bn);
-                Walk w = Walk::at(it.dhi, it.pa);
-                int since = 0;
-                bool fresh = true;
-                for (int pi = it.pa; ok && pi < it.pb; ++pi) {
-                    const uint32_t dcol = tmem + (uint32_t)(buf * BN);
-                    for (int kc = 0; kc < it.KT; ++kc, ++n) {
-                        const int st = (int)(n % NS);
-                        const unsigned ph = (unsigned)((n / NS) & 1);
-                        if (!mbar_wait<CG == 2>(&full[st], ph, abort_flag, WL)) { ok = false; break; }
-                        tc_fence_after();
-                        const uint64_t ad = desc_sw128(saddr(sA + (size_t)st * STAGE_A));
-                        const uint64_t bd = desc_sw128(saddr(sB + (size_t)st * SB));
+            // the digit type is the same for every item of a launch: one issue loop
+            // per type, so that no MMA of the loop waits on a branch
+            auto issue = [&](auto f16_tag) {
+                constexpr bool F16 = decltype(f16_tag)::value;
+                long long n = 0;
+                int buf = 0, uses[2] = {0, 0};
+                bool ok = mbar_wait<CG == 2>(&acce[0], 1u, abort_flag, WL);     // first use of buffer 0
+                for (int k = 0; ok; ++k) {
+                    const int idx = take(k, false, false);
+                    if (idx == -2) { ok = false; break; }
+                    if (idx < 0) break;
+                    Item it;
+                    item_at<CG>(sc, &single, &tmA, &tmB, idx, it, rank);
+                    const Prob p = *it.p;
+                    const uint32_t idesc = idesc_e4m3(BM * CG, it.bn);
+                    Walk w = Walk::at(it.dhi, it.pa);
+                    int since = 0;
+                    bool fresh = true;
+                    for (int pi = it.pa; ok && pi < it.pb; ++pi) {
+                        const uint32_t dcol = tmem + (uint32_t)(buf * BN);
+                        for (int kc = 0; kc < it.KT; ++kc, ++n) {
+                            const int st = (int)(n % NS);
+                            const unsigned ph = (unsigned)((n / NS) & 1);
+                            if (!mbar_wait<CG == 2>(&full[st], ph, abort_flag, WL)) { ok = false; break; }
+                            tc_fence_after();
+                            const uint64_t ad = desc_sw128(saddr(sA + (size_t)st * STAGE_A));
+                            const uint64_t bd = desc_sw128(saddr(sB + (size_t)st * SB));
 #pragma unroll
-                        for (int kk = 0; kk < BK / 32; ++kk) {
-                            // 32 bytes of K per MMA: 32 e4m3 or 16 binary16 digits
-                            const uint32_t acc = (fresh && kk == 0) ? 0u : 1u;
-                            const uint64_t a2 = ad + (uint64_t)(2 * kk), b2 = bd + (uint64_t)(2 * kk);
-                            if (p.kind) {
-                                if (CG == 2) mma_f16_tc_pair(dcol, a2, b2, idesc, acc);
-                                else mma_f16_tc(dcol, a2, b2, idesc, acc);
-                            } else {
-                                if (CG == 2) mma_e4m3_tc_pair(dcol, a2, b2, idesc, acc);
-                                else mma_e4m3_tc(dcol, a2, b2, idesc, acc);
+                            for (int kk = 0; kk < BK / 32; ++kk) {
+                                // 32 bytes of K per MMA: 32 e4m3 or 16 binary16 digits
+                                const uint32_t acc = (fresh && kk == 0) ? 0u : 1u;
+                                const uint64_t a2 = ad + (uint64_t)(2 * kk), b2 = bd + (uint64_t)(2 * kk);
+                                if constexpr (F16) {
+                                    if (CG == 2) mma_f16_tc_pair(dcol, a2, b2, idesc, acc);
+                                    else mma_f16_tc(dcol, a2, b2, idesc, acc);
+                                } else {
+                                    if (CG == 2) mma_e4m3_tc_pair(dcol, a2, b2, idesc, acc);
+                                    else mma_e4m3_tc(dcol, a2, b2, idesc, acc);
+                                }
+                            }
+                            fresh = false;
+                            if (CG == 2) mma_commit_pair(&empty[st]);
+                            else mma_commit(&empty[st]);
+                        }
+                        if (!ok) break;
+                        ++since;
+                        const bool diag_end = (w.t == w.d - 1);
+                        if (since == p.ppd || diag_end || pi == it.pb - 1) {
+                            if (CG == 2) mma_commit_pair(&accf[buf]);
+                            else mma_commit(&accf[buf]);
+                            uses[buf]++;
+                            buf ^= 1;
+                            since = 0;
+                            fresh = true;
+                            // the k-th use of a buffer waits for the epilogues' (k-1)-th release
+                            if (!mbar_wait<CG == 2>(&acce[buf], (unsigned)((uses[buf] & 1) ^ 1), abort_flag, WL)) {
+                                ok = false;
+                                break;
                             }
                         }
-                        fresh = false;
-                        if (CG == 2) mma_commit_pair(&empty[st]);
-                        else mma_commit(&empty[st]);
+                        w.next_pair();
                     }
-                    if (!ok) break;
-                    ++since;
-                    const bool diag_end = (w.t == w.d - 1);
-                    if (since == p.ppd || diag_end || pi == it.pb - 1) {
-                        if (CG == 2) mma_commit_pair(&accf[buf]);
-                        else mma_commit(&accf[buf]);
-                        uses[buf]++;
-                        buf ^= 1;
-                        since = 0;
-                        fresh = true;
-                        // the k-th use of a buffer waits for the epilogues' (k-1)-th release
-                        if (!mbar_wait<CG == 2>(&acce[buf], (unsigned)((uses[buf] & 1) ^ 1), abort_flag, WL)) {
-                            ok = false;
-                            break;
-                        }
-                    }
-                    w.next_pair();
                 }
-            }
-            if (!ok) raise_abort();
-            // every issued MMA (into both CTAs' tensor memory) has completed
-            // before the pair passes the final cluster barrier
-            if (CG == 2) mma_commit_local_pair(done);
-            else mma_commit(done);
-            volatile int never = 0;
-            mbar_wait<CG == 2>(done, 0u, &never, DL);
+                if (!ok) raise_abort();
+                // every issued MMA (into both CTAs' tensor memory) has completed
+                // before the pair passes the final cluster barrier
+                if (CG == 2) mma_commit_local_pair(done);
+                else mma_commit(done);
+                volatile int never = 0;
+                mbar_wait<CG == 2>(done, 0u, &never, DL);
+            };
+            if (sc.kind) issue(std::true_type{});
+            else issue(std::false_type{});
         }
     } else {
         // ------------------------------------------------------------ epilogue
@@ -593,6 +601,7 @@ cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t st) {
     sc.nitems = g.sched_nitems;
     sc.wait_limit = g.wait_limit;
     sc.inject_stall = g.inject_stall;
+    sc.kind = kind;
     sc.step_done = (sc.counter && g.lock_w > 0) ? g.step_done : nullptr;
     sc.retired = g.retired;
     sc.lock_w = g.lock_w;

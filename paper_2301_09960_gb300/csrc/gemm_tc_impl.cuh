@@ -364,6 +364,7 @@ struct Sched {
     int nitems;                //   (zeroed before the launch) instead of the per-CTA lists
     long long wait_limit;      // polls before a wait gives up (0: WAIT_LIMIT)
     int inject_stall;          // test hook: never load the first stage of each CTA's first item
+    int kind;                  // digit type of every problem of the launch (Prob::kind)
     // loose lockstep of the clusters' pair walks (null: off): step_done[P]
     // counts the clusters that issued their P-th whole-tile pair, retired the
     // clusters without whole tiles left; before pair P a leader waits a
