@@ -558,9 +558,12 @@ def config5_qd_fp64(oz, torch):
 def launches_per_step(oz, info, Bd, k, w, adaptive=True, check=True):
     """Kernels of one plan execution (the register splitter, q <= 4).
 
-    Slice count chosen from the data (adaptive): exponent init, the row and
-    the column exponent passes with the norms folded in, the choice, then
-    the row and the column digit kernels.  Fixed slice count: exponent init,
+    Slice count chosen from the data (adaptive): exponent init, the row
+    exponent pass with the norms folded in, then for B either the one-pass
+    column digit kernel, which also reduces B's exponents and norms (the
+    conditions below), or a column exponent pass with the norms; the choice;
+    the row digits (and the column digits when B took two kernels).  Fixed
+    slice count: exponent init,
     row exponents, then for B either one pass (e4m3 forms, 16-byte aligned
     column starts and lengths, at most 112 KB a column) or column exponents
     + column digits, the row digits, and the exponent statistics of the
@@ -570,12 +573,12 @@ def launches_per_step(oz, info, Bd, k, w, adaptive=True, check=True):
     form = oz.Form(info.form)
     e4m3 = form in (oz.Form.FP8, oz.Form.FP8_BAL, oz.Form.FP8_MMA)
     tc = form in (oz.Form.FP8, oz.Form.FP8_BAL, oz.Form.FP16)
+    ldb = Bd[0].stride(1)
+    one_pass = (e4m3 and (k * w) % 16 == 0 and (ldb * w) % 16 == 0 and len(Bd) * k * w <= 112 * 1024
+                and all(b.data_ptr() % 16 == 0 for b in Bd))
     if adaptive:
-        split = 4 + 2
+        split = 5 if one_pass else 6
     else:
-        ldb = Bd[0].stride(1)
-        one_pass = (e4m3 and (k * w) % 16 == 0 and (ldb * w) % 16 == 0 and len(Bd) * k * w <= 112 * 1024
-                    and all(b.data_ptr() % 16 == 0 for b in Bd))
         split = 3 + (1 if one_pass else 2) + (1 if check else 0)
     return split + 1 + (1 if tc else (1 if check else 0))
 

@@ -229,24 +229,38 @@ static ozmp_status do_split(ozmp_plan p, const void* const* A, int64_t lda, cons
         };
         // the exponent pass with the unscaled norms folded in, and the choice
         // in one launch; the scaled norms when the exponents leave their range
-        // (and for the many-component splitter)
-        if (cudaMemsetAsync(colA, 0, p->off_rowB - p->off_colA + (size_t)p->k * 8, p->stream) != cudaSuccess)
+        // (and for the many-component splitter).  Where the one-pass column
+        // digit kernel applies, it takes B's exponents and row norms itself:
+        // B's digits for the count of the last execution are then written
+        // before the choice, and B is read once.
+        float* rowBf = (float*)(w + p->off_rowBf);
+        if (cudaMemsetAsync(colA, 0, p->off_rowBf - p->off_colA + (size_t)p->k * 4, p->stream) != cudaSuccess)
             return OZMP_ERR_CUDA;
-        const cudaError_t en = launch_split_exponents_norm(a, colA, rowB, p->stream);
+        bool deferred = false;
+        const cudaError_t en = launch_split_exponents_norm(a, colA, rowB, &deferred, p->stream);
         bool ok;
         if (en == cudaErrorNotSupported) {
             cudaGetLastError();
             ok = launch_split_exponents(a, p->stream) == cudaSuccess && scaled_choice();
         } else {
-            ok = en == cudaSuccess && launch_bound_choose_raw(a.E, p->m, a.F, p->n, colA, rowB, p->k, bs,
-                                                              bound_form(p), p->s_lo, p->s_cap,
-                                                              p->stream) == cudaSuccess;
+            ok = en == cudaSuccess;
+            if (ok && deferred) {
+                SplitArgs b = a;
+                b.parts = 2;
+                b.rowBf = rowBf;
+                ok = launch_split_digits(b, p->stream) == cudaSuccess;
+            }
+            ok = ok && launch_bound_choose_raw(a.E, p->m, a.F, p->n, colA, rowB, deferred ? rowBf : nullptr, p->k,
+                                               bs, bound_form(p), p->s_lo, p->s_cap, p->stream) == cudaSuccess;
         }
         if (!ok || !copy_s()) return OZMP_ERR_CUDA;
-        // the digits for the count of the last execution go into the stream
-        // before the host waits for the new choice, so that the GPU splits
-        // while the host reads; a different choice splits again
-        if (launch_split_digits(a, p->stream) != cudaSuccess || cudaEventSynchronize(p->ev_s) != cudaSuccess)
+        // the digits for the count of the last execution (those of A alone
+        // when B's are written) go into the stream before the host waits for
+        // the new choice, so that the GPU splits while the host reads; a
+        // different choice splits again
+        SplitArgs ra = a;
+        if (deferred) ra.parts = 1;
+        if (launch_split_digits(ra, p->stream) != cudaSuccess || cudaEventSynchronize(p->ev_s) != cudaSuccess)
             return OZMP_ERR_CUDA;
         int s = *p->host_s;
         if (s < 0 && (!scaled_choice() || !read_s(&s))) return OZMP_ERR_CUDA;

@@ -212,8 +212,9 @@ __global__ void __launch_bounds__(256) k_bound_check(const T* C0, int64_t m, int
 // GE, GF, SE, SF from the exponents, est from the unscaled norms of the
 // exponent pass, and the slice count (-1: an exponent beyond the raw range)
 __global__ void __launch_bounds__(1024) k_bound_choose_raw(const int32_t* E, int64_t m, const int32_t* F, int64_t n,
-                                                           const double* colA, const double* rowB, int64_t k,
-                                                           BoundStats* st, BoundForm f, int s_lo, int s_hi) {
+                                                           const double* colA, const double* rowB,
+                                                           const float* rowBf, int64_t k, BoundStats* st,
+                                                           BoundForm f, int s_lo, int s_hi) {
     __shared__ int shi[32];
     __shared__ double shd[32];
     int ge = OZMP_EXP_ZERO, gf = OZMP_EXP_ZERO;
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__(1024) k_bound_choose_raw(const int32_t* E, int
         for (int u = 0; u < 4; ++u) {
             const int64_t p = p0 + (int64_t)u * blockDim.x;
             a4[u] = p < k ? colA[p] : 0.0;
-            b4[u] = p < k ? rowB[p] : 0.0;
+            b4[u] = p < k ? (rowBf ? (double)rowBf[p] : rowB[p]) : 0.0;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) v += a4[u] * b4[u];
@@ -311,9 +312,10 @@ cudaError_t launch_bound_choose(const void* const* A, int64_t lda, const void* c
 }
 
 cudaError_t launch_bound_choose_raw(const int32_t* E, int64_t m, const int32_t* F, int64_t n, const double* colA,
-                                    const double* rowB, int64_t k, BoundStats* st, const BoundForm& f, int s_lo,
-                                    int s_hi, cudaStream_t stream) {
-    k_bound_choose_raw<<<1, 1024, 0, stream>>>(E, m, F, n, colA, rowB, (m > 0 && n > 0) ? k : 0, st, f, s_lo, s_hi);
+                                    const double* rowB, const float* rowBf, int64_t k, BoundStats* st,
+                                    const BoundForm& f, int s_lo, int s_hi, cudaStream_t stream) {
+    k_bound_choose_raw<<<1, 1024, 0, stream>>>(E, m, F, n, colA, rowB, rowBf, (m > 0 && n > 0) ? k : 0, st, f, s_lo,
+                                               s_hi);
     return cudaGetLastError();
 }
 

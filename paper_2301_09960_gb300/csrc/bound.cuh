@@ -128,10 +128,12 @@ cudaError_t launch_bound_choose(const void* const* A, int64_t lda, const void* c
 // After launch_split_exponents_norm: the exponent statistics and the slice
 // count from the unscaled norms in one launch (resets the check's
 // accumulators too); st->s_needed = -1 when an exponent lies beyond
-// BOUND_RAW_EXP (then the scaled launches above decide).  s_hi - s_lo < 1024.
+// BOUND_RAW_EXP (then the scaled launches above decide).  B's row norms come
+// from rowBf (binary32, summed by the one-pass column digit kernel) when it is
+// set, else from rowB.  s_hi - s_lo < 1024.
 cudaError_t launch_bound_choose_raw(const int32_t* E, int64_t m, const int32_t* F, int64_t n, const double* colA,
-                                    const double* rowB, int64_t k, BoundStats* st, const BoundForm& f, int s_lo,
-                                    int s_hi, cudaStream_t stream);
+                                    const double* rowB, const float* rowBf, int64_t k, BoundStats* st,
+                                    const BoundForm& f, int s_lo, int s_hi, cudaStream_t stream);
 // The a-posteriori check of a result with s slices (first output component C0,
 // column-major m x n, leading dimension ldc): sets `flag` in *status when the
 // bound does not certify the target.

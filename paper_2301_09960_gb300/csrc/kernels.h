@@ -26,6 +26,9 @@ struct SplitArgs {
     int bal;               // balanced radix-32 e4m3 digits (beta = 5)
     long long wait_limit;  // one-pass column kernel: polls before its wait gives up (0: the default)
     int inject_stall;      // one-pass column kernel, test hook: copies never issued
+    int parts;             // digits of 1: A's rows only, 2: B's columns only (0: both)
+    float* rowBf;          // one-pass column kernel: also add each element's squared
+                           // magnitude estimate into rowBf[p] (null: no norms)
 };
 
 struct GemmArgs {
@@ -93,10 +96,16 @@ cudaError_t launch_split(const SplitArgs& a, cudaStream_t st);
 // included), then the digits for the plan's slice count
 cudaError_t launch_split_exponents(const SplitArgs& a, cudaStream_t st);
 // the exponent pass together with the unscaled squared norms, colA[p] =
-// sum_i a_ip^2 and rowB[p] = sum_j b_pj^2 (each element the binary64 sum of
-// its components; both zeroed by the caller); cudaErrorNotSupported for the
-// many-component splitter
-cudaError_t launch_split_exponents_norm(const SplitArgs& a, double* colA, double* rowB, cudaStream_t st);
+// sum_i a_ip^2 and rowB[p] = sum_j b_pj^2 (each element's magnitude estimated
+// from its exponent and leading component, in binary32; both zeroed by the
+// caller); cudaErrorNotSupported for the many-component splitter.  Where the
+// one-pass column digit kernel applies, B is left to it: *cols_deferred is
+// set, and F and the row norms (into SplitArgs::rowBf) come from that
+// kernel's launch (launch_split_digits with parts = 2)
+cudaError_t launch_split_exponents_norm(const SplitArgs& a, double* colA, double* rowB, bool* cols_deferred,
+                                        cudaStream_t st);
+// the digits for the plan's slice count (SplitArgs::parts: one operand only,
+// on the 1-byte digit forms)
 cudaError_t launch_split_digits(const SplitArgs& a, cudaStream_t st);
 cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t st);
 

@@ -46,7 +46,7 @@ struct ozmp_plan_s {
     void* sched_ws;
     // error bound (bound.cu): statistics region, per-column norms of A and
     // per-row norms of B (both k doubles), at offsets that depend on m, n, k only
-    size_t off_stats, off_colA, off_rowB;
+    size_t off_stats, off_colA, off_rowB, off_rowBf;
     int target_bits;   // the precision's normwise target 2^-target_bits
     int adapt;         // s chosen from the data at every execution (nslices = 0 at creation)
     int check;         // a-posteriori bound check after every execution
@@ -190,6 +190,7 @@ inline void fill_layout(ozmp_plan_s* p) {
     p->off_stats = off; off = align256(off + 256);
     p->off_colA = off; off = align256(off + kk * 8);
     p->off_rowB = off; off = align256(off + kk * 8);
+    p->off_rowBf = off; off = align256(off + kk * 4);
     p->off_Adig = off; off = align256(off + (size_t)p->s * p->mp * p->kp * p->db);
     p->off_Bdig = off; off = align256(off + (size_t)p->s * p->np * p->kp * p->db);
     p->off_acc = off;

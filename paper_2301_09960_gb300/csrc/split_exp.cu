@@ -51,6 +51,10 @@ static cudaError_t exponents(const SplitArgs& g, cudaStream_t st, bool all_cols)
 }
 
 cudaError_t launch_split_digits(const SplitArgs& g, cudaStream_t st) {
+    // one operand at a time (parts) and the row norms (rowBf) only on the
+    // 1-byte digit paths, whose launcher honours them
+    const bool b1 = !g.big && (g.form == OZMP_FORM_FP8 || g.form == OZMP_FORM_FP8_MMA || g.form == OZMP_FORM_INT8);
+    if ((g.parts != 0 || g.rowBf) && !b1) return cudaErrorInvalidValue;
     if (g.big) return launch_digits_big(g, st);
     if (g.form == OZMP_FORM_FP64) return launch_digits_fp64(g, st);
     if (g.form == OZMP_FORM_FP16) return launch_digits_fp16(g, st);
@@ -62,7 +66,8 @@ cudaError_t launch_split_digits(const SplitArgs& g, cudaStream_t st) {
 cudaError_t launch_split_exponents(const SplitArgs& g, cudaStream_t st) { return exponents(g, st, true); }
 
 template <typename T, int Q>
-static cudaError_t exponents_norm_impl(const SplitArgs& g, double* colA, double* rowB, cudaStream_t st) {
+static cudaError_t exponents_norm_impl(const SplitArgs& g, double* colA, double* rowB, bool defer_cols,
+                                       cudaStream_t st) {
     Operand<T> a = make_op<T>(g.A, g.q, g.lda);
     Operand<T> b = make_op<T>(g.B, g.q, g.ldb);
     init_exponents(g, st);
@@ -70,19 +75,24 @@ static cudaError_t exponents_norm_impl(const SplitArgs& g, double* colA, double*
         dim3 gr((unsigned)((g.m + 255) / 256), (unsigned)((g.k + 15) / 16));
         k_exp_rows_norm<T, Q><<<gr, 256, 0, st>>>(a, g.m, g.k, g.E, g.status, colA);
     }
-    if (g.n > 0 && g.k > 0) {
+    if (g.n > 0 && g.k > 0 && !defer_cols) {
         dim3 gr((unsigned)((g.k + 255) / 256), (unsigned)((g.n + 63) / 64));
         k_exp_cols_norm<T, Q><<<gr, 256, 0, st>>>(b, g.k, g.n, g.F, g.status, rowB);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_split_exponents_norm(const SplitArgs& g, double* colA, double* rowB, cudaStream_t st) {
+cudaError_t launch_split_exponents_norm(const SplitArgs& g, double* colA, double* rowB, bool* cols_deferred,
+                                        cudaStream_t st) {
     if (g.big) return cudaErrorNotSupported;   // the caller takes the exponents and the norms separately
-    return g.is_f32     ? exponents_norm_impl<float, 3>(g, colA, rowB, st)
-           : g.q == 2   ? exponents_norm_impl<double, 2>(g, colA, rowB, st)
-           : g.q == 3   ? exponents_norm_impl<double, 3>(g, colA, rowB, st)
-                        : exponents_norm_impl<double, 4>(g, colA, rowB, st);
+    // where the one-pass column digit kernel applies, it reduces B's exponents
+    // and sums B's row norms itself (SplitArgs::rowBf), so B is read once
+    const bool defer = cols_fused_smem(g) != 0 && g.n > 0 && g.k > 0;
+    *cols_deferred = defer;
+    return g.is_f32     ? exponents_norm_impl<float, 3>(g, colA, rowB, defer, st)
+           : g.q == 2   ? exponents_norm_impl<double, 2>(g, colA, rowB, defer, st)
+           : g.q == 3   ? exponents_norm_impl<double, 3>(g, colA, rowB, defer, st)
+                        : exponents_norm_impl<double, 4>(g, colA, rowB, defer, st);
 }
 
 cudaError_t launch_split(const SplitArgs& g, cudaStream_t st) {

@@ -681,10 +681,14 @@ __device__ __forceinline__ bool wait(uint64_t* b, long long polls) {
 }
 }  // namespace colbulk
 
+// With rowBf set, the exponent pass also adds each element's squared
+// magnitude estimate (mag_est_f32) into rowBf[p], coalesced along the column:
+// the row norms of B for the data-dependent slice count, without a pass of
+// its own over B.
 template <typename T, int FORM, int NW, int Q>
 __global__ void __launch_bounds__(256, 3) k_split_cols_fused(Operand<T> b, int64_t k, int64_t n, int32_t* F,
                                                           uint32_t* status, uint8_t* dig, int64_t np, int64_t kp,
-                                                          int s, long long polls, int stall) {
+                                                          int s, long long polls, int stall, float* rowBf) {
     extern __shared__ __align__(16) unsigned char smraw[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
     const T* col = reinterpret_cast<const T*>(smraw + 16);   // [Q][k]
@@ -722,6 +726,10 @@ __global__ void __launch_bounds__(256, 3) k_split_cols_fused(Operand<T> b, int64
             int e;
             ok &= exponent_loaded<T>(v, Q, e);
             emax = e > emax ? e : emax;
+            if (rowBf) {
+                const float x = mag_est_f32<T>(v, e);
+                if (x != 0.f) atomicAdd(&rowBf[p], x * x);
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -757,12 +765,20 @@ __global__ void __launch_bounds__(256, 3) k_split_cols_fused(Operand<T> b, int64
 }
 
 // binary64 digits, rows of A: 16 x 16 tile staged in shared memory
-// a digit (an integer of at most 26 bits) in the stored type: binary64, or
-// binary16 for the binary16-digit form (|d| <= 2047 there: exact)
+// a digit of magnitude `mag` (at most 26 bits) and the element's sign in the
+// stored type: binary64, or binary16 for the binary16-digit form (|d| <= 2047
+// there), converted from the integer directly (exact; no binary64 arithmetic,
+// whose pipe is narrow on this GPU; a zero digit is +0)
 template <typename DT>
-__device__ __forceinline__ DT digit_value(double d) { return (DT)d; }
+__device__ __forceinline__ DT digit_value(uint32_t mag, int sign) {
+    const double d = (double)mag;
+    return (DT)(sign < 0 ? -d : d);
+}
 template <>
-__device__ __forceinline__ __half digit_value<__half>(double d) { return __double2half(d); }
+__device__ __forceinline__ __half digit_value<__half>(uint32_t mag, int sign) {
+    const int v = (int)mag;
+    return __int2half_rn(sign < 0 ? -v : v);
+}
 
 template <typename T, int NW, typename DT = double>
 __global__ void __launch_bounds__(256) k_split_rows_f64(Operand<T> a, int64_t m, int64_t k, const int32_t* E,
@@ -777,8 +793,7 @@ __global__ void __launch_bounds__(256) k_split_rows_f64(Operand<T> a, int64_t m,
     uint64_t w[NW];
     const int sign = window_of<T, NW>(a, i < m && p < k, i + p * a.ld, Erow, w);
     for (int t = 1; t <= s; ++t) {
-        const double d = (double)digit_of_rt<NW>(w, t, beta);
-        sd[((t - 1) * TI + ri) * TP + pi] = digit_value<DT>(sign < 0 ? -d : d);
+        sd[((t - 1) * TI + ri) * TP + pi] = digit_value<DT>(digit_of_rt<NW>(w, t, beta), sign);
     }
     __syncthreads();
     const int total = s * TI * TP;
@@ -799,8 +814,7 @@ __global__ void __launch_bounds__(256) k_split_cols_f64(Operand<T> b, int64_t k,
     uint64_t w[NW];
     const int sign = window_of<T, NW>(b, j < n && p < k, p + j * b.ld, Ecol, w);
     for (int t = 1; t <= s; ++t) {
-        const double d = (double)digit_of_rt<NW>(w, t, beta);
-        dig[((size_t)(t - 1) * np + j) * kp + p] = digit_value<DT>(sign < 0 ? -d : d);
+        dig[((size_t)(t - 1) * np + j) * kp + p] = digit_value<DT>(digit_of_rt<NW>(w, t, beta), sign);
     }
 }
 
@@ -839,12 +853,16 @@ template <typename T, int FORM, int NW, int Q>
 static cudaError_t digits_b1_q(const SplitArgs& g, cudaStream_t st) {
     Operand<T> a = make_op<T>(g.A, g.q, g.lda);
     Operand<T> b = make_op<T>(g.B, g.q, g.ldb);
-    dim3 gr((unsigned)(g.mp / 32), (unsigned)(g.kp / 64));
-    size_t sm = (size_t)g.s * 32 * 16 * 4;
-    auto kr = k_split_rows_b1<T, FORM, NW, Q>;
-    cudaError_t e = cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    kr<<<gr, 256, sm, st>>>(a, g.m, g.k, g.E, (uint8_t*)g.Adig, g.mp, g.kp, g.s);
+    cudaError_t e = cudaSuccess;
+    if (g.parts != 2) {
+        dim3 gr((unsigned)(g.mp / 32), (unsigned)(g.kp / 64));
+        size_t sm = (size_t)g.s * 32 * 16 * 4;
+        auto kr = k_split_rows_b1<T, FORM, NW, Q>;
+        e = cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        kr<<<gr, 256, sm, st>>>(a, g.m, g.k, g.E, (uint8_t*)g.Adig, g.mp, g.kp, g.s);
+    }
+    if (g.parts == 1) return cudaGetLastError();
     if constexpr ((FORM == OZMP_FORM_FP8 || FORM == OZMP_FORM_FP8_BAL) && Q > 0) {
         const size_t fsm = cols_fused_smem(g);
         if (fsm) {
@@ -853,10 +871,11 @@ static cudaError_t digits_b1_q(const SplitArgs& g, cudaStream_t st) {
             if (e != cudaSuccess) return e;
             const long long polls = g.wait_limit > 0 ? g.wait_limit : colbulk::WAIT_POLLS;
             kf<<<(unsigned)g.np, 256, fsm, st>>>(b, g.k, g.n, g.F, g.status, (uint8_t*)g.Bdig, g.np, g.kp, g.s,
-                                                 polls, g.inject_stall);
+                                                 polls, g.inject_stall, g.rowBf);
             return cudaGetLastError();
         }
     }
+    if (g.rowBf) return cudaErrorInvalidValue;   // only the one-pass column kernel sums the norms
     int64_t tot = (g.kp / 4) * g.np;
     k_split_cols_b1<T, FORM, NW, Q><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(b, g.k, g.n, g.F,
                                                                                  (uint8_t*)g.Bdig, g.np, g.kp, g.s);
