@@ -818,6 +818,97 @@ __global__ void __launch_bounds__(256) k_split_cols_f64(Operand<T> b, int64_t k,
     }
 }
 
+// Binary16 digits of a width BETA known at compile time (5, 6 or 7 bits:
+// the widths of 259 <= k <= 17459), four consecutive k of one row or column
+// per thread as in the 1-byte digit kernels: digit t of element e is a fixed
+// bit field of its exact window, converted from the integer to binary16
+// directly (exact: |d| < 2^BETA), a zero digit +0.
+template <int NW, int BETA>
+__device__ __forceinline__ uint2 halves4(const uint64_t (&w)[4][NW], const int (&sg)[4], int t) {
+    uint32_t h[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int d = (int)digit_of<NW, BETA>(w[e], t);
+        h[e] = (uint32_t)__half_as_ushort(__int2half_rn(sg[e] < 0 ? -d : d));
+    }
+    return make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+}
+
+// Rows of A -> Adig[(t * mp + i) * kp + p] (binary16): tile 32 rows x 64
+// columns, thread (row, quad) takes 4 consecutive columns of one row (two
+// quads a thread); a slice's 4 digits go to shared memory as 8 bytes, quad qd
+// of tile row r at position qd ^ (r & 15) of its 16 (a warp's 32 rows then
+// fall on 16 distinct 8-byte slots: two wavefronts, the least for 256 bytes),
+// and the tile is written K-contiguous in 16-byte pieces.
+template <typename T, int NW, int Q, int BETA>
+__global__ void __launch_bounds__(256) k_split_rows_h(Operand<T> a, int64_t m, int64_t k, const int32_t* E,
+                                                      __half* dig, int64_t mp, int64_t kp, int s) {
+    constexpr int TI = 32, TP = 64, MAXS = (64 * NW - 65) / BETA;
+    extern __shared__ __align__(16) uint2 sq[];   // [s][TI][16]
+    const int64_t i0 = (int64_t)blockIdx.x * TI, p0 = (int64_t)blockIdx.y * TP;
+    const int ri = threadIdx.x & 31;
+    const int64_t i = i0 + ri;
+    const int Erow = (i < m) ? E[i] : OZMP_EXP_ZERO;
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        const int qd = (threadIdx.x >> 5) + 8 * h;
+        T v[4][4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int64_t p = p0 + 4 * qd + e;
+            load_raw<T>(a, Q, i < m && p < k, i + p * a.ld, v[e]);
+        }
+        uint64_t w[4][NW];
+        int sg[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) sg[e] = window_loaded<T, NW, Q>(v[e], Q, Erow, w[e]);
+        uint2* const dst = sq + ri * 16 + (qd ^ (ri & 15));
+#pragma unroll
+        for (int t = 1; t <= MAXS; ++t) {
+            if (t > s) break;
+            dst[(t - 1) * TI * 16] = halves4<NW, BETA>(w, sg, t);
+        }
+    }
+    __syncthreads();
+    const int total = s * TI * 8;   // 16-byte pieces: 8 a tile row and slice
+    for (int x = threadIdx.x; x < total; x += 256) {
+        const int t = x / (TI * 8), r = (x >> 3) % TI, c8 = x & 7;
+        const uint2* row = sq + (t * TI + r) * 16;
+        const int z = r & 15;
+        const uint2 lo = row[(2 * c8) ^ z], hi = row[(2 * c8 + 1) ^ z];
+        *reinterpret_cast<uint4*>(dig + ((size_t)t * mp + (i0 + r)) * kp + p0 + 8 * c8) =
+            make_uint4(lo.x, lo.y, hi.x, hi.y);
+    }
+}
+
+// Columns of B -> Bdig[(t * np + j) * kp + p] (binary16): thread g takes 4
+// consecutive k of column g / (kp / 4), one 8-byte store per slice (the
+// padding of the workspace gets zero digits).
+template <typename T, int NW, int Q, int BETA>
+__global__ void __launch_bounds__(256) k_split_cols_h(Operand<T> b, int64_t k, int64_t n, const int32_t* F,
+                                                      __half* dig, int64_t np, int64_t kp, int s) {
+    constexpr int MAXS = (64 * NW - 65) / BETA;
+    const int64_t quads = kp / 4;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= quads * np) return;
+    const int64_t j = g / quads, p0 = (g % quads) * 4;
+    const int Ecol = (j < n) ? F[j] : OZMP_EXP_ZERO;
+    T v[4][4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) load_raw<T>(b, Q, j < n && p0 + e < k, p0 + e + j * b.ld, v[e]);
+    uint64_t w[4][NW];
+    int sg[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) sg[e] = window_loaded<T, NW, Q>(v[e], Q, Ecol, w[e]);
+    uint2* const base = reinterpret_cast<uint2*>(dig + (size_t)j * kp + p0);
+    const size_t slice = (size_t)np * kp / 4;   // uint2 units
+#pragma unroll
+    for (int t = 1; t <= MAXS; ++t) {
+        if (t > s) break;
+        base[(size_t)(t - 1) * slice] = halves4<NW, BETA>(w, sg, t);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -916,6 +1007,23 @@ static cudaError_t digits_f64(const SplitArgs& g, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// binary16 digits of compile-time width BETA (k_split_rows_h, k_split_cols_h)
+template <typename T, int NW, int Q, int BETA>
+static cudaError_t digits_h(const SplitArgs& g, cudaStream_t st) {
+    Operand<T> a = make_op<T>(g.A, g.q, g.lda);
+    Operand<T> b = make_op<T>(g.B, g.q, g.ldb);
+    const size_t sm = (size_t)g.s * 32 * 16 * sizeof(uint2);
+    auto kr = k_split_rows_h<T, NW, Q, BETA>;
+    cudaError_t e = cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kr<<<dim3((unsigned)(g.mp / 32), (unsigned)(g.kp / 64)), 256, sm, st>>>(a, g.m, g.k, g.E, (__half*)g.Adig, g.mp,
+                                                                          g.kp, g.s);
+    const int64_t tot = (g.kp / 4) * g.np;
+    k_split_cols_h<T, NW, Q, BETA><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(b, g.k, g.n, g.F, (__half*)g.Bdig,
+                                                                                  g.np, g.kp, g.s);
+    return cudaGetLastError();
+}
+
 // digits of both operands for one form (the padded region gets zero digits)
 template <typename T, int FORM>
 static cudaError_t digits_impl(const SplitArgs& g, cudaStream_t st) {
@@ -924,7 +1032,15 @@ static cudaError_t digits_impl(const SplitArgs& g, cudaStream_t st) {
         if (nw <= 4) return digits_f64<T, 4>(g, st);
         return digits_f64<T, 7>(g, st);
     } else if constexpr (FORM == OZMP_FORM_FP16) {
-        if (nw <= 4) return digits_f64<T, 4, __half>(g, st);
+        if (nw <= 4) {
+            // the common widths and component counts: four digits a thread
+            // with the width known at compile time (DD, TS)
+            constexpr int QH = sizeof(T) == 8 ? 2 : 3;
+            if (g.q == QH && g.beta == 5) return digits_h<T, 4, QH, 5>(g, st);
+            if (g.q == QH && g.beta == 6) return digits_h<T, 4, QH, 6>(g, st);
+            if (g.q == QH && g.beta == 7) return digits_h<T, 4, QH, 7>(g, st);
+            return digits_f64<T, 4, __half>(g, st);
+        }
         return digits_f64<T, 7, __half>(g, st);
     } else {
         if (nw <= 4) return digits_b1<T, FORM, 4>(g, st);

@@ -70,6 +70,16 @@ def test_split_bit_exact(prec, form):
     _split_check(prec, form, 150, 140, 130, phi=1.0, seed=1, nslices={"fp64": 6, "fp16": 10}.get(form, 14))
 
 
+@pytest.mark.parametrize("k", [300, 1100, 4300])
+@pytest.mark.parametrize("prec", ["dd", "ts"])
+def test_split_bit_exact_binary16_widths(prec, k):
+    # binary16 digits of 7, 6 and 5 bits (the widths of k = 300, 1100, 4300),
+    # split four elements a thread with the width fixed at compile time, on
+    # ragged row and column tiles; the automatic slice count
+    p = _split_check(prec, "fp16", 70, 90, k, phi=1.0, seed=2, nslices=0)[0]
+    assert p.info.beta == {300: 7, 1100: 6, 4300: 5}[k]
+
+
 @pytest.mark.parametrize("form,s", [("fp8", 64), ("fp8", 65), ("fp8bal", 63), ("fp8bal", 1)])
 def test_split_widest_register_windows(form, s):
     # the register splitter writes up to 64 e4m3 slices (63 balanced ones,
@@ -174,7 +184,7 @@ CASES = [("dd", "fp8", 130, 140, 150), ("dd", "fp8mma", 140, 130, 150), ("dd", "
          ("dd", "fp8bal", 130, 140, 150), ("dd", "fp8bal", 300, 520, 260), ("td", "fp8bal", 130, 70, 100),
          ("qd", "fp8bal", 70, 130, 64), ("ts", "fp8bal", 150, 140, 130),
          ("dd", "fp16", 300, 520, 260), ("td", "fp16", 130, 70, 100), ("qd", "fp16", 70, 130, 64),
-         ("ts", "fp16", 150, 140, 130)]
+         ("ts", "fp16", 150, 140, 130), ("ts", "fp16", 40, 36, 1100), ("dd", "fp16", 40, 36, 4300)]
 
 
 @pytest.mark.parametrize("prec,form,m,n,k", CASES)
