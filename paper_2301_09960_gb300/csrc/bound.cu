@@ -210,56 +210,85 @@ __global__ void __launch_bounds__(256) k_bound_check(const T* C0, int64_t m, int
 }
 
 // GE, GF, SE, SF from the exponents, est from the unscaled norms of the
-// exponent pass, and the slice count (-1: an exponent beyond the raw range)
-__global__ void __launch_bounds__(1024) k_bound_choose_raw(const int32_t* E, int64_t m, const int32_t* F, int64_t n,
+// exponent pass, and the slice count (-1: an exponent beyond the raw range).
+// One block; its latency is a fixed cost of every product, so the loads go
+// in two passes (maxima and est, then SE and SF) and each pass's values are
+// reduced together: warp shuffles, one shared-memory round, warp 0.
+__global__ void __launch_bounds__(256) k_bound_choose_raw(const int32_t* E, int64_t m, const int32_t* F, int64_t n,
                                                            const double* colA, const double* rowB,
                                                            const float* rowBf, int64_t k, BoundStats* st,
                                                            BoundForm f, int s_lo, int s_hi) {
-    __shared__ int shi[32];
-    __shared__ double shd[32];
+    __shared__ int shi[2][32];
+    __shared__ double shd[3][32];
+    __shared__ double bc[3];   // SE, SF, est to every thread
+    __shared__ int bg[2];      // GE, GF to every thread
+    __shared__ int best;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // pass 1: the largest exponents and est = sum_p colA[p] rowB[p]
     int ge = OZMP_EXP_ZERO, gf = OZMP_EXP_ZERO;
+    double v = 0.0;
     for (int64_t i = threadIdx.x; i < m; i += blockDim.x) ge = max(ge, E[i]);
     for (int64_t j = threadIdx.x; j < n; j += blockDim.x) gf = max(gf, F[j]);
-    ge = block_max(ge, shi);
-    gf = block_max(gf, shi);
-    double se = 0.0, sf = 0.0, v = 0.0;
+    for (int64_t p = threadIdx.x; p < k; p += blockDim.x) v += colA[p] * (rowBf ? (double)rowBf[p] : rowB[p]);
+    ge = warp_max(ge);
+    gf = warp_max(gf);
+    v = warp_sum(v);
+    if (lane == 0) {
+        shi[0][wid] = ge;
+        shi[1][wid] = gf;
+        shd[2][wid] = v;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        ge = lane < nw ? shi[0][lane] : OZMP_EXP_ZERO;
+        gf = lane < nw ? shi[1][lane] : OZMP_EXP_ZERO;
+        v = lane < nw ? shd[2][lane] : 0.0;
+        ge = warp_max(ge);
+        gf = warp_max(gf);
+        v = warp_sum(v);
+        if (lane == 0) {
+            bg[0] = ge;
+            bg[1] = gf;
+            bc[2] = v;
+            best = s_hi;
+        }
+    }
+    __syncthreads();
+    ge = bg[0];
+    gf = bg[1];
+    v = bc[2];
+    // pass 2: SE = sum_i 4^(E_i - GE), SF = sum_j 4^(F_j - GF)
+    double se = 0.0, sf = 0.0;
     if (ge != OZMP_EXP_ZERO)
         for (int64_t i = threadIdx.x; i < m; i += blockDim.x)
             if (E[i] != OZMP_EXP_ZERO) se += pow2(2 * (E[i] - ge));
     if (gf != OZMP_EXP_ZERO)
         for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
             if (F[j] != OZMP_EXP_ZERO) sf += pow2(2 * (F[j] - gf));
-    for (int64_t p0 = threadIdx.x; p0 < k; p0 += 4 * (int64_t)blockDim.x) {
-        double a4[4], b4[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t p = p0 + (int64_t)u * blockDim.x;
-            a4[u] = p < k ? colA[p] : 0.0;
-            b4[u] = p < k ? (rowBf ? (double)rowBf[p] : rowB[p]) : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) v += a4[u] * b4[u];
+    se = warp_sum(se);
+    sf = warp_sum(sf);
+    if (lane == 0) {
+        shd[0][wid] = se;
+        shd[1][wid] = sf;
     }
-    se = block_sum(se, shd);
     __syncthreads();
-    sf = block_sum(sf, shd);
-    __syncthreads();
-    v = block_sum(v, shd);
-    __shared__ double bc[3];   // SE, SF, est to every thread
-    __shared__ int best;
-    if (threadIdx.x == 0) {
-        bc[0] = se;
-        bc[1] = sf;
-        bc[2] = v;
-        best = s_hi;
+    const bool zero = (ge == OZMP_EXP_ZERO || gf == OZMP_EXP_ZERO || !(v > 0.0));
+    const bool raw = !(ge > BOUND_RAW_EXP || ge < -BOUND_RAW_EXP || gf > BOUND_RAW_EXP || gf < -BOUND_RAW_EXP);
+    __shared__ double blest;
+    if (wid == 0) {
+        se = warp_sum(lane < nw ? shd[0][lane] : 0.0);
+        sf = warp_sum(lane < nw ? shd[1][lane] : 0.0);
+        if (lane == 0) {
+            bc[0] = se;
+            bc[1] = sf;
+            // log2 of est scaled by 4^-(GE + GF), once (binary64 is slow on this GPU)
+            blest = zero ? 0.0 : log2(v) - 2.0 * (double)(ge + gf);
+        }
     }
     __syncthreads();
     se = bc[0];
     sf = bc[1];
-    v = bc[2];
-    const bool zero = (ge == OZMP_EXP_ZERO || gf == OZMP_EXP_ZERO || !(v > 0.0));
-    const bool raw = !(ge > BOUND_RAW_EXP || ge < -BOUND_RAW_EXP || gf > BOUND_RAW_EXP || gf < -BOUND_RAW_EXP);
-    const double lest = zero ? 0.0 : log2(v) - 2.0 * (double)(ge + gf);   // log2 of est scaled by 4^-(GE + GF)
+    const double lest = blest;
     // candidate s_lo + x in thread x (the binary64 logarithms are slow one after another)
     const int t = s_lo + (int)threadIdx.x;
     if (!zero && raw && t <= s_hi && bound_log2(f, t, se, sf) <= -(double)(f.target + 1) + 0.5 * lest)
@@ -314,7 +343,7 @@ cudaError_t launch_bound_choose(const void* const* A, int64_t lda, const void* c
 cudaError_t launch_bound_choose_raw(const int32_t* E, int64_t m, const int32_t* F, int64_t n, const double* colA,
                                     const double* rowB, const float* rowBf, int64_t k, BoundStats* st,
                                     const BoundForm& f, int s_lo, int s_hi, cudaStream_t stream) {
-    k_bound_choose_raw<<<1, 1024, 0, stream>>>(E, m, F, n, colA, rowB, rowBf, (m > 0 && n > 0) ? k : 0, st, f, s_lo,
+    k_bound_choose_raw<<<1, 256, 0, stream>>>(E, m, F, n, colA, rowB, rowBf, (m > 0 && n > 0) ? k : 0, st, f, s_lo,
                                                s_hi);
     return cudaGetLastError();
 }

@@ -130,7 +130,8 @@ cudaError_t launch_bound_choose(const void* const* A, int64_t lda, const void* c
 // accumulators too); st->s_needed = -1 when an exponent lies beyond
 // BOUND_RAW_EXP (then the scaled launches above decide).  B's row norms come
 // from rowBf (binary32, summed by the one-pass column digit kernel) when it is
-// set, else from rowB.  s_hi - s_lo < 1024.
+// set, else from rowB.  s_hi - s_lo < 256 (one block of 256 threads, a candidate
+// count each).
 cudaError_t launch_bound_choose_raw(const int32_t* E, int64_t m, const int32_t* F, int64_t n, const double* colA,
                                     const double* rowB, const float* rowBf, int64_t k, BoundStats* st,
                                     const BoundForm& f, int s_lo, int s_hi, cudaStream_t stream);
