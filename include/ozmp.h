@@ -42,7 +42,8 @@
  * Every product of a plan is followed by an a-posteriori check of its error
  * bound (OZMP_ERR_ACCURACY when the bound does not certify the target).
  * Calls are stream-ordered and asynchronous, except that a plan with a
- * data-dependent slice count (nslices = 0) waits for its exponent pass.
+ * data-dependent slice count (nslices = 0) waits for the passes that reduce
+ * its exponents.
  */
 #ifndef OZMP_H
 #define OZMP_H
@@ -136,7 +137,10 @@ typedef struct {
  *   times an estimate of ||C||_F (from the column norms of A and the row
  *   norms of B) -- target 2^-100 DD, 2^-150 TD, 2^-200 QD, 2^(-50 q) for q
  *   binary64 components, 2^-66 TS.  That choice is read back to the host, so
- *   the execution waits for the exponent pass.  The plan reserves the
+ *   the execution waits for the passes that reduce the exponents (for 1-byte
+ *   e4m3 digits whose columns of B are 16-byte aligned and at most 112 KB,
+ *   B's pass also writes B's digits for the previous count; A's digits are
+ *   queued before the wait).  The plan reserves the
  *   workspace of the slice counts within about 50 bits of the count
  *   ceil((target + log2 k + 16) / beta) (for s outside, the nearest end is
  *   used); ozmp_plan_get_info reports the count of the last execution.
