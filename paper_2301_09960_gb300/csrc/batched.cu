@@ -673,7 +673,7 @@ extern "C" ozmp_status ozmp_gemm_batched(const ozmp_problem* probs, int count, o
                     cudaMemsetAsync((char*)b->ws + b->off_split, 0, b->split_bytes, cs);
                 if (b->grid > 0) {
                     tc::Sched sc;
-                    memset(&sc, 0, sizeof(sc));   // no lockstep, no dynamic feed
+                    memset(&sc, 0, sizeof(sc));   // no lockstep, no dynamic feed, one diagonal at a time
                     sc.probs = (const tc::Prob*)((char*)b->meta + b->off_probs);
                     sc.maps = (const CUtensorMap*)((char*)b->meta + b->off_maps);
                     sc.items = (const tc::WorkItem*)((char*)b->meta + b->off_items);

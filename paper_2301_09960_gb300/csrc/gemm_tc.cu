@@ -143,17 +143,18 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                 const int jb = (int)it.j0 + (CG == 2 ? (int)rank * (BN / 2) : 0);
                 const bool whole = it.pa == 0 && it.pb == p.s * (p.s + 1) / 2;
                 if (lock && !whole && !gone) { atomicAdd(sc.retired, 1); gone = true; }
-                Walk w = Walk::at(it.dhi, it.pa);
+                PairWalk w;
+                w.start(it.dhi, it.dlo, p.ppd, it.pa, it.pb, sc.snake, 0);   // (the accumulators do not matter here)
                 for (int pi = it.pa; ok && pi < it.pb; ++pi) {
+                    const PairStep ps = w.step();
                     if (lock && whole && P >= sc.lock_w && P - sc.lock_w < sc.lock_n) {
                         // soft: after LOCK_POLLS polls the walk goes on regardless
                         const volatile int* dp = sc.step_done + (P - sc.lock_w);
                         const volatile int* rp = sc.retired;
                         for (int x = 0; x < LOCK_POLLS && *dp + *rp < ncl; ++x) __nanosleep(128);
                     }
-                    const int u = w.d - w.t;
-                    const int ya = (w.t - 1) * (int)p.mp + (int)it.i0;
-                    const int yb = (u - 1) * (int)p.np + jb;
+                    const int ya = (ps.t - 1) * (int)p.mp + (int)it.i0;
+                    const int yb = (ps.u - 1) * (int)p.np + jb;
                     for (int kc = 0; kc < it.KT; ++kc, ++n) {
                         const int st = (int)(n % NS);
                         const unsigned ph = (unsigned)((n / NS) & 1);
@@ -174,7 +175,6 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                         if (P < sc.lock_n) atomicAdd(sc.step_done + P, 1);
                         ++P;
                     }
-                    w.next_pair();
                 }
             }
             if (lock && !gone) atomicAdd(sc.retired, 1);
@@ -197,8 +197,9 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
             auto issue = [&](auto f16_tag) {
                 constexpr bool F16 = decltype(f16_tag)::value;
                 long long n = 0;
-                int buf = 0, uses[2] = {0, 0};
-                bool ok = mbar_wait<CG == 2>(&acce[0], 1u, abort_flag, WL);     // first use of buffer 0
+                int uses[2] = {0, 0};   // groups closed so far in each accumulator
+                int nb = 0;             // accumulator of the next item's first pair
+                bool ok = true;
                 for (int k = 0; ok; ++k) {
                     const int idx = take(k, false, false);
                     if (idx == -2) { ok = false; break; }
@@ -207,10 +208,19 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                     item_at<CG>(sc, &single, &tmA, &tmB, idx, it, rank);
                     const Prob p = *it.p;
                     const uint32_t idesc = idesc_e4m3(BM * CG, it.bn);
-                    Walk w = Walk::at(it.dhi, it.pa);
-                    int since = 0;
-                    bool fresh = true;
+                    PairWalk w;
+                    w.start(it.dhi, it.dlo, p.ppd, it.pa, it.pb, sc.snake, nb);
                     for (int pi = it.pa; ok && pi < it.pb; ++pi) {
+                        const PairStep ps = w.step();
+                        const int buf = ps.buf;
+                        nb = buf ^ 1;
+                        // a group's first MMA waits until the epilogues have released the
+                        // accumulator's previous group (the k-th use waits for the (k-1)-th release)
+                        if (ps.open && !mbar_wait<CG == 2>(&acce[buf], (unsigned)((uses[buf] & 1) ^ 1), abort_flag, WL)) {
+                            ok = false;
+                            break;
+                        }
+                        bool fresh = ps.open;
                         const uint32_t dcol = tmem + (uint32_t)(buf * BN);
                         for (int kc = 0; kc < it.KT; ++kc, ++n) {
                             const int st = (int)(n % NS);
@@ -237,22 +247,11 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                             else mma_commit(&empty[st]);
                         }
                         if (!ok) break;
-                        ++since;
-                        const bool diag_end = (w.t == w.d - 1);
-                        if (since == p.ppd || diag_end || pi == it.pb - 1) {
+                        if (ps.close) {
                             if (CG == 2) mma_commit_pair(&accf[buf]);
                             else mma_commit(&accf[buf]);
                             uses[buf]++;
-                            buf ^= 1;
-                            since = 0;
-                            fresh = true;
-                            // the k-th use of a buffer waits for the epilogues' (k-1)-th release
-                            if (!mbar_wait<CG == 2>(&acce[buf], (unsigned)((uses[buf] & 1) ^ 1), abort_flag, WL)) {
-                                ok = false;
-                                break;
-                            }
                         }
-                        w.next_pair();
                     }
                 }
                 if (!ok) raise_abort();
@@ -270,7 +269,8 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
         // ------------------------------------------------------------ epilogue
         const int quarter = warp & 3;
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
-        int ev = 0;
+        int drains[2] = {0, 0};   // groups drained so far from each accumulator
+        int nb = 0;               // accumulator of the next item's first pair
         bool ok = true;
         for (int k = 0; ok; ++k) {
             const int idx = take(k, false, true);
@@ -289,25 +289,26 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
             // split tiles: limb l of tile column jj, row ii at sbase[l * sstride + jj * BM + ii]
             const size_t sstride = (size_t)it.bn * BM;
             int64_t* sbase = split ? p.sacc + (size_t)slot * nl * sstride : nullptr;
-            Walk w = Walk::at(it.dhi, it.pa);
-            int since = 0;
-            int top_li = -1;   // highest limb stored so far for this tile (whole tiles)
+            PairWalk w;
+            w.start(it.dhi, it.dlo, p.ppd, it.pa, it.pb, sc.snake, nb);
+            // limbs of this tile written so far (whole tiles): bit l set once limb l has
+            // been stored, so that a drain stores a limb's first value and adds to it after
+            uint64_t touched = 0;
             for (int pi = it.pa; ok && pi < it.pb; ++pi) {
-                ++since;
-                const bool diag_end = (w.t == w.d - 1);
-                if (since == p.ppd || diag_end || pi == it.pb - 1) {
-                    since = 0;
+                const PairStep ps = w.step();
+                nb = ps.buf ^ 1;
+                if (ps.close) {
                     // the last drain rounds the tile into C unless a separate pass does
                     const bool last = (pi == it.pb - 1) && !p.defer;
-                    const int buf = ev & 1;
-                    const unsigned par = (unsigned)((ev >> 1) & 1);
-                    ++ev;
+                    const int buf = ps.buf;
+                    const unsigned par = (unsigned)(drains[buf] & 1);
+                    ++drains[buf];
                     int got = 0;
                     if (lane == 0) got = mbar_wait<CG == 2>(&accf[buf], par, abort_flag, WL) ? 1 : 0;
                     if (!__shfl_sync(0xffffffffu, got, 0)) { ok = false; break; }
                     __syncwarp();
                     tc_fence_after();
-                    const int fsh = p.d_only ? 0 : p.beta * (p.s + 1 - w.d);
+                    const int fsh = p.d_only ? 0 : p.beta * (p.s + 1 - ps.d);
                     const int li = fsh >> 4, off = fsh & 15;
                     const int nchunk = it.bn / 32;
 #pragma unroll 1
@@ -333,16 +334,18 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                                 atomicAdd(lp + (size_t)x * BM, (unsigned long long)((uint64_t)v << off));
                             }
                         } else if (last) {
-                            // limbs 0 .. top_li hold data; li may open one more (li == top_li + 1)
+                            // the limbs in `touched` hold data; this drain's adds into limb li
+                            const int nlt = touched ? 64 - __clzll((long long)touched) : 0;
 #pragma unroll 1
                             for (int x = 0; x < 32; ++x) {
                                 const int64_t v = (int64_t)__float2int_rn(__uint_as_float(r[x]));
-                                finish_dispatch(g, top_li + 1, p.acc, plane, (size_t)(jb + x) * p.mp + i, i, jb + x,
-                                                (int64_t)((uint64_t)v << off), li, top_li < 0);
+                                finish_dispatch(g, nlt, p.acc, plane, (size_t)(jb + x) * p.mp + i, i, jb + x,
+                                                (int64_t)((uint64_t)v << off), li, touched == 0, touched);
                             }
-                        } else if (li > top_li) {
-                            // first touch of this limb: store (limb indices only grow along the walk,
-                            // so every limb below it has been stored already and none above is read)
+                        } else if (!((touched >> li) & 1)) {
+                            // first touch of this limb: store (in the snake a drain may reach a
+                            // limb before the drain of the diagonal above it does, so the
+                            // written limbs are tracked one by one)
 #pragma unroll
                             for (int x = 0; x < 32; ++x) {
                                 const int64_t v = (int64_t)__float2int_rn(__uint_as_float(r[x]));
@@ -359,7 +362,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                             }
                         }
                     }
-                    if (li > top_li) top_li = li;
+                    touched |= 1ull << li;
                     if (split && last) {
                         // the last chunk of the tile to finish rounds it: publish this chunk's
                         // additions, count it, and let the finisher read every chunk's
@@ -377,7 +380,6 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const Sched sc, const __grid_
                         asm volatile("bar.sync 1, 128;\n" ::: "memory");
                     }
                 }
-                w.next_pair();
             }
         }
         if (!ok) raise_abort();
@@ -602,6 +604,7 @@ cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t st) {
     sc.wait_limit = g.wait_limit;
     sc.inject_stall = g.inject_stall;
     sc.kind = kind;
+    sc.snake = g.tc_snake;
     sc.step_done = (sc.counter && g.lock_w > 0) ? g.step_done : nullptr;
     sc.retired = g.retired;
     sc.lock_w = g.lock_w;

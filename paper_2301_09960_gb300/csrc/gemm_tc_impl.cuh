@@ -5,7 +5,9 @@
 //
 // Paper, Sec. 3, Algorithm 1: C_{alpha beta} := A_alpha B_beta over the pair
 // triangle, then the L-bit sum.  One CTA owns a 128 x 256 tile of C and walks
-// the triangle by anti-diagonal d = s+1 .. 2 exactly as the mma.sync kernels.
+// the triangle in the order of walk.h: one anti-diagonal at a time,
+// d = s+1 .. 2, as the mma.sync kernels (or, OZMP_TC_WALK=1, two
+// anti-diagonals interleaved so that consecutive pairs share an operand slice).
 //
 // Roles (192 threads):
 //   warp 0      TMA producer: 128x128-byte A tile + 256x128-byte B tile per
@@ -28,6 +30,7 @@
 #include <cudaTypedefs.h>
 #include "kernels.h"
 #include "ozmp_internal.cuh"
+#include "walk.h"
 
 namespace ozmp {
 namespace tc {
@@ -229,39 +232,26 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
-// walk of the pair triangle shared by the three roles
-struct Walk {
-    int d, t;
-    __device__ __forceinline__ bool next_pair() {   // advance; false when past the end
-        if (++t == d) { --d; t = 1; }
-        return true;
-    }
-    // position of pair index `idx` of the walk starting at diagonal dhi
-    __device__ __forceinline__ static Walk at(int dhi, int idx) {
-        Walk w{dhi, 1};
-        while (idx >= w.d - 1) { idx -= w.d - 1; --w.d; }
-        w.t = 1 + idx;
-        return w;
-    }
-};
-
 // Limb accumulator of one element: limbs 0 .. nl-1 of int64, limb l weighs
 // 2^(16 l), limb l of the element at base[l * lstride + idx].  `x` is added
 // to limb `li` (the last drain's contribution when it is fused here);
-// `zero` skips the loads (first and last drain of a tile coincide).  The
+// `zero` skips the loads (first and last drain of a tile coincide), and only
+// the limbs l < nl whose bit is set in `have` are loaded (the others hold no
+// data yet: the fused last drain passes the limbs its tile has written).  The
 // limbs are streamed through one carry chain into a two's complement value
 // of 64 NW bits, rounded canonically into C(i, j) (or written to T in the
 // diagnostic mode).  Returns the first component written (0 otherwise).
 template <int NW>
 __device__ __forceinline__ double finish_element(const GemmArgs& g, int nl, const int64_t* base, size_t lstride,
-                                                 size_t idx, int64_t i, int64_t j, int64_t x, int li, bool zero) {
+                                                 size_t idx, int64_t i, int64_t j, int64_t x, int li, bool zero,
+                                                 uint64_t have = ~0ull) {
     uint64_t w[NW];
 #pragma unroll
     for (int x2 = 0; x2 < NW; ++x2) w[x2] = 0;
     int64_t carry = 0;
 #pragma unroll
     for (int l = 0; l < 4 * NW; ++l) {
-        int64_t t = (!zero && l < nl) ? __ldcg(base + l * lstride + idx) : 0;   // |limb| < 2^48
+        int64_t t = (!zero && l < nl && ((have >> l) & 1)) ? __ldcg(base + l * lstride + idx) : 0;   // |limb| < 2^48
         if (l == li) t += x;
         t += carry;                                // |carry| < 2^48
         w[l >> 2] |= ((uint64_t)t & 0xffffull) << (16 * (l & 3));
@@ -296,14 +286,15 @@ __device__ __forceinline__ double finish_element(const GemmArgs& g, int nl, cons
 }
 
 __device__ __forceinline__ void finish_dispatch(const GemmArgs& g, int nl, const int64_t* base, size_t lstride,
-                                                size_t idx, int64_t i, int64_t j, int64_t x, int li, bool zero) {
+                                                size_t idx, int64_t i, int64_t j, int64_t x, int li, bool zero,
+                                                uint64_t have = ~0ull) {
     switch (g.acc_words) {
-        case 2: finish_element<2>(g, nl, base, lstride, idx, i, j, x, li, zero); break;
-        case 3: finish_element<3>(g, nl, base, lstride, idx, i, j, x, li, zero); break;
-        case 4: finish_element<4>(g, nl, base, lstride, idx, i, j, x, li, zero); break;
-        case 5: finish_element<5>(g, nl, base, lstride, idx, i, j, x, li, zero); break;
-        case 6: finish_element<6>(g, nl, base, lstride, idx, i, j, x, li, zero); break;
-        default: finish_element<7>(g, nl, base, lstride, idx, i, j, x, li, zero); break;
+        case 2: finish_element<2>(g, nl, base, lstride, idx, i, j, x, li, zero, have); break;
+        case 3: finish_element<3>(g, nl, base, lstride, idx, i, j, x, li, zero, have); break;
+        case 4: finish_element<4>(g, nl, base, lstride, idx, i, j, x, li, zero, have); break;
+        case 5: finish_element<5>(g, nl, base, lstride, idx, i, j, x, li, zero, have); break;
+        case 6: finish_element<6>(g, nl, base, lstride, idx, i, j, x, li, zero, have); break;
+        default: finish_element<7>(g, nl, base, lstride, idx, i, j, x, li, zero, have); break;
     }
 }
 
@@ -365,6 +356,7 @@ struct Sched {
     long long wait_limit;      // polls before a wait gives up (0: WAIT_LIMIT)
     int inject_stall;          // test hook: never load the first stage of each CTA's first item
     int kind;                  // digit type of every problem of the launch (Prob::kind)
+    int snake;                 // pair order (walk.h): 1 the snake, 0 one diagonal at a time
     // loose lockstep of the clusters' pair walks (null: off): step_done[P]
     // counts the clusters that issued their P-th whole-tile pair, retired the
     // clusters without whole tiles left; before pair P a leader waits a

@@ -67,6 +67,7 @@ struct GemmArgs {
     int sched_nitems;
     size_t split_bytes;        // bytes of sacc + cnt + counter
     int tc_cg;                 // 2: CTA-pair tiles (256 x 256, cta_group::2); else one CTA per tile
+    int tc_snake;              // tcgen05 pair order (walk.h): 1 two diagonals interleaved, 0 one at a time
     // loose lockstep of the clusters' pair walks (lock_w > 0, dynamic feed):
     // step counters and the retired count, zeroed with the split region
     int* step_done;

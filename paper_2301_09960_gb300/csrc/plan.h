@@ -53,8 +53,9 @@ struct ozmp_plan_s {
     int s_lo, s_cap;   // adaptive plans: the slice counts the reserved workspace holds
     size_t ws_cap;     // bytes of the current workspace
     // schedule knobs, read from the environment once (OZMP_TC_PAIR, OZMP_TC_DYNAMIC,
-    // OZMP_TC_GROUP, OZMP_TC_MAX_CHUNKS) and kept when the plan is re-made for another s
-    int env_read, env_pair_off, env_static, env_group, env_maxc, env_lock;
+    // OZMP_TC_GROUP, OZMP_TC_MAX_CHUNKS, OZMP_TC_LOCKSTEP, OZMP_TC_WALK) and kept
+    // when the plan is re-made for another s
+    int env_read, env_pair_off, env_static, env_group, env_maxc, env_lock, env_walk;
     // adaptive plans: pinned host word of the chosen s and the event after its copy
     int* host_s;
     cudaEvent_t ev_s;
@@ -294,6 +295,7 @@ inline GemmArgs gemm_args(ozmp_plan_s* p) {
             g.lock_w = p->env_lock;
             g.lock_n = p->sched_ntiles * (p->s * (p->s + 1) / 2);
         }
+        g.tc_snake = p->env_walk;
         g.cnt_region = cnt;
         g.tile_slot = (const int*)(w + p->off_tslot);
         g.sched_nitems = p->sched_items;
@@ -337,6 +339,10 @@ inline ozmp_status plan_schedule(ozmp_plan_s* p) {
         p->env_maxc = mxc ? atoi(mxc) : 0;
         const char* lk = getenv("OZMP_TC_LOCKSTEP");
         p->env_lock = lk ? atoi(lk) : 1;
+        // pair order (walk.h): 0 one diagonal at a time, 1 the snake (the same
+        // DRAM bytes and time at DD 4096^3, so the order with more drain slack stays)
+        const char* wk = getenv("OZMP_TC_WALK");
+        p->env_walk = (wk && wk[0] == '1') ? 1 : 0;
         // test hooks of the bounded waits: a smaller poll limit, and a stage
         // whose copies are never issued so that the waits on it run out
         const char* wl = getenv("OZMP_TC_WAIT_LIMIT");
