@@ -812,7 +812,8 @@ def main():
     # there, with the default tile order
     traffic = None
     if (oz.Form(info.form) == oz.Form.FP8_BAL and prec == "dd" and m == n == k == 4096 and info.nslices == 25
-            and os.environ.get("OZMP_TC_LOCKSTEP", "1") == "1" and os.environ.get("OZMP_TC_GROUP", "8") == "8"):
+            and os.environ.get("OZMP_TC_LOCKSTEP", "1") == "1" and os.environ.get("OZMP_TC_GROUP", "8") == "8"
+            and os.environ.get("OZMP_TC_WALK", "0") == "0"):
         traffic = 32.019e9 + 4.535e9
 
     line = {
