@@ -31,6 +31,7 @@ static ozmp_status plan_make_like(const ozmp_plan_s* p, int s, ozmp_plan_s* t) {
         t->env_group = p->env_group;
         t->env_maxc = p->env_maxc;
         t->env_lock = p->env_lock;
+        t->env_walk = p->env_walk;
         t->tc_wait_limit = p->tc_wait_limit;
         t->tc_inject_stall = p->tc_inject_stall;
     }

@@ -87,6 +87,10 @@ struct GemmArgs {
 // Tiles are taken in bands of `group` of the tm row tiles (0: column-major).
 // maxc: pair-range chunks of one tail tile at most (0: TC_MAX_CHUNKS).
 constexpr int TC_MAX_CHUNKS = 32;
+// The snake pair order (walk.h) overlaps each drain with one pair's MMAs
+// only, so it is the default where a pair takes long against a drain and the
+// operand panels are large: k >= TC_SNAKE_K.
+constexpr int64_t TC_SNAKE_K = 4096;
 int tc_schedule(int ntiles, int pairs, int sms, int* items, int* off, int* nitems, int* nslots, bool regroup,
                 int tm, int group, int maxc = 0);
 int tc_num_sms();

@@ -295,7 +295,7 @@ inline GemmArgs gemm_args(ozmp_plan_s* p) {
             g.lock_w = p->env_lock;
             g.lock_n = p->sched_ntiles * (p->s * (p->s + 1) / 2);
         }
-        g.tc_snake = p->env_walk;
+        g.tc_snake = p->env_walk >= 0 ? p->env_walk : (p->k >= TC_SNAKE_K ? 1 : 0);
         g.cnt_region = cnt;
         g.tile_slot = (const int*)(w + p->off_tslot);
         g.sched_nitems = p->sched_items;
@@ -339,10 +339,10 @@ inline ozmp_status plan_schedule(ozmp_plan_s* p) {
         p->env_maxc = mxc ? atoi(mxc) : 0;
         const char* lk = getenv("OZMP_TC_LOCKSTEP");
         p->env_lock = lk ? atoi(lk) : 1;
-        // pair order (walk.h): 0 one diagonal at a time, 1 the snake (the same
-        // DRAM bytes and time at DD 4096^3, so the order with more drain slack stays)
+        // pair order (walk.h): 0 one diagonal at a time, 1 the snake; unset: the
+        // snake where k >= TC_SNAKE_K
         const char* wk = getenv("OZMP_TC_WALK");
-        p->env_walk = (wk && wk[0] == '1') ? 1 : 0;
+        p->env_walk = wk ? (wk[0] == '1' ? 1 : 0) : -1;
         // test hooks of the bounded waits: a smaller poll limit, and a stage
         // whose copies are never issued so that the waits on it run out
         const char* wl = getenv("OZMP_TC_WAIT_LIMIT");
