@@ -809,12 +809,12 @@ def main():
     # DRAM bytes (read + write) of one launch of the product kernel, from the
     # one-pass ncu capture of this workload's launch in
     # profiles/k_gemm_tc_bal_dd4096_s25_dram.md; only for the workload captured
-    # there, with the default tile order
+    # there, with the default tile and pair orders
     traffic = None
     if (oz.Form(info.form) == oz.Form.FP8_BAL and prec == "dd" and m == n == k == 4096 and info.nslices == 25
             and os.environ.get("OZMP_TC_LOCKSTEP", "1") == "1" and os.environ.get("OZMP_TC_GROUP", "8") == "8"
-            and os.environ.get("OZMP_TC_WALK", "0") == "0"):
-        traffic = 32.230e9 + 4.562e9
+            and os.environ.get("OZMP_TC_WALK", "1") == "1"):
+        traffic = 18.865e9 + 3.367e9
 
     line = {
         "metric": metric, "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,

@@ -5,9 +5,9 @@
 //
 // Paper, Sec. 3, Algorithm 1: C_{alpha beta} := A_alpha B_beta over the pair
 // triangle, then the L-bit sum.  One CTA owns a 128 x 256 tile of C and walks
-// the triangle in the order of walk.h: one anti-diagonal at a time,
-// d = s+1 .. 2, as the mma.sync kernels (or, OZMP_TC_WALK=1, two
-// anti-diagonals interleaved so that consecutive pairs share an operand slice).
+// the triangle in the order of walk.h: where k >= 4096 two anti-diagonals
+// interleaved so that consecutive pairs share an operand slice, else one
+// anti-diagonal at a time, d = s+1 .. 2, as the mma.sync kernels.
 //
 // Roles (192 threads):
 //   warp 0      TMA producer: 128x128-byte A tile + 256x128-byte B tile per
