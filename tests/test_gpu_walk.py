@@ -7,7 +7,8 @@ exact integer limbs, so the product must not depend on the order: both are
 compared bit for bit with each other and, on sampled blocks, with the
 oracle's exact Ozaki sum.  The shapes cover tail tiles split into pair-range
 chunks, diagonals longer than one accumulator group (k = 8192: at most 8 or
-9 pairs per group), the single-CTA and CTA-pair tile forms, the binary16
+9 pairs per group in e4m3 digits, 2 in binary16 ones), the single-CTA and
+CTA-pair tile forms, the binary16
 digits with the widest digit (beta = 10, drains that reach a limb before the
 diagonal above them does), and the diagonal-only diagnostic launches.
 """
